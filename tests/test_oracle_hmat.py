@@ -1,0 +1,160 @@
+"""Pins of the oracle's H-matrix arithmetic against dense linear algebra
+(numpy/LAPACK) and the structural facts of Sections 3-6."""
+import numpy as np
+import pytest
+
+import hmat_synth as hs
+import oracle
+
+
+def random_hmatrix(bt, seed, k=3):
+    """H-matrix on bt with random dense leaves and random rank-k leaves
+    (inputs drawn from the seeded generator)."""
+    H = oracle.HMatrix.zero(bt)
+    bn = bt.nodes()
+    cn = bt.rows.nodes()
+    off = 0
+    for b in range(len(bn["t"])):
+        m, n = int(cn["size"][bn["t"][b]]), int(cn["size"][bn["s"][b]])
+        if bn["kind"][b] == 1:
+            H.set_dense(b, hs.normal(seed, m * n, off).reshape(n, m).T)
+            off += m * n
+        elif bn["kind"][b] == 2:
+            A = hs.normal(seed, m * k, off).reshape(k, m).T
+            off += m * k
+            B = hs.normal(seed, n * k, off).reshape(k, n).T * 0.3
+            off += n * k
+            H.set_lowrank(b, A, B)
+    return H
+
+
+def trees(N, d, leaf, eta=2.0):
+    ct = oracle.ClusterTree(hs.grid_coords(N, d), leaf)
+    return ct, oracle.BlockTree(ct, ct, eta)
+
+
+def test_from_csr_roundtrip():
+    p = hs.small_laplace(16, 2, 8, 0.0)
+    ct, bt, csr, H = oracle.setup(p)
+    perm = ct.perm()
+    assert np.array_equal(H.to_dense(), csr.to_dense()[np.ix_(perm, perm)])
+    assert np.all(H.ranks()[bt.nodes()["kind"] == 2] == 0)
+
+
+@pytest.mark.parametrize("N,d,leaf", [(16, 2, 8), (8, 3, 16)])
+def test_addeval_matches_dense(N, d, leaf):
+    ct, bt = trees(N, d, leaf)
+    H = random_hmatrix(bt, 11)
+    G = H.to_dense()
+    X = hs.normal(3, G.shape[0] * 4).reshape(-1, 4)
+    Y0 = hs.normal(4, G.shape[0] * 4).reshape(-1, 4)
+    assert np.allclose(H.addeval(0.5, X, Y0), Y0 + 0.5 * G @ X, atol=1e-12 * np.abs(G).max() * G.shape[0])
+    assert np.allclose(H.addeval(-2.0, X, Y0, trans=True), Y0 - 2.0 * G.T @ X,
+                       atol=1e-12 * np.abs(G).max() * G.shape[0])
+
+
+def product_tree_size(bt):
+    """#T_IJK from eq. (product_block): (t,s,r) in T_IJK iff (t,s) in T_IJ and
+    (s,r) in T_JK (here all three trees are the same)."""
+    bn = bt.nodes()
+    by_row = np.bincount(bn["t"], minlength=bn["t"].max() + 1)
+    return int(sum(by_row[s] for s in bn["s"]))
+
+
+@pytest.mark.parametrize("accumulated", [False, True])
+def test_hmul_exact_at_eps0(accumulated):
+    ct, bt = trees(16, 2, 8)
+    X, Y, Z = random_hmatrix(bt, 1), random_hmatrix(bt, 2), random_hmatrix(bt, 3)
+    Xd, Yd, Zd = X.to_dense(), Y.to_dense(), Z.to_dense()
+    oracle.stats_reset()
+    oracle.hmul(-0.5, X, Y, Z, 0.0, accumulated)
+    ref = Zd - 0.5 * Xd @ Yd
+    assert np.abs(Z.to_dense() - ref).max() <= 1e-12 * np.abs(ref).max()
+    st = oracle.stats()
+    if accumulated:
+        # every node of the product tree is visited exactly once
+        assert st["addproducts"] + st["pending"] == product_tree_size(bt)
+
+
+def test_hmul_truncated_error_and_modes_agree():
+    ct, bt = trees(32, 2, 8)
+    X, Y = random_hmatrix(bt, 5, k=2), random_hmatrix(bt, 6, k=2)
+    Xd, Yd = X.to_dense(), Y.to_dense()
+    ref = Xd @ Yd
+    nrm = np.linalg.norm(ref, 2)
+    res = {}
+    for acc in (False, True):
+        Z = oracle.HMatrix.zero(bt)
+        oracle.hmul(1.0, X, Y, Z, 1e-4, acc)
+        res[acc] = Z.to_dense()
+        # relative spectral error well below the truncation tolerance scale
+        assert np.linalg.norm(res[acc] - ref, 2) / nrm < 1e-3
+    assert np.linalg.norm(res[True] - res[False], 2) / nrm < 1e-3
+
+
+def dense_lu_nopivot(A):
+    M = A.copy()
+    for k in range(M.shape[0]):
+        M[k + 1:, k] /= M[k, k]
+        M[k + 1:, k + 1:] -= np.outer(M[k + 1:, k], M[k, k + 1:])
+    return M
+
+
+@pytest.mark.parametrize("N,d,leaf", [(32, 2, 16), (16, 2, 8), (8, 3, 16), (10, 3, 32)])
+@pytest.mark.parametrize("accumulated", [False, True])
+def test_hlu_eps0_is_dense_lu(N, d, leaf, accumulated):
+    p = hs.small_laplace(N, d, leaf, 0.0)
+    ct, bt, csr, H = oracle.setup(p)
+    perm = ct.perm()
+    A = csr.to_dense()[np.ix_(perm, perm)]
+    H.lu(0.0, accumulated)
+    D = H.to_dense()
+    n = A.shape[0]
+    L = np.tril(D, -1) + np.eye(n)
+    U = np.triu(D)
+    # L unit lower, U upper with L U = P A P^T determine the no-pivot LU
+    assert np.abs(L @ U - A).max() <= 1e-12 * np.abs(A).max()
+    assert np.abs(D - dense_lu_nopivot(A)).max() <= 1e-10 * np.abs(D).max()
+    # solves with the factors
+    b = hs.normal(8, n * 2).reshape(n, 2)
+    x = H.solve(b)
+    assert np.abs(A @ x - b).max() <= 1e-10 * np.abs(b).max()
+    y = H.solve(b, trans=True)
+    assert np.abs(A.T @ y - b).max() <= 1e-10 * np.abs(b).max()
+
+
+def precond_error_dense(D, A):
+    n = A.shape[0]
+    L = np.tril(D, -1) + np.eye(n)
+    U = np.triu(D)
+    E = np.eye(n) - np.linalg.solve(U, np.linalg.solve(L, A))
+    return np.linalg.norm(E, 2)
+
+
+@pytest.mark.parametrize("N,d,leaf,eps", [(32, 2, 16, 1e-3), (10, 3, 32, 1e-2)])
+def test_precond_error_power_iteration(N, d, leaf, eps):
+    p = hs.small_laplace(N, d, leaf, eps)
+    ct, bt, csr, H = oracle.setup(p)
+    perm = ct.perm()
+    A = csr.to_dense()[np.ix_(perm, perm)]
+    H.lu(eps, True)
+    exact = precond_error_dense(H.to_dense(), A)
+    est, it = H.precond_error(csr, hs.start_vector(p.n, 0)[perm], maxit=200, rtol=1e-6)
+    assert 0 < exact < 1
+    # power iteration converges to the largest singular value from below
+    assert est <= exact * (1 + 1e-9) and est >= 0.9 * exact
+
+
+def test_accumulated_fewer_truncations_same_quality():
+    p = hs.laplace2d_64()
+    res = {}
+    for acc in (False, True):
+        ct, bt, csr, H = oracle.setup(p)
+        oracle.stats_reset()
+        H.lu(p.eps, acc)
+        st = oracle.stats()
+        err, _ = H.precond_error(csr, hs.start_vector(p.n, 0))
+        res[acc] = (st["truncations"], st["flops_trunc"], err)
+    assert res[True][0] < res[False][0] and res[True][1] < res[False][1]
+    assert res[True][2] < 2 * res[False][2] + 1e-12
+    assert res[True][2] < 1e-4
