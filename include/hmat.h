@@ -1,0 +1,184 @@
+/*
+ * hmat.h -- C ABI of the GB300 (sm_103a) H-matrix library: truncated
+ * low-rank updates in the accumulated form of
+ *   S. Boerm, "Hierarchical matrix arithmetic with accumulated updates"
+ *   (arXiv:1703.09085),
+ * used inside the H-LU factorisation of finite-difference matrices.
+ *
+ * Conventions for every entry point:
+ *  - Return value: an hmat_status (HMAT_OK = 0).  No call aborts or throws
+ *    across this boundary; hmat_last_error() gives the message of the last
+ *    failure on the calling thread.
+ *  - Matrices are column-major FP64.  "host" arguments are ordinary host
+ *    pointers, "device" arguments are pointers into device memory of the
+ *    context's GPU.  Buffers passed in stay owned by the caller; the library
+ *    copies host inputs and uses device buffers in place where stated.
+ *  - Objects (contexts, trees, H-matrices) are opaque, owned by the library
+ *    and released by the matching *_destroy call.  An H-matrix lives in the
+ *    context's device memory.
+ *  - Calls taking a context run asynchronously on the context's CUDA stream
+ *    unless stated otherwise; *_build, *_nodes, *_perm and hmat_stats are
+ *    synchronous host calls.
+ */
+#ifndef HMAT_H
+#define HMAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HMAT_OK = 0,
+  HMAT_ERR_ARG = 1,        /* invalid argument or unsupported input          */
+  HMAT_ERR_NOMEM = 2,      /* device or host allocation failed               */
+  HMAT_ERR_SINGULAR = 3,   /* zero pivot in a dense leaf LU                   */
+  HMAT_ERR_NONFINITE = 4,  /* NaN or Inf produced or met                      */
+  HMAT_ERR_RANK = 5,       /* a truncated rank exceeded the block capacity    */
+  HMAT_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up              */
+  HMAT_ERR_CUDA = 7,       /* a CUDA runtime call failed                      */
+  HMAT_ERR_INTERNAL = 9
+} hmat_status;
+
+typedef struct hmat_ctx hmat_ctx;
+typedef struct hmat_ctree hmat_ctree;
+typedef struct hmat_btree hmat_btree;
+typedef struct hmat hmat;
+
+/* Options of the arithmetic.
+ *  eps        truncation tolerance: every truncation keeps the smallest rank k
+ *             with sum_{i>k} sigma_i^2 <= eps^2 sum_i sigma_i^2 (relative
+ *             Frobenius, per block); the paper leaves "choose new rank k"
+ *             open (Fig. rkadd).  eps = 0 keeps every nonzero singular value.
+ *  max_rank   capacity of every low-rank block and accumulator (<= 0: 64).
+ *             A truncation whose rank exceeds it keeps the first max_rank
+ *             singular triplets and reports HMAT_ERR_RANK.
+ *  precision  HMAT_FP64 or HMAT_MIXED (see hmat_lu).
+ *  spin_limit iterations of a bounded device-side dependency wait before it
+ *             gives up with HMAT_ERR_TIMEOUT (<= 0: library default). */
+enum { HMAT_FP64 = 0, HMAT_MIXED = 1 };
+typedef struct {
+  double eps;
+  int64_t max_rank;
+  int precision;
+  int64_t spin_limit;
+} hmat_opts;
+
+typedef struct {
+  int64_t n;              /* matrix dimension                                   */
+  int64_t blocks;         /* block-tree nodes                                   */
+  int64_t dense_leaves;
+  int64_t lowrank_leaves;
+  int64_t max_rank;       /* largest rank among admissible leaves               */
+  double mean_rank;
+  int64_t tasks;          /* device tasks of the last hmat_lu schedule          */
+  int64_t truncations;    /* rank-revealing factorisations of the last hmat_lu  */
+  double factor_seconds;  /* device time of the last hmat_lu numeric phase      */
+  double schedule_seconds;/* host time of the last hmat_lu symbolic phase       */
+  int64_t device_bytes;   /* device memory held by the H-matrix and its arena   */
+  int status;             /* device status word of the last hmat_lu             */
+} hmat_stats;
+
+/* Message of the last failure on this thread, copied into buf (NUL-terminated,
+ * truncated to size).  Returns the full length. */
+size_t hmat_last_error(char* buf, size_t size);
+
+/* Context on CUDA device `device`, issuing work on `cuda_stream` (a
+ * cudaStream_t, NULL for the legacy default stream).  The stream stays owned by
+ * the caller and must outlive the context. */
+hmat_status hmat_ctx_create(int device, void* cuda_stream, hmat_ctx** out);
+hmat_status hmat_ctx_destroy(hmat_ctx* ctx);
+
+/* Cluster tree (Section 2, Definition "Cluster tree") of n points in d = 2 or
+ * 3 dimensions by geometric bisection: a cluster with more than leaf_size
+ * points is split at the midpoint of its tight bounding box along the longest
+ * side (first side on ties); points below the midpoint go to the first son,
+ * order kept.  coords: host, n x d row-major.  Synchronous. */
+hmat_status hmat_clustertree_build(hmat_ctx* ctx, const double* coords, int64_t n, int d,
+                                   int64_t leaf_size, hmat_ctree** out);
+/* perm[i] = original index of permuted index i (host, caller-owned, n). */
+hmat_status hmat_clustertree_perm(const hmat_ctree* ct, int64_t* perm);
+int64_t hmat_clustertree_size(const hmat_ctree* ct);
+/* Per node (pre-order, root 0): first permuted index, size, level, parent
+ * (-1 for the root), number of sons.  Host arrays of hmat_clustertree_size. */
+hmat_status hmat_clustertree_nodes(const hmat_ctree* ct, int64_t* off, int64_t* size, int* level,
+                                   int* parent, int* nsons);
+hmat_status hmat_ctree_destroy(hmat_ctree* ct);
+
+/* Block tree (Section 2, Definition "Block tree"): (t, s) is an admissible
+ * leaf iff dist(t, s) > 0 and max(diam t, diam s) <= eta dist(t, s) (Euclidean
+ * box diameter and distance); otherwise an inadmissible leaf if t or s is a
+ * leaf, otherwise subdivided into sons(t) x sons(s).  Synchronous. */
+hmat_status hmat_blocktree_build(hmat_ctx* ctx, const hmat_ctree* rows, const hmat_ctree* cols,
+                                 double eta, hmat_btree** out);
+int64_t hmat_blocktree_size(const hmat_btree* bt);
+/* Per node (pre-order, root 0): row cluster, column cluster, level, parent,
+ * kind (0 subdivided, 1 inadmissible/dense leaf, 2 admissible/low-rank leaf). */
+hmat_status hmat_blocktree_nodes(const hmat_btree* bt, int* t, int* s, int* level, int* parent, int* kind);
+hmat_status hmat_btree_destroy(hmat_btree* bt);
+
+/* H-matrix on bt from a sparse matrix in CSR form in the ORIGINAL ordering
+ * (host arrays rowptr[n+1], colidx[nnz], val[nnz]); the library permutes.
+ * Admissible blocks start at rank 0; an entry inside an admissible block is
+ * rejected with HMAT_ERR_ARG (finite-difference stencils have none there,
+ * Section 3 opening paragraph).  The CSR arrays are copied to the device and
+ * scattered into the dense leaves by a kernel. */
+hmat_status hmat_create_from_csr(hmat_ctx* ctx, const hmat_btree* bt, int64_t n, const int64_t* rowptr,
+                                 const int64_t* colidx, const double* val, hmat** out);
+hmat_status hmat_destroy(hmat* H);
+
+/* Dense copy of H in the permuted ordering into out (device, n x n, ld n). */
+hmat_status hmat_to_dense(hmat_ctx* ctx, const hmat* H, double* out);
+
+/* Y <- Y + alpha H X (trans = 0) or Y <- Y + alpha H^T X (trans = 1): the
+ * multiplication by a thin dense matrix of Fig. addeval / addevaltrans.
+ * X, Y: device, n x ncol, leading dimension n, permuted ordering. */
+hmat_status hmat_addeval(hmat_ctx* ctx, const hmat* H, double alpha, int trans, int64_t ncol,
+                         const double* X, double* Y);
+
+/* In-place H-LU with accumulated updates: afterwards H holds the unit lower
+ * factor L (strictly lower part) and the upper factor U.  The recursion is the
+ * block LU with Schur complement of Section 6, accumulators split as in
+ * Fig. invert, products added by Fig. addproduct, flushed by Fig. flush.
+ * A host-side symbolic pass turns the recursion into a dependency-ordered task
+ * list that one persistent kernel executes.  precision HMAT_FP64 runs every
+ * task in FP64; HMAT_MIXED runs the factor products and the tall parts of the
+ * truncations in FP32 and keeps FP64 for R factors, the small core SVD and the
+ * leaf LU.  Returns the device status (HMAT_ERR_SINGULAR, _RANK, _TIMEOUT,
+ * _NONFINITE) after synchronising the stream. */
+hmat_status hmat_lu(hmat_ctx* ctx, hmat* H, const hmat_opts* opts);
+
+/* B <- (LU)^{-1} B (trans = 0) or (LU)^{-T} B (trans = 1) with the factors of
+ * hmat_lu; B: device, n x nrhs, leading dimension ldb, permuted ordering. */
+hmat_status hmat_solve(hmat_ctx* ctx, const hmat* LU, int trans, int64_t nrhs, double* B, int64_t ldb);
+
+/* Truncation of one low-rank matrix in place (Section 3, "Truncation"): with
+ * R = U V^T, U (m x k, ldu) and V (n x k, ldv) in device memory, overwrite the
+ * first k_new columns with the best approximation of the rank chosen by eps:
+ * U <- left singular vectors, V <- right singular vectors times the singular
+ * values (as Fig. rkadd returns C and D).  *k_new is written on the host after
+ * the stream is synchronised.  k <= 512. */
+hmat_status trunc_lowrank(hmat_ctx* ctx, int64_t m, int64_t n, int64_t k, double* U, int64_t ldu, double* V,
+                          int64_t ldv, double eps, int64_t* k_new);
+
+/* Batched truncation: count independent problems, problem i with sizes
+ * m[i], n[i], k[i] (host arrays, k[i] <= 256) and factors at the device
+ * pointers U[i] (ld m[i]) and V[i] (ld n[i]) (host array of device pointers).
+ * k_new is a DEVICE array of count entries receiving the new ranks.  One CTA
+ * per problem; the call synchronises the context stream before returning. */
+hmat_status trunc_lowrank_batched(hmat_ctx* ctx, int64_t count, const int64_t* m, const int64_t* n,
+                                  const int64_t* k, double* const* U, double* const* V, double eps,
+                                  int64_t* k_new);
+
+/* Statistics of H and of its last hmat_lu (synchronous). */
+hmat_status hmat_stats_get(const hmat* H, hmat_stats* out);
+
+/* Per block-tree node: rank of an admissible leaf, -1 otherwise (host array). */
+hmat_status hmat_ranks(const hmat* H, int64_t* ranks);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HMAT_H */

@@ -1,0 +1,241 @@
+"""GB300 (sm_103a) H-matrix arithmetic with accumulated updates.
+
+Thin ctypes binding of ``libhmat.so`` (C ABI declared in ``include/hmat.h``).
+Every function here only marshals arguments; all arithmetic runs in the CUDA
+kernels of ``csrc/``.  Device buffers are torch CUDA tensors (float64,
+contiguous, column-major by convention: a tensor of shape (ncol, n) holds an
+n x ncol column-major matrix) or raw device pointers.
+
+Importing this module loads the shared library; if it has not been built the
+import of any entry point raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhmat.so")
+_lib = None
+
+I64P = ctypes.POINTER(ctypes.c_int64)
+F64P = ctypes.POINTER(ctypes.c_double)
+I32P = ctypes.POINTER(ctypes.c_int)
+
+STATUS = {0: "HMAT_OK", 1: "HMAT_ERR_ARG", 2: "HMAT_ERR_NOMEM", 3: "HMAT_ERR_SINGULAR",
+          4: "HMAT_ERR_NONFINITE", 5: "HMAT_ERR_RANK", 6: "HMAT_ERR_TIMEOUT", 7: "HMAT_ERR_CUDA",
+          9: "HMAT_ERR_INTERNAL"}
+HMAT_FP64, HMAT_MIXED = 0, 1
+
+# Every symbol include/hmat.h declares.
+EXPORTS = ["hmat_last_error", "hmat_ctx_create", "hmat_ctx_destroy", "hmat_clustertree_build",
+           "hmat_clustertree_perm", "hmat_clustertree_size", "hmat_clustertree_nodes", "hmat_ctree_destroy",
+           "hmat_blocktree_build", "hmat_blocktree_size", "hmat_blocktree_nodes", "hmat_btree_destroy",
+           "hmat_create_from_csr", "hmat_destroy", "hmat_to_dense", "hmat_addeval", "hmat_lu", "hmat_solve",
+           "trunc_lowrank", "trunc_lowrank_batched", "hmat_stats_get", "hmat_ranks"]
+
+
+class HmatError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("max_rank", ctypes.c_int64), ("precision", ctypes.c_int),
+                ("spin_limit", ctypes.c_int64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("blocks", ctypes.c_int64), ("dense_leaves", ctypes.c_int64),
+                ("lowrank_leaves", ctypes.c_int64), ("max_rank", ctypes.c_int64), ("mean_rank", ctypes.c_double),
+                ("tasks", ctypes.c_int64), ("truncations", ctypes.c_int64), ("factor_seconds", ctypes.c_double),
+                ("schedule_seconds", ctypes.c_double), ("device_bytes", ctypes.c_int64), ("status", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def lib():
+    """The loaded libhmat.so; raises if it was not built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libhmat.so is not built: run paper_1703_09085_gb300.build.build() "
+                               "(nvcc, sm_103a); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        L.hmat_last_error.restype = ctypes.c_size_t
+        L.hmat_clustertree_size.restype = ctypes.c_int64
+        L.hmat_blocktree_size.restype = ctypes.c_int64
+        for name in EXPORTS:
+            if name not in ("hmat_last_error", "hmat_clustertree_size", "hmat_blocktree_size"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(1024)
+    lib().hmat_last_error(buf, ctypes.c_size_t(1024))
+    return buf.value.decode(errors="replace")
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise HmatError(rc, last_error())
+
+
+def _dptr(x) -> ctypes.c_void_p:
+    """Device pointer of a torch CUDA float64 tensor (or an int address)."""
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    if not x.is_cuda or x.dtype.__str__() != "torch.float64" or not x.is_contiguous():
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _hp(a: np.ndarray, t):
+    return a.ctypes.data_as(t)
+
+
+class Context:
+    """hmat_ctx_create on `device` issuing work on `stream` (torch stream, raw
+    cudaStream_t int, or None for the legacy default stream)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        if stream is not None and not isinstance(stream, int):
+            stream = stream.cuda_stream
+        h = ctypes.c_void_p()
+        _check(lib().hmat_ctx_create(ctypes.c_int(device), ctypes.c_void_p(stream or 0), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hmat_ctx_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+
+class ClusterTree:
+    def __init__(self, ctx: Context, coords: np.ndarray, leaf: int):
+        coords = np.ascontiguousarray(coords, dtype=np.float64)
+        self.n, self.d = coords.shape
+        h = ctypes.c_void_p()
+        _check(lib().hmat_clustertree_build(ctx.h, _hp(coords, F64P), ctypes.c_int64(self.n), ctypes.c_int(self.d),
+                                            ctypes.c_int64(leaf), ctypes.byref(h)))
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().hmat_ctree_destroy(self.h)
+            self.h = None
+
+    def perm(self) -> np.ndarray:
+        p = np.zeros(self.n, np.int64)
+        _check(lib().hmat_clustertree_perm(self.h, _hp(p, I64P)))
+        return p
+
+    def nodes(self) -> dict:
+        c = lib().hmat_clustertree_size(self.h)
+        off = np.zeros(c, np.int64)
+        size = np.zeros(c, np.int64)
+        level = np.zeros(c, np.int32)
+        parent = np.zeros(c, np.int32)
+        nsons = np.zeros(c, np.int32)
+        _check(lib().hmat_clustertree_nodes(self.h, _hp(off, I64P), _hp(size, I64P), _hp(level, I32P),
+                                            _hp(parent, I32P), _hp(nsons, I32P)))
+        return dict(off=off, size=size, level=level, parent=parent, nsons=nsons)
+
+
+class BlockTree:
+    def __init__(self, ctx: Context, rows: ClusterTree, cols: ClusterTree, eta: float):
+        self.rows, self.cols = rows, cols
+        h = ctypes.c_void_p()
+        _check(lib().hmat_blocktree_build(ctx.h, rows.h, cols.h, ctypes.c_double(eta), ctypes.byref(h)))
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().hmat_btree_destroy(self.h)
+            self.h = None
+
+    def nodes(self) -> dict:
+        c = lib().hmat_blocktree_size(self.h)
+        arrs = [np.zeros(c, np.int32) for _ in range(5)]
+        _check(lib().hmat_blocktree_nodes(self.h, *[_hp(a, I32P) for a in arrs]))
+        return dict(zip(["t", "s", "level", "parent", "kind"], arrs))
+
+
+class HMatrix:
+    """An H-matrix in device memory (hmat_create_from_csr)."""
+
+    def __init__(self, ctx: Context, bt: BlockTree, csr):
+        self.ctx, self.bt = ctx, bt
+        self.n = csr.n
+        rp = np.ascontiguousarray(csr.rowptr, np.int64)
+        ci = np.ascontiguousarray(csr.colidx, np.int64)
+        va = np.ascontiguousarray(csr.val, np.float64)
+        h = ctypes.c_void_p()
+        _check(lib().hmat_create_from_csr(ctx.h, bt.h, ctypes.c_int64(csr.n), _hp(rp, I64P), _hp(ci, I64P),
+                                          _hp(va, F64P), ctypes.byref(h)))
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().hmat_destroy(self.h)
+            self.h = None
+
+    def lu(self, eps: float, max_rank: int = 0, precision: int = HMAT_FP64, spin_limit: int = 0):
+        o = Opts(eps, max_rank, precision, spin_limit)
+        _check(lib().hmat_lu(self.ctx.h, self.h, ctypes.byref(o)))
+
+    def to_dense(self, out):
+        _check(lib().hmat_to_dense(self.ctx.h, self.h, _dptr(out)))
+
+    def addeval(self, alpha: float, X, Y, trans: bool = False):
+        ncol = X.shape[0] if X.dim() == 2 else 1
+        _check(lib().hmat_addeval(self.ctx.h, self.h, ctypes.c_double(alpha), ctypes.c_int(int(trans)),
+                                  ctypes.c_int64(ncol), _dptr(X), _dptr(Y)))
+
+    def solve(self, B, trans: bool = False):
+        nrhs = B.shape[0] if B.dim() == 2 else 1
+        _check(lib().hmat_solve(self.ctx.h, self.h, ctypes.c_int(int(trans)), ctypes.c_int64(nrhs), _dptr(B),
+                                ctypes.c_int64(self.n)))
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().hmat_stats_get(self.h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def ranks(self) -> np.ndarray:
+        r = np.zeros(lib().hmat_blocktree_size(self.bt.h), np.int64)
+        _check(lib().hmat_ranks(self.h, _hp(r, I64P)))
+        return r
+
+
+def trunc_lowrank(ctx: Context, U, V, eps: float) -> int:
+    """In-place truncation of U V^T; U: tensor (k, m) holding m x k column-major,
+    V: (k, n).  Returns the new rank (first columns hold the result)."""
+    k, m = U.shape
+    n = V.shape[1]
+    kn = ctypes.c_int64(0)
+    _check(lib().trunc_lowrank(ctx.h, ctypes.c_int64(m), ctypes.c_int64(n), ctypes.c_int64(k), _dptr(U),
+                               ctypes.c_int64(max(m, 1)), _dptr(V), ctypes.c_int64(max(n, 1)), ctypes.c_double(eps),
+                               ctypes.byref(kn)))
+    return kn.value
+
+
+def trunc_lowrank_batched(ctx: Context, Us, Vs, eps: float, k_new) -> None:
+    """Batched in-place truncation; Us[i]: (k_i, m_i) tensors, Vs[i]: (k_i, n_i),
+    k_new: int64 CUDA tensor of len(Us) receiving the new ranks."""
+    cnt = len(Us)
+    m = np.array([u.shape[1] for u in Us], np.int64)
+    k = np.array([u.shape[0] for u in Us], np.int64)
+    n = np.array([v.shape[1] for v in Vs], np.int64)
+    up = (ctypes.c_void_p * cnt)(*[_dptr(u).value for u in Us])
+    vp = (ctypes.c_void_p * cnt)(*[_dptr(v).value for v in Vs])
+    _check(lib().trunc_lowrank_batched(ctx.h, ctypes.c_int64(cnt), _hp(m, I64P), _hp(n, I64P), _hp(k, I64P), up, vp,
+                                       ctypes.c_double(eps), ctypes.c_void_p(k_new.data_ptr())))

@@ -1,0 +1,483 @@
+// hmat_device.cuh -- CTA-level FP64 building blocks of the H-matrix tasks.
+//
+// Every routine here is executed by all HM_THREADS threads of one CTA and
+// synchronises the CTA with __syncthreads(); none of them waits on another CTA.
+// Matrices are column-major FP64 in global memory (L2 resident for the block
+// sizes of the hot path); small square cores live in shared memory.
+//
+// Dense building blocks follow the textbook mathematics: Householder QR with
+// reflectors P = I - tau v v^T built from the column scaled by its largest
+// entry (so squared norms cannot under/overflow), one-sided Jacobi SVD
+// (Hestenes 1958; Demmel and Veselic 1992) with the parallel round-robin
+// ordering, no-pivot Gaussian elimination.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hmat_tasks.h"
+
+#define HM_THREADS 256
+#define HM_WARPS (HM_THREADS / 32)
+#define HM_LMAX 256            // largest stacked width of a truncation
+#define HM_JAC_SMEM 9216       // doubles of shared memory for the Jacobi core
+
+namespace hm {
+
+// Shared-memory layout of one CTA (dynamic shared memory).
+struct Smem {
+  double red[HM_WARPS * 2];
+  double bcast[8];
+  double tauB[HM_LMAX];
+  double rdiagB[HM_LMAX];
+  double tauA[HM_LMAX];
+  double rdiagA[HM_LMAX];
+  double sigma[HM_LMAX];
+  int order[HM_LMAX];
+  int ivals[16];
+  double jac[HM_JAC_SMEM];
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide sum / max; result returned to every thread.
+__device__ __forceinline__ double block_sum(double v, Smem& s) {
+  v = warp_sum(v);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) s.red[w] = v;
+  __syncthreads();
+  double r = 0.0;
+#pragma unroll
+  for (int i = 0; i < HM_WARPS; ++i) r += s.red[i];
+  return r;
+}
+__device__ __forceinline__ double block_max(double v, Smem& s) {
+  v = warp_max(v);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) s.red[w] = v;
+  __syncthreads();
+  double r = 0.0;
+#pragma unroll
+  for (int i = 0; i < HM_WARPS; ++i) r = fmax(r, s.red[i]);
+  return r;
+}
+
+__device__ __forceinline__ void set_status(int* status, int code) {
+  atomicCAS(status, 0, code);
+}
+
+// ---------------------------------------------------------------------------
+// Householder QR in place: X (rows x cols, ld) -> reflectors v_j stored in
+// X(j:rows, j) (v scaled, first entry explicit), tau[j], R diagonal rdiag[j],
+// R(i, c) = X(i, c) for c > i.  q = min(rows, cols) reflectors.
+// ---------------------------------------------------------------------------
+__device__ void cta_qr(double* X, int ld, int rows, int cols, double* tau, double* rdiag, Smem& s) {
+  int q = rows < cols ? rows : cols;
+  int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int j = 0; j < q; ++j) {
+    double* xj = X + (int64_t)j * ld;
+    double mx = 0.0;
+    for (int i = j + tid; i < rows; i += HM_THREADS) mx = fmax(mx, fabs(xj[i]));
+    mx = block_max(mx, s);
+    if (mx == 0.0) {
+      if (tid == 0) {
+        tau[j] = 0.0;
+        rdiag[j] = 0.0;
+      }
+      __syncthreads();
+      continue;
+    }
+    double inv = 1.0 / mx;
+    double tail = 0.0;
+    for (int i = j + 1 + tid; i < rows; i += HM_THREADS) {
+      double v = xj[i] * inv;
+      tail += v * v;
+    }
+    tail = block_sum(tail, s);
+    if (tid == 0) {
+      double v0 = xj[j] * inv;
+      double xn = sqrt(tail + v0 * v0);
+      double alpha = v0 >= 0.0 ? -xn : xn;
+      double v0n = v0 - alpha;
+      tau[j] = 2.0 / (tail + v0n * v0n);
+      rdiag[j] = alpha * mx;
+      s.bcast[0] = v0n;
+    }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < rows; i += HM_THREADS) xj[i] *= inv;
+    if (tid == 0) xj[j] = s.bcast[0];
+    __syncthreads();
+    double tj = tau[j];
+    for (int c = j + 1 + warp; c < cols; c += HM_WARPS) {
+      double* xc = X + (int64_t)c * ld;
+      double d = 0.0;
+      for (int i = j + lane; i < rows; i += 32) d += xj[i] * xc[i];
+      d = warp_sum(d) * tj;
+      for (int i = j + lane; i < rows; i += 32) xc[i] -= d * xj[i];
+    }
+    __syncthreads();
+  }
+}
+
+// Apply Q = P_0 P_1 ... P_{q-1} (reflectors of cta_qr stored in V) to the
+// matrix Y (rows x ncols, ld): Y <- Q Y.  Reflectors are applied in reverse.
+__device__ void cta_apply_q(const double* V, int ldv, int rows, int q, const double* tau, double* Y, int ldy,
+                            int ncols) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int j = q - 1; j >= 0; --j) {
+    double tj = tau[j];
+    if (tj != 0.0) {
+      const double* vj = V + (int64_t)j * ldv;
+      for (int c = warp; c < ncols; c += HM_WARPS) {
+        double* yc = Y + (int64_t)c * ldy;
+        double d = 0.0;
+        for (int i = j + lane; i < rows; i += 32) d += vj[i] * yc[i];
+        d = warp_sum(d) * tj;
+        for (int i = j + lane; i < rows; i += 32) yc[i] -= d * vj[i];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One-sided Jacobi on J (p x c, ld p, p >= c) with accumulated rotations
+// Vr (c x c, ld c): on return J's columns are mutually orthogonal and
+// J_in Vr = J_out.
+// ---------------------------------------------------------------------------
+__device__ void cta_jacobi(double* J, int p, int c, double* Vr, Smem& s) {
+  int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int idx = tid; idx < c * c; idx += HM_THREADS) Vr[idx] = (idx % c == idx / c) ? 1.0 : 0.0;
+  __syncthreads();
+  if (c < 2) return;
+  int N = c + (c & 1);
+  const double tol = 1e-15;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    if (tid == 0) s.ivals[0] = 0;
+    __syncthreads();
+    for (int r = 0; r < N - 1; ++r) {
+      for (int k = warp; k < N / 2; k += HM_WARPS) {
+        int a, b;
+        if (k == 0) {
+          a = r;
+          b = N - 1;
+        } else {
+          a = (r + k) % (N - 1);
+          b = (r - k + (N - 1)) % (N - 1);
+        }
+        if (a > b) {
+          int t = a;
+          a = b;
+          b = t;
+        }
+        if (b >= c) continue;
+        double* ja = J + (int64_t)a * p;
+        double* jb = J + (int64_t)b * p;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int i = lane; i < p; i += 32) {
+          double x = ja[i], y = jb[i];
+          al += x * x;
+          be += y * y;
+          ga += x * y;
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (al == 0.0 || be == 0.0) continue;
+        if (fabs(ga) <= tol * sqrt(al) * sqrt(be)) continue;
+        double zeta = (be - al) / (2.0 * ga);
+        double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double cs = 1.0 / sqrt(1.0 + t * t);
+        double sn = cs * t;
+        for (int i = lane; i < p; i += 32) {
+          double x = ja[i], y = jb[i];
+          ja[i] = cs * x - sn * y;
+          jb[i] = sn * x + cs * y;
+        }
+        double* va = Vr + (int64_t)a * c;
+        double* vb = Vr + (int64_t)b * c;
+        for (int i = lane; i < c; i += 32) {
+          double x = va[i], y = vb[i];
+          va[i] = cs * x - sn * y;
+          vb[i] = sn * x + cs * y;
+        }
+        if (lane == 0) s.ivals[0] = 1;
+      }
+      __syncthreads();
+    }
+    int rotated = s.ivals[0];
+    __syncthreads();
+    if (!rotated) break;
+  }
+}
+
+// Column norms of J into sigma, and the order of decreasing sigma into order.
+__device__ void cta_sort_sigma(const double* J, int p, int c, Smem& s) {
+  int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int j = warp; j < c; j += HM_WARPS) {
+    const double* jj = J + (int64_t)j * p;
+    double x = 0.0;
+    for (int i = lane; i < p; i += 32) x += jj[i] * jj[i];
+    x = warp_sum(x);
+    if (lane == 0) s.sigma[j] = sqrt(x);
+  }
+  __syncthreads();
+  for (int j = tid; j < c; j += HM_THREADS) {
+    double sj = s.sigma[j];
+    int rk = 0;
+    for (int i = 0; i < c; ++i) {
+      double si = s.sigma[i];
+      rk += (si > sj) || (si == sj && i < j);
+    }
+    s.order[rk] = j;
+  }
+  __syncthreads();
+}
+
+// "Choose new rank k": smallest k with sum_{i>k} s_i^2 <= eps^2 sum_i s_i^2.
+__device__ int cta_choose_rank(int c, double eps, Smem& s) {
+  if (threadIdx.x == 0) {
+    double total = 0.0;
+    for (int i = 0; i < c; ++i) {
+      double x = s.sigma[s.order[i]];
+      total += x * x;
+    }
+    double bound = eps * eps * total;
+    double tail = 0.0;
+    int k = c;
+    while (k > 0) {
+      double x = s.sigma[s.order[k - 1]];
+      if (tail + x * x <= bound) {
+        tail += x * x;
+        --k;
+      } else {
+        break;
+      }
+    }
+    s.ivals[1] = k;
+  }
+  __syncthreads();
+  int k = s.ivals[1];
+  __syncthreads();
+  return k;
+}
+
+// ---------------------------------------------------------------------------
+// Truncation core (Section 3 "Truncation", Fig. rkadd, Fig. rowmerge).
+//
+// R = sum_j SA_j SB_j^T with nb (1 or 2) blocks; block j has SA_j (m x k_j,
+// ld m) and SB_j (n_j x k_j, ld n_j), the SB_j stacked (rows n_0 then n_1) in
+// the result.  nb = 1 is rkadd on the stacked factors, nb = 2 is rowmerge.
+// SB_j are overwritten (QR reflectors).  W is scratch of m x (sum q_j).
+// Result: U (m x k, ld ldu) = left singular vectors, V (sum n_j x k, ld ldv)
+// = right singular vectors times singular values; k returned (<= cap).
+// ---------------------------------------------------------------------------
+struct TruncIn {
+  int nb;
+  int m;
+  int n[2];
+  int k[2];
+  const double* SA[2];
+  double* SB[2];
+  double* W;        // m x (q0 + q1)
+  double* Jg;       // global fallback for the Jacobi core (p*c + c*c doubles)
+};
+
+__device__ int trunc_core(const TruncIn& in, double eps, int cap, double* U, int ldu, double* V, int ldv,
+                          int* status, Smem& s) {
+  int tid = threadIdx.x;
+  int m = in.m;
+  int q[2] = {0, 0};
+  int qoff[2] = {0, 0};
+  for (int j = 0; j < in.nb; ++j) q[j] = in.n[j] < in.k[j] ? in.n[j] : in.k[j];
+  qoff[1] = q[0];
+  int qs = q[0] + (in.nb > 1 ? q[1] : 0);
+  // tauB / rdiagB hold both blocks' reflectors at offsets qoff.
+  for (int j = 0; j < in.nb; ++j)
+    cta_qr(in.SB[j], in.n[j], in.n[j], in.k[j], s.tauB + qoff[j], s.rdiagB + qoff[j], s);
+  if (m == 0 || qs == 0) return 0;
+  // Ahat = [SA_0 R_0^T, SA_1 R_1^T]  (m x qs)
+  for (int j = 0; j < in.nb; ++j) {
+    const double* SA = in.SA[j];
+    const double* SB = in.SB[j];
+    int nj = in.n[j], kj = in.k[j];
+    for (int idx = tid; idx < m * q[j]; idx += HM_THREADS) {
+      int r = idx % m, i = idx / m;
+      double acc = SA[(int64_t)i * m + r] * s.rdiagB[qoff[j] + i];
+      for (int c = i + 1; c < kj; ++c) acc += SA[(int64_t)c * m + r] * SB[(int64_t)c * nj + i];
+      in.W[(int64_t)(qoff[j] + i) * m + r] = acc;
+    }
+  }
+  __syncthreads();
+  // QR of Ahat
+  cta_qr(in.W, m, m, qs, s.tauA, s.rdiagA, s);
+  int qa = m < qs ? m : qs;
+  // Jacobi core: case A (qa == qs): J = R_A (qs x qs); case B: J = R_A^T (qs x qa)
+  bool caseA = (qa == qs);
+  int p = caseA ? qs : qs;
+  int c = caseA ? qs : qa;
+  double* J;
+  double* Vr;
+  if ((int64_t)p * c + (int64_t)c * c <= HM_JAC_SMEM) {
+    J = s.jac;
+  } else {
+    J = in.Jg;
+  }
+  Vr = J + (int64_t)p * c;
+  for (int idx = tid; idx < p * c; idx += HM_THREADS) {
+    int i = idx % p, j = idx / p;
+    // R_A(row, col) with row < qa, col < qs
+    int row = caseA ? i : j, col = caseA ? j : i;
+    double v;
+    if (row > col) v = 0.0;
+    else if (row == col) v = s.rdiagA[row];
+    else v = in.W[(int64_t)col * m + row];
+    J[idx] = v;
+  }
+  __syncthreads();
+  cta_jacobi(J, p, c, Vr, s);
+  cta_sort_sigma(J, p, c, s);
+  int k = cta_choose_rank(c, eps, s);
+  if (k > cap) {
+    if (tid == 0) set_status(status, DS_RANK);
+    k = cap;
+  }
+  // Left factor: U = Q_A [left(:, order[0:k]); 0]
+  for (int idx = tid; idx < m * k; idx += HM_THREADS) {
+    int r = idx % m, jj = idx / m;
+    int col = s.order[jj];
+    double v = 0.0;
+    if (r < qa) {
+      if (caseA) {
+        double sg = s.sigma[col];
+        v = sg > 0.0 ? J[(int64_t)col * p + r] / sg : 0.0;
+      } else {
+        v = Vr[(int64_t)col * c + r];
+      }
+    }
+    U[(int64_t)jj * ldu + r] = v;
+  }
+  // Right factor per block j: V_j = Q_j [right(qoff_j : qoff_j + q_j, order) * sigma; 0]
+  int voff = 0;
+  for (int j = 0; j < in.nb; ++j) {
+    int nj = in.n[j];
+    for (int idx = tid; idx < nj * k; idx += HM_THREADS) {
+      int r = idx % nj, jj = idx / nj;
+      int col = s.order[jj];
+      double v = 0.0;
+      if (r < q[j]) {
+        int rr = qoff[j] + r;
+        if (caseA) v = Vr[(int64_t)col * c + rr] * s.sigma[col];
+        else v = J[(int64_t)col * p + rr];
+      }
+      V[(int64_t)jj * ldv + voff + r] = v;
+    }
+    voff += nj;
+  }
+  __syncthreads();
+  cta_apply_q(in.W, m, m, qa, s.tauA, U, ldu, k);
+  voff = 0;
+  for (int j = 0; j < in.nb; ++j) {
+    cta_apply_q(in.SB[j], in.n[j], in.n[j], q[j], s.tauB + qoff[j], V + voff, ldv, k);
+    voff += in.n[j];
+  }
+  return k;
+}
+
+// ---------------------------------------------------------------------------
+// Dense leaf operations
+// ---------------------------------------------------------------------------
+// No-pivot LU in place (L unit lower, U upper).
+__device__ void cta_lu(double* A, int ld, int n, int* status) {
+  int tid = threadIdx.x;
+  for (int k = 0; k < n; ++k) {
+    double piv = A[(int64_t)k * ld + k];
+    if (piv == 0.0 || !isfinite(piv)) {
+      if (tid == 0) set_status(status, piv == 0.0 ? DS_SINGULAR : DS_NONFINITE);
+      return;
+    }
+    double inv = 1.0 / piv;
+    for (int i = k + 1 + tid; i < n; i += HM_THREADS) A[(int64_t)k * ld + i] *= inv;
+    __syncthreads();
+    int rem = n - k - 1;
+    for (int idx = tid; idx < rem * rem; idx += HM_THREADS) {
+      int i = k + 1 + idx % rem, j = k + 1 + idx / rem;
+      A[(int64_t)j * ld + i] -= A[(int64_t)k * ld + i] * A[(int64_t)j * ld + k];
+    }
+    __syncthreads();
+  }
+}
+
+// Thin solves with a dense diagonal leaf N (n x n, ld): X (n x w, ldx).
+__device__ void cta_trsm(int kind, const double* N, int ld, int n, double* X, int ldx, int w) {
+  int tid = threadIdx.x;
+  if (w <= 0) return;
+  if (kind == TRSM_L) {  // X <- L^{-1} X, forward, unit diagonal
+    for (int k = 0; k < n - 1; ++k) {
+      int rem = n - k - 1;
+      for (int idx = tid; idx < rem * w; idx += HM_THREADS) {
+        int i = k + 1 + idx % rem, c = idx / rem;
+        X[(int64_t)c * ldx + i] -= N[(int64_t)k * ld + i] * X[(int64_t)c * ldx + k];
+      }
+      __syncthreads();
+    }
+  } else if (kind == TRSM_U) {  // X <- U^{-1} X, backward
+    for (int k = n - 1; k >= 0; --k) {
+      for (int c = tid; c < w; c += HM_THREADS) X[(int64_t)c * ldx + k] /= N[(int64_t)k * ld + k];
+      __syncthreads();
+      for (int idx = tid; idx < k * w; idx += HM_THREADS) {
+        int i = idx % k, c = idx / k;
+        X[(int64_t)c * ldx + i] -= N[(int64_t)k * ld + i] * X[(int64_t)c * ldx + k];
+      }
+      __syncthreads();
+    }
+  } else if (kind == TRSM_UT) {  // X <- U^{-T} X, forward
+    for (int k = 0; k < n; ++k) {
+      for (int c = tid; c < w; c += HM_THREADS) X[(int64_t)c * ldx + k] /= N[(int64_t)k * ld + k];
+      __syncthreads();
+      int rem = n - k - 1;
+      for (int idx = tid; idx < rem * w; idx += HM_THREADS) {
+        int i = k + 1 + idx % rem, c = idx / rem;
+        X[(int64_t)c * ldx + i] -= N[(int64_t)i * ld + k] * X[(int64_t)c * ldx + k];
+      }
+      __syncthreads();
+    }
+  } else {  // TRSM_LT: X <- L^{-T} X, backward, unit diagonal
+    for (int k = n - 1; k > 0; --k) {
+      for (int idx = tid; idx < k * w; idx += HM_THREADS) {
+        int i = idx % k, c = idx / k;
+        X[(int64_t)c * ldx + i] -= N[(int64_t)i * ld + k] * X[(int64_t)c * ldx + k];
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// C (m x n, ldc) (+)= alpha op(A) op(B), op(A) m x kk, op(B) kk x n.
+__device__ void cta_gemm(double* C, int ldc, int m, int n, int kk, double alpha, const double* A, int lda,
+                         bool ta, const double* B, int ldb, bool tb, bool zero) {
+  int tid = threadIdx.x;
+  for (int idx = tid; idx < m * n; idx += HM_THREADS) {
+    int i = idx % m, j = idx / m;
+    double acc = 0.0;
+    for (int l = 0; l < kk; ++l) {
+      double a = ta ? A[(int64_t)i * lda + l] : A[(int64_t)l * lda + i];
+      double b = tb ? B[(int64_t)l * ldb + j] : B[(int64_t)j * ldb + l];
+      acc += a * b;
+    }
+    double* c = C + (int64_t)j * ldc + i;
+    *c = zero ? alpha * acc : *c + alpha * acc;
+  }
+}
+
+}  // namespace hm

@@ -1,0 +1,1790 @@
+// hmat_host.cpp -- host side of the GB300 H-matrix library and its C ABI.
+//
+// Trees are built on the host (they are integer work, negligible next to the
+// arithmetic).  The numerical recursions -- H-LU with accumulated updates
+// (Section 6 with Section 4's addproduct / split / flush), the H-matrix solve
+// and the H x thin-dense product (Fig. addeval) -- are unrolled by a symbolic
+// pass into a task list in program order.  A task's predecessors are found by
+// tracking, per memory object, its last writer and the readers since; scratch
+// memory comes from size-classed free lists whose chunks are memory objects
+// too, so reusing a chunk orders the new writer after the old readers.  The
+// task list runs in one persistent kernel (hmat_kernels.cu).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "hmat.h"
+#include "hmat_kernels.h"
+#include "hmat_tasks.h"
+
+using namespace hm;
+
+namespace {
+
+struct HmError : std::runtime_error {
+  int code;
+  HmError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define HM_CUDA(call)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      throw HmError(e_ == cudaErrorMemoryAllocation ? HMAT_ERR_NOMEM : HMAT_ERR_CUDA,   \
+                    std::string(#call) + ": " + cudaGetErrorString(e_));                \
+  } while (0)
+
+thread_local std::string g_last_error;
+
+template <class F>
+hmat_status guarded(F f) {
+  try {
+    f();
+    return HMAT_OK;
+  } catch (const HmError& e) {
+    g_last_error = e.what();
+    return (hmat_status)e.code;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return HMAT_ERR_NOMEM;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return HMAT_ERR_INTERNAL;
+  }
+}
+
+void require(bool ok, const char* msg) {
+  if (!ok) throw HmError(HMAT_ERR_ARG, msg);
+}
+
+const int64_t DEFAULT_MAX_RANK = 64;
+const int64_t HM_LMAX_HOST = 256;  // largest stacked width a truncation task accepts
+const int64_t TAG_SHIFT = 60;
+inline int64_t tag_ws(int64_t off) { return off | ((int64_t)1 << TAG_SHIFT); }
+inline int64_t tag_ext(int which, int64_t off) { return off | ((int64_t)(2 + which) << TAG_SHIFT); }
+
+// Device buffer that frees itself.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() {}
+  explicit DevBuf(size_t b) { alloc(b); }
+  void alloc(size_t b) {
+    release();
+    if (b == 0) b = 16;
+    HM_CUDA(cudaMalloc(&p, b));
+    bytes = b;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  ~DevBuf() { release(); }
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  template <class T>
+  T* as() const {
+    return (T*)p;
+  }
+};
+
+template <class T>
+void upload(DevBuf& b, const std::vector<T>& v, cudaStream_t st) {
+  b.alloc(v.size() * sizeof(T));
+  if (!v.empty()) HM_CUDA(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+}
+
+}  // namespace
+
+// ===========================================================================
+// Context
+// ===========================================================================
+struct hmat_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  int blocks_per_sm = 1;
+};
+
+// ===========================================================================
+// Trees (Section 2)
+// ===========================================================================
+struct CNodeH {
+  int64_t off = 0, size = 0;
+  int level = 0, parent = -1, nsons = 0;
+  int son[2] = {-1, -1};
+  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+};
+
+struct hmat_ctree {
+  int d = 0;
+  std::vector<CNodeH> nodes;
+  std::vector<int64_t> perm;
+};
+
+struct BNodeH {
+  int t = 0, s = 0, level = 0, parent = -1, kind = 0;
+  int son0 = 0, nsons = 0;
+};
+
+struct hmat_btree {
+  const hmat_ctree* R = nullptr;
+  const hmat_ctree* C = nullptr;
+  std::vector<BNodeH> nodes;
+  std::vector<int> sons;
+  int child(int b, int i, int j) const {
+    const BNodeH& nd = nodes[(size_t)b];
+    return sons[(size_t)(nd.son0 + i * C->nodes[(size_t)nd.s].nsons + j)];
+  }
+};
+
+namespace {
+
+// Geometric bisection on idx[lo, hi): tight box, longest side (first on
+// ties), stable partition at the box midpoint.  idx ends as the permutation.
+int ct_rec(hmat_ctree& T, const double* x, std::vector<int64_t>& idx, std::vector<int64_t>& tmp, int64_t lo,
+           int64_t hi, int level, int parent, int64_t leaf) {
+  int id = (int)T.nodes.size();
+  T.nodes.emplace_back();
+  CNodeH nd;
+  nd.off = lo;
+  nd.size = hi - lo;
+  nd.level = level;
+  nd.parent = parent;
+  int d = T.d;
+  for (int a = 0; a < d; ++a) {
+    nd.lo[a] = INFINITY;
+    nd.hi[a] = -INFINITY;
+  }
+  for (int64_t i = lo; i < hi; ++i)
+    for (int a = 0; a < d; ++a) {
+      double v = x[idx[(size_t)i] * d + a];
+      nd.lo[a] = std::min(nd.lo[a], v);
+      nd.hi[a] = std::max(nd.hi[a], v);
+    }
+  if (hi - lo > leaf) {
+    int dim = 0;
+    double ext = nd.hi[0] - nd.lo[0];
+    for (int a = 1; a < d; ++a)
+      if (nd.hi[a] - nd.lo[a] > ext) {
+        ext = nd.hi[a] - nd.lo[a];
+        dim = a;
+      }
+    double mid = (nd.lo[dim] + nd.hi[dim]) / 2.0;
+    int64_t nlo = 0, nhi = 0;
+    for (int64_t i = lo; i < hi; ++i)
+      if (x[idx[(size_t)i] * d + dim] < mid) idx[(size_t)(lo + nlo++)] = idx[(size_t)i];
+      else tmp[(size_t)(nhi++)] = idx[(size_t)i];
+    for (int64_t i = 0; i < nhi; ++i) idx[(size_t)(lo + nlo + i)] = tmp[(size_t)i];
+    if (nlo == 0 || nhi == 0) throw HmError(HMAT_ERR_ARG, "cluster tree: points cannot be bisected (duplicates?)");
+    T.nodes[(size_t)id] = nd;
+    int s0 = ct_rec(T, x, idx, tmp, lo, lo + nlo, level + 1, id, leaf);
+    int s1 = ct_rec(T, x, idx, tmp, lo + nlo, hi, level + 1, id, leaf);
+    T.nodes[(size_t)id].nsons = 2;
+    T.nodes[(size_t)id].son[0] = s0;
+    T.nodes[(size_t)id].son[1] = s1;
+  } else {
+    T.nodes[(size_t)id] = nd;
+  }
+  return id;
+}
+
+double box_diam(const CNodeH& c, int d) {
+  double x = 0.0;
+  for (int a = 0; a < d; ++a) {
+    double e = c.hi[a] - c.lo[a];
+    x += e * e;
+  }
+  return std::sqrt(x);
+}
+
+double box_dist(const CNodeH& p, const CNodeH& q, int d) {
+  double x = 0.0;
+  for (int a = 0; a < d; ++a) {
+    double g = std::max(0.0, std::max(p.lo[a] - q.hi[a], q.lo[a] - p.hi[a]));
+    x += g * g;
+  }
+  return std::sqrt(x);
+}
+
+int bt_rec(hmat_btree& B, int t, int s, int level, int parent, double eta) {
+  int id = (int)B.nodes.size();
+  BNodeH nd;
+  nd.t = t;
+  nd.s = s;
+  nd.level = level;
+  nd.parent = parent;
+  B.nodes.push_back(nd);
+  const CNodeH& ct = B.R->nodes[(size_t)t];
+  const CNodeH& cs = B.C->nodes[(size_t)s];
+  int d = B.R->d;
+  double dst = box_dist(ct, cs, d);
+  if (dst > 0.0 && std::max(box_diam(ct, d), box_diam(cs, d)) <= eta * dst) {
+    B.nodes[(size_t)id].kind = 2;
+    return id;
+  }
+  if (ct.nsons == 0 || cs.nsons == 0) {
+    B.nodes[(size_t)id].kind = 1;
+    return id;
+  }
+  std::vector<int> kids;
+  for (int i = 0; i < ct.nsons; ++i)
+    for (int j = 0; j < cs.nsons; ++j) kids.push_back(bt_rec(B, ct.son[i], cs.son[j], level + 1, id, eta));
+  B.nodes[(size_t)id].son0 = (int)B.sons.size();
+  B.nodes[(size_t)id].nsons = (int)kids.size();
+  B.sons.insert(B.sons.end(), kids.begin(), kids.end());
+  return id;
+}
+
+}  // namespace
+
+// ===========================================================================
+// H-matrix: device storage of every leaf
+// ===========================================================================
+struct hmat {
+  hmat_ctx* ctx = nullptr;
+  const hmat_btree* bt = nullptr;
+  int64_t n = 0;
+  int64_t max_rank = DEFAULT_MAX_RANK;
+  std::vector<int64_t> loc, vloc;  // per block: N or U offset, V offset (doubles)
+  std::vector<int> cap, slot;
+  std::vector<char> zero;          // statically known zero leaf
+  int nslots = 0;
+  DevBuf store;                    // leaves
+  DevBuf ranks;                    // rank slots of the low-rank leaves
+  int64_t store_doubles = 0;
+  hmat_stats st{};
+  int64_t rows(int b) const { return bt->R->nodes[(size_t)bt->nodes[(size_t)b].t].size; }
+  int64_t cols(int b) const { return bt->C->nodes[(size_t)bt->nodes[(size_t)b].s].size; }
+  int kind(int b) const { return bt->nodes[(size_t)b].kind; }
+  const CNodeH& tc(int b) const { return bt->R->nodes[(size_t)bt->nodes[(size_t)b].t]; }
+  const CNodeH& sc(int b) const { return bt->C->nodes[(size_t)bt->nodes[(size_t)b].s]; }
+};
+
+namespace {
+
+// ===========================================================================
+// Task scheduler
+// ===========================================================================
+struct Sched {
+  std::vector<HTask> tasks;
+  std::vector<int64_t> dep_ptr{0};
+  std::vector<int32_t> dep_idx;
+  std::vector<LeafRef> leaves;
+  struct Obj {
+    int32_t writer = -1;
+    std::vector<int32_t> readers;
+  };
+  std::vector<Obj> objs;
+  int next_slot = 0;
+  struct Chunk {
+    int64_t off;
+    int cls;
+    int obj;
+  };
+  std::vector<Chunk> chunks;
+  std::vector<std::deque<int>> freelist = std::vector<std::deque<int>>(64);
+  int64_t ws_top = 0;
+  std::vector<int32_t> depbuf;
+
+  int new_obj() {
+    objs.emplace_back();
+    return (int)objs.size() - 1;
+  }
+  int new_slot() { return next_slot++; }
+
+  static int cls_of(int64_t dbl) {
+    int c = 8;
+    while (((int64_t)1 << c) < dbl) ++c;
+    return c;
+  }
+  // Keep this many chunks of a class in flight before reusing one, so that
+  // independent tasks rarely wait on each other through scratch reuse.
+  static size_t keep(int c) {
+    int64_t k = ((int64_t)1 << 25) >> c;
+    return (size_t)std::max<int64_t>(4, std::min<int64_t>(512, k));
+  }
+  int alloc(int64_t dbl) {
+    int c = cls_of(std::max<int64_t>(dbl, 1));
+    auto& fl = freelist[(size_t)c];
+    if (fl.size() > keep(c)) {
+      int id = fl.front();
+      fl.pop_front();
+      return id;
+    }
+    Chunk ch;
+    ch.off = ws_top;
+    ch.cls = c;
+    ch.obj = new_obj();
+    ws_top += (int64_t)1 << c;
+    chunks.push_back(ch);
+    return (int)chunks.size() - 1;
+  }
+  void release(int id) { freelist[(size_t)chunks[(size_t)id].cls].push_back(id); }
+  int64_t chunk_loc(int id) const { return tag_ws(chunks[(size_t)id].off); }
+  int chunk_obj(int id) const { return chunks[(size_t)id].obj; }
+
+  int32_t emit(const HTask& t, const std::vector<int>& reads, const std::vector<int>& writes) {
+    int32_t id = (int32_t)tasks.size();
+    depbuf.clear();
+    for (int w : writes) {
+      Obj& o = objs[(size_t)w];
+      if (o.writer >= 0) depbuf.push_back(o.writer);
+      depbuf.insert(depbuf.end(), o.readers.begin(), o.readers.end());
+    }
+    for (int r : reads) {
+      Obj& o = objs[(size_t)r];
+      if (o.writer >= 0) depbuf.push_back(o.writer);
+    }
+    std::sort(depbuf.begin(), depbuf.end());
+    depbuf.erase(std::unique(depbuf.begin(), depbuf.end()), depbuf.end());
+    dep_idx.insert(dep_idx.end(), depbuf.begin(), depbuf.end());
+    dep_ptr.push_back((int64_t)dep_idx.size());
+    for (int r : reads) {
+      Obj& o = objs[(size_t)r];
+      if (o.readers.empty() || o.readers.back() != id) o.readers.push_back(id);
+    }
+    for (int w : writes) {
+      Obj& o = objs[(size_t)w];
+      o.writer = id;
+      o.readers.clear();
+    }
+    tasks.push_back(t);
+    return id;
+  }
+};
+
+struct Hold {
+  Sched* S;
+  int chunk;
+  Hold(Sched* s, int c) : S(s), chunk(c) {}
+  ~Hold() { S->release(chunk); }
+};
+typedef std::shared_ptr<Hold> HoldP;
+
+HTask blank(int type) {
+  HTask t;
+  std::memset(&t, 0, sizeof(t));
+  t.type = type;
+  t.rin = t.rout = -1;
+  t.a = t.b = t.c = t.d = t.e = t.f = t.ws = -1;
+  return t;
+}
+
+int64_t rk_ws(int64_t m, int64_t n, int64_t l) { return (2 * m + n) * l + 2 * l * l + 64; }
+
+// ===========================================================================
+// Symbolic arithmetic: the paper's procedures emitting tasks
+// ===========================================================================
+
+// A low-rank matrix under construction: own storage, or a row-restricted view
+// of another one (Section 3, "Splitting": no arithmetic).
+struct SLow {
+  int64_t u = -1, v = -1;
+  int ldu = 0, ldv = 0;
+  int wcode = 0;   // width: fixed (>= 0) or rank slot (< 0)
+  int cap = 0;     // capacity of own storage (columns a result may have)
+  int wmax = 0;    // largest width the current data can have (a view keeps its parent's)
+  int obj = -1;
+  bool own = false;
+  bool zero = true;
+  HoldP hold;
+  int slot = -1;   // rank slot when own
+};
+
+struct SPend {
+  double alpha;
+  const hmat* X;
+  int xb;
+  const hmat* Y;
+  int yb;
+};
+
+// Accumulator (Rhat_{t,r}, P_{t,r}) (Section 4).  Blocks with a leaf cluster
+// on either side keep Rhat in standard representation (exact additions, one
+// truncation when flushed into an admissible leaf); all others factorised.
+struct SAcc {
+  int t = 0, r = 0;
+  bool dense = false;
+  bool dzero = true;
+  int64_t dloc = -1;
+  int dobj = -1;
+  HoldP dhold;
+  SLow R;
+  std::vector<SPend> P;
+};
+
+// Target of a flush: a block of an H-matrix, or a temporary low-rank matrix.
+struct STarget {
+  hmat* M = nullptr;
+  int b = -1;
+  SLow* tmp = nullptr;
+  int t = 0, r = 0;
+};
+
+// Factors Ahat Bhat^T of a product in low-rank form.
+struct SProd {
+  bool zero = false;
+  int wcode = 0, wcap = 0;
+  int64_t a = -1, b = -1;
+  int lda = 0, ldb = 0;
+  bool aid = false, bid = false, btr = false;
+  std::vector<int> objs;
+  std::vector<HoldP> holds;
+};
+
+struct Sym {
+  Sched& S;
+  const hmat_ctree& RT;
+  const hmat_ctree& CT;
+  int64_t maxrank;
+  std::vector<const hmat*> mats;
+  std::vector<int> objbase;
+
+  Sym(Sched& s, const hmat_ctree& rt, const hmat_ctree& ct, int64_t mr) : S(s), RT(rt), CT(ct), maxrank(mr) {}
+
+  void add_matrix(const hmat* M) {
+    mats.push_back(M);
+    objbase.push_back((int)S.objs.size());
+    for (size_t b = 0; b < M->bt->nodes.size(); ++b) S.new_obj();
+  }
+  int obj_of(const hmat* M, int b) const {
+    for (size_t i = 0; i < mats.size(); ++i)
+      if (mats[i] == M) return objbase[i] + b;
+    throw HmError(HMAT_ERR_INTERNAL, "unknown matrix");
+  }
+  const CNodeH& rc(int t) const { return RT.nodes[(size_t)t]; }
+  const CNodeH& cc(int r) const { return CT.nodes[(size_t)r]; }
+  int capof(int64_t m, int64_t n) const { return (int)std::min<int64_t>(std::min(m, n), maxrank); }
+
+  // ---- leaves of a subtree --------------------------------------------------
+  void collect(const hmat* M, int b, int64_t r0, int64_t c0, bool nonzero_only, std::vector<LeafRef>& out,
+               std::vector<int>& objs) {
+    const BNodeH& nd = M->bt->nodes[(size_t)b];
+    if (nd.kind == 0) {
+      for (int k = 0; k < nd.nsons; ++k)
+        collect(M, M->bt->sons[(size_t)(nd.son0 + k)], r0, c0, nonzero_only, out, objs);
+      return;
+    }
+    if (nonzero_only && M->zero[(size_t)b]) return;
+    LeafRef L;
+    std::memset(&L, 0, sizeof(L));
+    L.kind = nd.kind;
+    L.rows = (int)M->rows(b);
+    L.cols = (int)M->cols(b);
+    L.roff = (int)(M->tc(b).off - r0);
+    L.coff = (int)(M->sc(b).off - c0);
+    L.lda = (int)M->rows(b);
+    L.ldb = (int)M->cols(b);
+    L.a = M->loc[(size_t)b];
+    L.b = nd.kind == 2 ? M->vloc[(size_t)b] : -1;
+    L.rank_slot = nd.kind == 2 ? M->slot[(size_t)b] : -1;
+    out.push_back(L);
+    objs.push_back(obj_of(M, b));
+  }
+
+  // out (ldout) += alpha op(M|b) in (ldin), width wcode.  Returns false when
+  // nothing was emitted (subtree statically zero and no zeroing requested).
+  bool hmv(const hmat* M, int b, bool trans, double alpha, int64_t in, int ldin, int inobj, int64_t out, int ldout,
+           int outobj, int wcode, bool zero_out, int out_rows) {
+    std::vector<LeafRef> L;
+    std::vector<int> reads;
+    collect(M, b, M->tc(b).off, M->sc(b).off, true, L, reads);
+    if (L.empty() && !zero_out) return false;
+    HTask t = blank(T_HMV);
+    t.flags = (trans ? F_TRANS : 0) | (zero_out ? F_ZERO_OUT : 0);
+    t.m = out_rows;
+    t.alpha = alpha;
+    t.b = in;
+    t.ldb = ldin;
+    t.c = out;
+    t.ldc = ldout;
+    t.wa = wcode;
+    t.list_begin = (int)S.leaves.size();
+    t.list_len = (int)L.size();
+    S.leaves.insert(S.leaves.end(), L.begin(), L.end());
+    if (inobj >= 0) reads.push_back(inobj);
+    S.emit(t, reads, {outobj});
+    return true;
+  }
+
+  bool subtree_zero(const hmat* M, int b) {
+    const BNodeH& nd = M->bt->nodes[(size_t)b];
+    if (nd.kind != 0) return M->zero[(size_t)b];
+    for (int k = 0; k < nd.nsons; ++k)
+      if (!subtree_zero(M, M->bt->sons[(size_t)(nd.son0 + k)])) return false;
+    return true;
+  }
+
+  // ---- H-matrix solves with a thin right-hand side (rows of d's cluster) -----
+  // kind: TRSM_L (L^{-1}), TRSM_U (U^{-1}), TRSM_UT (U^{-T}), TRSM_LT (L^{-T})
+  void hsolve(const hmat* M, int d, int kind, int64_t x, int ldx, int xobj, int wcode) {
+    const BNodeH& nd = M->bt->nodes[(size_t)d];
+    if (nd.kind == 1) {
+      HTask t = blank(T_TRSM);
+      t.p = kind;
+      t.m = (int)M->rows(d);
+      t.a = M->loc[(size_t)d];
+      t.lda = (int)M->rows(d);
+      t.b = x;
+      t.ldb = ldx;
+      t.wa = wcode;
+      S.emit(t, {obj_of(M, d)}, {xobj});
+      return;
+    }
+    if (nd.kind != 0) throw HmError(HMAT_ERR_ARG, "H-solve: admissible diagonal block");
+    const CNodeH& t = rc(nd.t);
+    int p = t.nsons;
+    auto xoff = [&](int i) { return x + (rc(t.son[i]).off - t.off); };
+    auto rows = [&](int i) { return (int)rc(t.son[i]).size; };
+    if (kind == TRSM_L || kind == TRSM_UT) {
+      for (int i = 0; i < p; ++i) {
+        hsolve(M, M->bt->child(d, i, i), kind, xoff(i), ldx, xobj, wcode);
+        for (int j = i + 1; j < p; ++j) {
+          if (kind == TRSM_L)
+            hmv(M, M->bt->child(d, j, i), false, -1.0, xoff(i), ldx, xobj, xoff(j), ldx, xobj, wcode, false, rows(j));
+          else
+            hmv(M, M->bt->child(d, i, j), true, -1.0, xoff(i), ldx, xobj, xoff(j), ldx, xobj, wcode, false, rows(j));
+        }
+      }
+    } else {
+      for (int i = p - 1; i >= 0; --i) {
+        hsolve(M, M->bt->child(d, i, i), kind, xoff(i), ldx, xobj, wcode);
+        for (int j = 0; j < i; ++j) {
+          if (kind == TRSM_U)
+            hmv(M, M->bt->child(d, j, i), false, -1.0, xoff(i), ldx, xobj, xoff(j), ldx, xobj, wcode, false, rows(j));
+          else
+            hmv(M, M->bt->child(d, i, j), true, -1.0, xoff(i), ldx, xobj, xoff(j), ldx, xobj, wcode, false, rows(j));
+        }
+      }
+    }
+  }
+
+  // ---- products (Fig. addproduct, four leaf cases) -----------------------------
+  int scratch(int64_t dbl, SProd& P) {
+    int c = S.alloc(dbl);
+    P.holds.push_back(std::make_shared<Hold>(&S, c));
+    P.objs.push_back(S.chunk_obj(c));
+    return c;
+  }
+
+  SProd leaf_product(const hmat* X, int xb, const hmat* Y, int yb) {
+    SProd P;
+    const CNodeH& t = X->tc(xb);
+    const CNodeH& s = X->sc(xb);
+    const CNodeH& r = Y->sc(yb);
+    int nt = (int)t.size, ns = (int)s.size, nr = (int)r.size;
+    int kx = X->kind(xb), ky = Y->kind(yb);
+    if (kx == 1) {
+      if (X->zero[(size_t)xb] || subtree_zero(Y, yb)) {
+        P.zero = true;
+        return P;
+      }
+      int xobj = obj_of(X, xb);
+      if (nt <= ns) {
+        // Ahat = I, Bhat = Y^T N_X^T (r x t)
+        int cT = scratch((int64_t)ns * nt, P);
+        HTask tc = blank(T_COPY);
+        tc.flags = F_TRANS;
+        tc.m = ns;
+        tc.n = nt;
+        tc.a = X->loc[(size_t)xb];
+        tc.lda = nt;
+        tc.c = S.chunk_loc(cT);
+        tc.ldc = ns;
+        S.emit(tc, {xobj}, {S.chunk_obj(cT)});
+        int cB = scratch((int64_t)nr * nt, P);
+        hmv(Y, yb, true, 1.0, S.chunk_loc(cT), ns, S.chunk_obj(cT), S.chunk_loc(cB), nr, S.chunk_obj(cB), nt, true,
+            nr);
+        P.aid = true;
+        P.b = S.chunk_loc(cB);
+        P.ldb = nr;
+        P.wcode = P.wcap = nt;
+      } else {
+        // Ahat = N_X (t x s), Bhat = Y^T (r x s)
+        int cB = scratch((int64_t)nr * ns, P);
+        densify(Y, yb, true, S.chunk_loc(cB), nr, S.chunk_obj(cB));
+        P.a = X->loc[(size_t)xb];
+        P.lda = nt;
+        P.objs.push_back(xobj);
+        P.b = S.chunk_loc(cB);
+        P.ldb = nr;
+        P.wcode = P.wcap = ns;
+      }
+    } else if (ky == 1) {
+      if (Y->zero[(size_t)yb] || subtree_zero(X, xb)) {
+        P.zero = true;
+        return P;
+      }
+      int yobj = obj_of(Y, yb);
+      if (nr <= ns) {
+        // Bhat = I, Ahat = X N_Y (t x r)
+        int cA = scratch((int64_t)nt * nr, P);
+        hmv(X, xb, false, 1.0, Y->loc[(size_t)yb], ns, yobj, S.chunk_loc(cA), nt, S.chunk_obj(cA), nr, true, nt);
+        P.bid = true;
+        P.a = S.chunk_loc(cA);
+        P.lda = nt;
+        P.wcode = P.wcap = nr;
+      } else {
+        // Bhat = N_Y^T (given transposed), Ahat = X densified (t x s)
+        int cA = scratch((int64_t)nt * ns, P);
+        densify(X, xb, false, S.chunk_loc(cA), nt, S.chunk_obj(cA));
+        P.a = S.chunk_loc(cA);
+        P.lda = nt;
+        P.b = Y->loc[(size_t)yb];
+        P.ldb = ns;
+        P.btr = true;
+        P.objs.push_back(yobj);
+        P.wcode = P.wcap = ns;
+      }
+    } else if (kx == 2) {
+      if (X->zero[(size_t)xb] || subtree_zero(Y, yb)) {
+        P.zero = true;
+        return P;
+      }
+      int xobj = obj_of(X, xb);
+      int cx = X->cap[(size_t)xb];
+      int wc = width_from_slot(X->slot[(size_t)xb]);
+      int cB = scratch((int64_t)nr * cx, P);
+      hmv(Y, yb, true, 1.0, X->vloc[(size_t)xb], ns, xobj, S.chunk_loc(cB), nr, S.chunk_obj(cB), wc, true, nr);
+      P.a = X->loc[(size_t)xb];
+      P.lda = nt;
+      P.objs.push_back(xobj);
+      P.b = S.chunk_loc(cB);
+      P.ldb = nr;
+      P.wcode = wc;
+      P.wcap = cx;
+    } else {
+      if (Y->zero[(size_t)yb] || subtree_zero(X, xb)) {
+        P.zero = true;
+        return P;
+      }
+      int yobj = obj_of(Y, yb);
+      int cy = Y->cap[(size_t)yb];
+      int wc = width_from_slot(Y->slot[(size_t)yb]);
+      int cA = scratch((int64_t)nt * cy, P);
+      hmv(X, xb, false, 1.0, Y->loc[(size_t)yb], ns, yobj, S.chunk_loc(cA), nt, S.chunk_obj(cA), wc, true, nt);
+      P.b = Y->vloc[(size_t)yb];
+      P.ldb = nr;
+      P.objs.push_back(yobj);
+      P.a = S.chunk_loc(cA);
+      P.lda = nt;
+      P.wcode = wc;
+      P.wcap = cy;
+    }
+    return P;
+  }
+
+  void densify(const hmat* M, int b, bool trans, int64_t out, int ldout, int outobj) {
+    std::vector<LeafRef> L;
+    std::vector<int> reads;
+    collect(M, b, M->tc(b).off, M->sc(b).off, false, L, reads);
+    HTask t = blank(T_DENSIFY);
+    t.flags = trans ? F_TRANS : 0;
+    t.c = out;
+    t.ldc = ldout;
+    t.list_begin = (int)S.leaves.size();
+    t.list_len = (int)L.size();
+    S.leaves.insert(S.leaves.end(), L.begin(), L.end());
+    S.emit(t, reads, {outobj});
+  }
+
+  // ---- accumulators -------------------------------------------------------------
+  SAcc acc_new(int t, int r) {
+    SAcc a;
+    a.t = t;
+    a.r = r;
+    a.dense = rc(t).nsons == 0 || cc(r).nsons == 0;
+    a.R.cap = capof(rc(t).size, cc(r).size);
+    return a;
+  }
+
+  void dense_ensure(SAcc& a) {
+    if (a.dloc >= 0) return;
+    int64_t m = rc(a.t).size, n = cc(a.r).size;
+    int c = S.alloc(m * n);
+    a.dhold = std::make_shared<Hold>(&S, c);
+    a.dloc = S.chunk_loc(c);
+    a.dobj = S.chunk_obj(c);
+    HTask z = blank(T_ZERO);
+    z.m = (int)m;
+    z.n = (int)n;
+    z.c = a.dloc;
+    z.ldc = (int)m;
+    S.emit(z, {}, {a.dobj});
+    a.dzero = true;
+  }
+
+  // give a low-rank matrix its own storage (m x cap, n x cap) and rank slot
+  void own_storage(SLow& L, int64_t m, int64_t n) {
+    if (L.own) return;
+    int c = S.alloc((m + n) * L.cap);
+    L.hold = std::make_shared<Hold>(&S, c);
+    L.u = S.chunk_loc(c);
+    L.v = L.u + m * L.cap;
+    L.ldu = (int)m;
+    L.ldv = (int)n;
+    L.obj = S.chunk_obj(c);
+    L.own = true;
+    L.slot = S.new_slot();
+    L.wmax = L.cap;
+  }
+
+  // low-rank target <- trunc(target + alpha P) by one T_RKADD, in place.
+  void rkadd_into(double alpha, const SProd& P, SLow& Z, int64_t m, int64_t n) {
+    int rin = Z.zero ? -1 : (Z.wcode < 0 ? -(Z.wcode + 1) : -2);
+    if (rin == -2) throw HmError(HMAT_ERR_INTERNAL, "rkadd: fixed-width target");
+    int64_t cu = Z.u, cv = Z.v;
+    int ldcu = Z.ldu, ldcv = Z.ldv, inobj = Z.obj;
+    own_storage(Z, m, n);
+    HTask t = blank(T_RKADD);
+    t.flags = (P.aid ? F_A_IDENT : 0) | (P.bid ? F_B_IDENT : 0) | (P.btr ? F_B_TRANS : 0) | F_CHECK_ZERO;
+    t.m = (int)m;
+    t.n = (int)n;
+    t.alpha = alpha;
+    t.a = P.a;
+    t.lda = P.lda;
+    t.b = P.b;
+    t.ldb = P.ldb;
+    t.wa = P.wcode;
+    t.c = rin >= 0 ? cu : -1;
+    t.d = rin >= 0 ? cv : -1;
+    t.ldc = ldcu;
+    t.ldd = ldcv;
+    t.rin = rin;
+    t.e = Z.u;
+    t.f = Z.v;
+    t.lde = Z.ldu;
+    t.ldf = Z.ldv;
+    t.rout = Z.slot;
+    t.cap = Z.cap;
+    int64_t l = (int64_t)P.wcap + (rin >= 0 ? Z.wmax : 0);
+    if (l > HM_LMAX_HOST) throw HmError(HMAT_ERR_RANK, "stacked width exceeds the truncation limit");
+    int inmax = Z.wmax;
+    int ws = S.alloc(rk_ws(m, n, l));
+    t.ws = S.chunk_loc(ws);
+    std::vector<int> reads = P.objs;
+    if (rin >= 0 && inobj >= 0 && inobj != Z.obj) reads.push_back(inobj);
+    S.emit(t, reads, {Z.obj, S.chunk_obj(ws)});
+    S.release(ws);
+    Z.wcode = width_from_slot(Z.slot);
+    Z.zero = false;
+    Z.wmax = Z.cap;
+    (void)inmax;
+  }
+
+  void add_product(double alpha, SProd& P, SAcc& a) {
+    int64_t m = rc(a.t).size, n = cc(a.r).size;
+    if (a.dense) {
+      dense_ensure(a);
+      HTask t = blank(P.aid || P.bid ? T_ADD : T_GEMM);
+      t.m = (int)m;
+      t.n = (int)n;
+      t.alpha = alpha;
+      t.c = a.dloc;
+      t.ldc = (int)m;
+      if (P.aid) {
+        t.flags = F_TRANS;  // D += alpha Bhat^T
+        t.a = P.b;
+        t.lda = P.ldb;
+      } else if (P.bid) {
+        t.a = P.a;
+        t.lda = P.lda;
+      } else {
+        t.a = P.a;
+        t.lda = P.lda;
+        t.b = P.b;
+        t.ldb = P.ldb;
+        t.wa = P.wcode;
+        t.flags = P.btr ? F_B_TRANS : 0;
+      }
+      std::vector<int> reads = P.objs;
+      S.emit(t, reads, {a.dobj});
+      a.dzero = false;
+    } else {
+      rkadd_into(alpha, P, a.R, m, n);
+    }
+  }
+
+  // Fig. addproduct
+  void addproduct(double alpha, const hmat* X, int xb, const hmat* Y, int yb, SAcc& a) {
+    if (X->kind(xb) != 0 || Y->kind(yb) != 0) {
+      SProd P = leaf_product(X, xb, Y, yb);
+      if (P.zero) return;
+      add_product(alpha, P, a);
+    } else {
+      a.P.push_back(SPend{alpha, X, xb, Y, yb});
+    }
+  }
+
+  // Fig. split
+  std::vector<std::vector<SAcc>> split(SAcc& a) {
+    if (a.dense) throw HmError(HMAT_ERR_INTERNAL, "split: accumulator in standard representation");
+    const CNodeH& t = rc(a.t);
+    const CNodeH& r = cc(a.r);
+    std::vector<std::vector<SAcc>> sons((size_t)t.nsons);
+    for (int i = 0; i < t.nsons; ++i)
+      for (int j = 0; j < r.nsons; ++j) {
+        SAcc s = acc_new(t.son[i], r.son[j]);
+        int64_t ro = rc(s.t).off - t.off, co = cc(s.r).off - r.off;
+        int64_t sm = rc(s.t).size, sn = cc(s.r).size;
+        if (!a.R.zero) {
+          if (s.dense) {
+            dense_ensure(s);
+            HTask g = blank(T_GEMM);
+            g.flags = F_ZERO_OUT;
+            g.m = (int)sm;
+            g.n = (int)sn;
+            g.alpha = 1.0;
+            g.a = a.R.u + ro;
+            g.lda = a.R.ldu;
+            g.b = a.R.v + co;
+            g.ldb = a.R.ldv;
+            g.wa = a.R.wcode;
+            g.c = s.dloc;
+            g.ldc = (int)sm;
+            S.emit(g, {a.R.obj}, {s.dobj});
+            s.dzero = false;
+          } else {
+            s.R = a.R;  // view
+            s.R.own = false;
+            s.R.u = a.R.u + ro;
+            s.R.v = a.R.v + co;
+            s.R.cap = capof(sm, sn);
+          }
+        }
+        for (const SPend& p : a.P) {
+          int ns = p.X->sc(p.xb).nsons;
+          for (int k = 0; k < ns; ++k)
+            addproduct(p.alpha, p.X, p.X->bt->child(p.xb, i, k), p.Y, p.Y->bt->child(p.yb, k, j), s);
+        }
+        sons[(size_t)i].push_back(std::move(s));
+      }
+    return sons;
+  }
+
+  // rkupdate of a factorised Rhat (Fig. rkupdate)
+  void rkupdate(const SLow& R, int t, int r, STarget z) {
+    if (R.zero) return;
+    int64_t m = rc(t).size, n = cc(r).size;
+    if (z.tmp) {
+      SProd P;
+      P.a = R.u;
+      P.lda = R.ldu;
+      P.b = R.v;
+      P.ldb = R.ldv;
+      P.wcode = R.wcode;
+      P.wcap = R.wmax;
+      P.objs.push_back(R.obj);
+      rkadd_into(1.0, P, *z.tmp, m, n);
+      return;
+    }
+    hmat* M = z.M;
+    int kind = M->kind(z.b);
+    if (kind == 1) {
+      HTask g = blank(T_GEMM);
+      g.m = (int)m;
+      g.n = (int)n;
+      g.alpha = 1.0;
+      g.a = R.u;
+      g.lda = R.ldu;
+      g.b = R.v;
+      g.ldb = R.ldv;
+      g.wa = R.wcode;
+      g.c = M->loc[(size_t)z.b];
+      g.ldc = (int)m;
+      int o = obj_of(M, z.b);
+      S.emit(g, {R.obj}, {o});
+      M->zero[(size_t)z.b] = 0;
+    } else if (kind == 2) {
+      SLow L = leaf_low(M, z.b);
+      SProd P;
+      P.a = R.u;
+      P.lda = R.ldu;
+      P.b = R.v;
+      P.ldb = R.ldv;
+      P.wcode = R.wcode;
+      P.wcap = R.wmax;
+      P.objs.push_back(R.obj);
+      rkadd_into(1.0, P, L, m, n);
+      M->zero[(size_t)z.b] = 0;
+    } else {
+      const BNodeH& nd = M->bt->nodes[(size_t)z.b];
+      const CNodeH& tt = rc(t);
+      const CNodeH& rr = cc(r);
+      for (int i = 0; i < tt.nsons; ++i)
+        for (int j = 0; j < rr.nsons; ++j) {
+          SLow V = R;
+          V.u = R.u + (rc(tt.son[i]).off - tt.off);
+          V.v = R.v + (cc(rr.son[j]).off - rr.off);
+          STarget c;
+          c.M = M;
+          c.b = M->bt->child(z.b, i, j);
+          c.t = tt.son[i];
+          c.r = rr.son[j];
+          (void)nd;
+          rkupdate(V, c.t, c.r, c);
+        }
+    }
+  }
+
+  // low-rank leaf of an H-matrix as an SLow with its own storage and slot
+  SLow leaf_low(hmat* M, int b) {
+    SLow L;
+    L.u = M->loc[(size_t)b];
+    L.v = M->vloc[(size_t)b];
+    L.ldu = (int)M->rows(b);
+    L.ldv = (int)M->cols(b);
+    L.cap = M->cap[(size_t)b];
+    L.slot = M->slot[(size_t)b];
+    L.wcode = width_from_slot(L.slot);
+    L.obj = obj_of(M, b);
+    L.own = true;
+    L.zero = M->zero[(size_t)b];
+    L.wmax = L.cap;
+    return L;
+  }
+
+  // Fig. flush
+  void flush(SAcc& a, STarget z) {
+    int64_t m = rc(a.t).size, n = cc(a.r).size;
+    if (a.dense) {
+      if (!a.P.empty()) throw HmError(HMAT_ERR_INTERNAL, "flush: pending products on a leaf-cluster block");
+      if (a.dloc < 0 || a.dzero) return;
+      bool zdense = !z.tmp && z.M->kind(z.b) == 1;
+      if (zdense) {
+        HTask t = blank(T_ADD);
+        t.m = (int)m;
+        t.n = (int)n;
+        t.alpha = 1.0;
+        t.a = a.dloc;
+        t.lda = (int)m;
+        t.c = z.M->loc[(size_t)z.b];
+        t.ldc = (int)m;
+        int o = obj_of(z.M, z.b);
+        S.emit(t, {a.dobj}, {o});
+        z.M->zero[(size_t)z.b] = 0;
+      } else {
+        if (!z.tmp && z.M->kind(z.b) != 2) throw HmError(HMAT_ERR_INTERNAL, "flush: dense accumulator, subdivided target");
+        SProd P;
+        P.objs.push_back(a.dobj);
+        if (m <= n) {
+          P.aid = true;
+          P.b = a.dloc;
+          P.ldb = (int)m;
+          P.btr = true;
+          P.wcode = P.wcap = (int)m;
+        } else {
+          P.bid = true;
+          P.a = a.dloc;
+          P.lda = (int)m;
+          P.wcode = P.wcap = (int)n;
+        }
+        if (z.tmp) {
+          rkadd_into(1.0, P, *z.tmp, m, n);
+        } else {
+          SLow L = leaf_low(z.M, z.b);
+          rkadd_into(1.0, P, L, m, n);
+          z.M->zero[(size_t)z.b] = 0;
+        }
+      }
+      a.dhold.reset();
+      a.dloc = -1;
+      a.dzero = true;
+      return;
+    }
+    if (a.P.empty()) {
+      rkupdate(a.R, a.t, a.r, z);
+    } else if (!z.tmp && z.M->kind(z.b) == 0) {
+      auto sons = split(a);
+      for (size_t i = 0; i < sons.size(); ++i)
+        for (size_t j = 0; j < sons[i].size(); ++j) {
+          STarget c;
+          c.M = z.M;
+          c.b = z.M->bt->child(z.b, (int)i, (int)j);
+          c.t = sons[i][j].t;
+          c.r = sons[i][j].r;
+          flush(sons[i][j], c);
+        }
+    } else {
+      // (t, r) is a leaf of Z with pending products: temporaries + rkmerge
+      if (!z.tmp && z.M->kind(z.b) != 2) throw HmError(HMAT_ERR_INTERNAL, "flush: pending products on a dense leaf");
+      SLow base = z.tmp ? *z.tmp : leaf_low(z.M, z.b);
+      const CNodeH& tt = rc(a.t);
+      const CNodeH& rr = cc(a.r);
+      if (tt.nsons != 2 || rr.nsons != 2) throw HmError(HMAT_ERR_ARG, "rkmerge needs binary cluster trees");
+      SLow tmp[2][2];
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+          SLow& T = tmp[i][j];
+          T = base;
+          T.own = false;
+          T.u = base.u + (rc(tt.son[i]).off - tt.off);
+          T.v = base.v + (cc(rr.son[j]).off - rr.off);
+          T.cap = capof(rc(tt.son[i]).size, cc(rr.son[j]).size);
+          T.hold = base.hold;
+        }
+      auto sons = split(a);
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+          STarget c;
+          c.tmp = &tmp[i][j];
+          c.t = tt.son[i];
+          c.r = rr.son[j];
+          flush(sons[(size_t)i][(size_t)j], c);
+        }
+      // Fig. rkmerge: merge the block columns (rowmerge of adjoints), then the row
+      SLow col[2];
+      for (int j = 0; j < 2; ++j) {
+        int64_t nrj = cc(rr.son[j]).size;
+        SLow& C = col[j];
+        C.cap = capof(nrj, m);
+        own_storage(C, nrj, m);  // "A" role: r_j x cap, "B" role: t x cap
+        HTask t = blank(T_ROWMERGE);
+        t.m = (int)nrj;
+        t.p = (int)rc(tt.son[0]).size;
+        t.q = (int)rc(tt.son[1]).size;
+        t.a = tmp[0][j].v;
+        t.lda = tmp[0][j].ldv;
+        t.b = tmp[0][j].u;
+        t.ldb = tmp[0][j].ldu;
+        t.wa = tmp[0][j].zero ? 0 : tmp[0][j].wcode;
+        t.c = tmp[1][j].v;
+        t.ldc = tmp[1][j].ldv;
+        t.d = tmp[1][j].u;
+        t.ldd = tmp[1][j].ldu;
+        t.wb = tmp[1][j].zero ? 0 : tmp[1][j].wcode;
+        t.e = C.u;
+        t.lde = C.ldu;
+        t.f = C.v;
+        t.ldf = C.ldv;
+        t.rout = C.slot;
+        t.cap = C.cap;
+        int64_t l = (tmp[0][j].zero ? 0 : tmp[0][j].wmax) + (tmp[1][j].zero ? 0 : tmp[1][j].wmax);
+        if (l > HM_LMAX_HOST) throw HmError(HMAT_ERR_RANK, "merged width exceeds the truncation limit");
+        int ws = S.alloc(rk_ws(nrj, m, l) + (int64_t)nrj * l);
+        t.ws = S.chunk_loc(ws);
+        std::vector<int> reads;
+        for (int i = 0; i < 2; ++i)
+          if (tmp[i][j].obj >= 0) reads.push_back(tmp[i][j].obj);
+        S.emit(t, reads, {C.obj, S.chunk_obj(ws)});
+        S.release(ws);
+        C.wcode = width_from_slot(C.slot);
+        C.zero = false;
+      }
+      SLow out = base;
+      if (z.tmp) {
+        own_storage(*z.tmp, m, n);
+        out = *z.tmp;
+      }
+      HTask t = blank(T_ROWMERGE);
+      t.m = (int)m;
+      t.p = (int)cc(rr.son[0]).size;
+      t.q = (int)cc(rr.son[1]).size;
+      t.a = col[0].v;  // column j = Bc_j Ac_j^T: "A" role Bc_j (t x k), "B" role Ac_j (r_j x k)
+      t.lda = col[0].ldv;
+      t.b = col[0].u;
+      t.ldb = col[0].ldu;
+      t.wa = col[0].wcode;
+      t.c = col[1].v;
+      t.ldc = col[1].ldv;
+      t.d = col[1].u;
+      t.ldd = col[1].ldu;
+      t.wb = col[1].wcode;
+      t.e = out.u;
+      t.lde = out.ldu;
+      t.f = out.v;
+      t.ldf = out.ldv;
+      t.rout = out.slot;
+      t.cap = out.cap;
+      int64_t l = (int64_t)col[0].cap + col[1].cap;
+      if (l > HM_LMAX_HOST) throw HmError(HMAT_ERR_RANK, "merged width exceeds the truncation limit");
+      int ws = S.alloc(rk_ws(m, n, l) + (int64_t)m * l);
+      t.ws = S.chunk_loc(ws);
+      S.emit(t, {col[0].obj, col[1].obj}, {out.obj, S.chunk_obj(ws)});
+      S.release(ws);
+      if (z.tmp) {
+        z.tmp->wcode = width_from_slot(z.tmp->slot);
+        z.tmp->zero = false;
+      } else {
+        z.M->zero[(size_t)z.b] = 0;
+      }
+    }
+    a.P.clear();
+    a.R = SLow();
+  }
+
+  // ---- H-LU with accumulators --------------------------------------------------
+  void trsm_L(hmat* G, int d, int b) {
+    int kind = G->kind(b);
+    if (kind == 1) {
+      if (!G->zero[(size_t)b])
+        hsolve(G, d, TRSM_L, G->loc[(size_t)b], (int)G->rows(b), obj_of(G, b), (int)G->cols(b));
+    } else if (kind == 2) {
+      if (!G->zero[(size_t)b])
+        hsolve(G, d, TRSM_L, G->loc[(size_t)b], (int)G->rows(b), obj_of(G, b), width_from_slot(G->slot[(size_t)b]));
+    } else {
+      const CNodeH& t = G->tc(b);
+      const CNodeH& r = G->sc(b);
+      for (int j = 0; j < r.nsons; ++j) {
+        std::vector<SAcc> acc;
+        for (int i = 0; i < t.nsons; ++i) acc.push_back(acc_new(t.son[i], r.son[j]));
+        for (int i = 0; i < t.nsons; ++i) {
+          int bi = G->bt->child(b, i, j);
+          STarget z;
+          z.M = G;
+          z.b = bi;
+          z.t = t.son[i];
+          z.r = r.son[j];
+          flush(acc[(size_t)i], z);
+          trsm_L(G, G->bt->child(d, i, i), bi);
+          for (int l = i + 1; l < t.nsons; ++l) addproduct(-1.0, G, G->bt->child(d, l, i), G, bi, acc[(size_t)l]);
+        }
+      }
+    }
+  }
+
+  void trsm_U(hmat* G, int d, int b) {
+    int kind = G->kind(b);
+    if (kind == 1) {
+      if (G->zero[(size_t)b]) return;
+      // X U = N  <=>  U^T X^T = N^T: solve on a transposed copy
+      int m = (int)G->rows(b), n = (int)G->cols(b);
+      int c = S.alloc((int64_t)m * n);
+      int cobj = S.chunk_obj(c);
+      int bobj = obj_of(G, b);
+      HTask t1 = blank(T_COPY);
+      t1.flags = F_TRANS;
+      t1.m = n;
+      t1.n = m;
+      t1.a = G->loc[(size_t)b];
+      t1.lda = m;
+      t1.c = S.chunk_loc(c);
+      t1.ldc = n;
+      S.emit(t1, {bobj}, {cobj});
+      hsolve(G, d, TRSM_UT, S.chunk_loc(c), n, cobj, m);
+      HTask t2 = blank(T_COPY);
+      t2.flags = F_TRANS;
+      t2.m = m;
+      t2.n = n;
+      t2.a = S.chunk_loc(c);
+      t2.lda = n;
+      t2.c = G->loc[(size_t)b];
+      t2.ldc = m;
+      S.emit(t2, {cobj}, {bobj});
+      S.release(c);
+    } else if (kind == 2) {
+      if (!G->zero[(size_t)b])
+        hsolve(G, d, TRSM_UT, G->vloc[(size_t)b], (int)G->cols(b), obj_of(G, b),
+               width_from_slot(G->slot[(size_t)b]));
+    } else {
+      const CNodeH& r = G->tc(b);
+      const CNodeH& t = G->sc(b);
+      for (int j = 0; j < r.nsons; ++j) {
+        std::vector<SAcc> acc;
+        for (int i = 0; i < t.nsons; ++i) acc.push_back(acc_new(r.son[j], t.son[i]));
+        for (int i = 0; i < t.nsons; ++i) {
+          int bi = G->bt->child(b, j, i);
+          STarget z;
+          z.M = G;
+          z.b = bi;
+          z.t = r.son[j];
+          z.r = t.son[i];
+          flush(acc[(size_t)i], z);
+          trsm_U(G, G->bt->child(d, i, i), bi);
+          for (int l = i + 1; l < t.nsons; ++l) addproduct(-1.0, G, bi, G, G->bt->child(d, i, l), acc[(size_t)l]);
+        }
+      }
+    }
+  }
+
+  void lu(hmat* G, int b, SAcc& acc) {
+    int kind = G->kind(b);
+    if (kind == 1) {
+      STarget z;
+      z.M = G;
+      z.b = b;
+      z.t = acc.t;
+      z.r = acc.r;
+      flush(acc, z);
+      HTask t = blank(T_LU);
+      t.m = (int)G->rows(b);
+      t.a = G->loc[(size_t)b];
+      t.lda = t.m;
+      int o = obj_of(G, b);
+      S.emit(t, {}, {o});
+      return;
+    }
+    if (kind != 0) throw HmError(HMAT_ERR_ARG, "H-LU: admissible diagonal block");
+    auto sub = split(acc);
+    acc.P.clear();
+    acc.R = SLow();
+    int p = G->tc(b).nsons;
+    for (int i = 0; i < p; ++i) {
+      int di = G->bt->child(b, i, i);
+      lu(G, di, sub[(size_t)i][(size_t)i]);
+      for (int j = i + 1; j < p; ++j) {
+        int bij = G->bt->child(b, i, j);
+        STarget z;
+        z.M = G;
+        z.b = bij;
+        z.t = sub[(size_t)i][(size_t)j].t;
+        z.r = sub[(size_t)i][(size_t)j].r;
+        flush(sub[(size_t)i][(size_t)j], z);
+        trsm_L(G, di, bij);
+      }
+      for (int j = i + 1; j < p; ++j) {
+        int bji = G->bt->child(b, j, i);
+        STarget z;
+        z.M = G;
+        z.b = bji;
+        z.t = sub[(size_t)j][(size_t)i].t;
+        z.r = sub[(size_t)j][(size_t)i].r;
+        flush(sub[(size_t)j][(size_t)i], z);
+        trsm_U(G, di, bji);
+      }
+      for (int j = i + 1; j < p; ++j)
+        for (int l = i + 1; l < p; ++l)
+          addproduct(-1.0, G, G->bt->child(b, j, i), G, G->bt->child(b, i, l), sub[(size_t)j][(size_t)l]);
+    }
+  }
+};
+
+// ===========================================================================
+// Running a task list
+// ===========================================================================
+struct RunResult {
+  int status = 0;
+  double ms = 0.0;
+  unsigned long long truncations = 0;
+};
+
+RunResult run_tasks(hmat_ctx* ctx, const Sched& S, double* hbase, int* ranks, double eps, int64_t spin_limit,
+                    double* ext0, double* ext1) {
+  RunResult rr;
+  if (S.tasks.empty()) return rr;
+  cudaStream_t st = ctx->stream;
+  DevBuf dtasks, dptr, didx, dleaves, ddone, dws, dmisc;
+  upload(dtasks, S.tasks, st);
+  upload(dptr, S.dep_ptr, st);
+  upload(didx, S.dep_idx, st);
+  upload(dleaves, S.leaves, st);
+  ddone.alloc(S.tasks.size() * sizeof(int));
+  HM_CUDA(cudaMemsetAsync(ddone.p, 0, S.tasks.size() * sizeof(int), st));
+  dws.alloc((size_t)std::max<int64_t>(S.ws_top, 1) * sizeof(double));
+  dmisc.alloc(64);
+  HM_CUDA(cudaMemsetAsync(dmisc.p, 0, 64, st));
+  ExecEnv e;
+  e.hbase = hbase;
+  e.wsbase = dws.as<double>();
+  e.ext0 = ext0;
+  e.ext1 = ext1;
+  e.ranks = ranks;
+  e.tasks = dtasks.as<HTask>();
+  e.ntasks = (long long)S.tasks.size();
+  e.dep_ptr = dptr.as<int64_t>();
+  e.dep_idx = didx.as<int32_t>();
+  e.leaves = dleaves.as<LeafRef>();
+  e.done = ddone.as<int>();
+  e.head = (unsigned long long*)dmisc.p;
+  e.counters = (unsigned long long*)dmisc.p + 1;
+  e.status = (int*)((unsigned long long*)dmisc.p + 2);
+  e.eps = eps;
+  e.spin_iters = spin_limit > 0 ? spin_limit : (1ll << 28);
+  e.spin_ns = 20ull * 1000000000ull;
+  int grid = ctx->num_sms * ctx->blocks_per_sm;
+  cudaEvent_t e0, e1;
+  HM_CUDA(cudaEventCreate(&e0));
+  HM_CUDA(cudaEventCreate(&e1));
+  HM_CUDA(cudaEventRecord(e0, st));
+  HM_CUDA(launch_exec(e, grid, st));
+  HM_CUDA(cudaEventRecord(e1, st));
+  unsigned long long misc[3];
+  HM_CUDA(cudaMemcpyAsync(misc, dmisc.p, sizeof(misc), cudaMemcpyDeviceToHost, st));
+  HM_CUDA(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  HM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  rr.ms = ms;
+  rr.truncations = misc[1];
+  rr.status = (int)(misc[2] & 0xffffffffu);
+  return rr;
+}
+
+hmat_ctx* check_ctx(hmat_ctx* ctx) {
+  require(ctx != nullptr, "null context");
+  HM_CUDA(cudaSetDevice(ctx->device));
+  return ctx;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+size_t hmat_last_error(char* buf, size_t size) {
+  if (buf && size) {
+    size_t n = std::min(size - 1, g_last_error.size());
+    std::memcpy(buf, g_last_error.data(), n);
+    buf[n] = 0;
+  }
+  return g_last_error.size();
+}
+
+hmat_status hmat_ctx_create(int device, void* cuda_stream, hmat_ctx** out) {
+  return guarded([&] {
+    require(out != nullptr, "null output");
+    int ndev = 0;
+    HM_CUDA(cudaGetDeviceCount(&ndev));
+    require(device >= 0 && device < ndev, "no such CUDA device");
+    HM_CUDA(cudaSetDevice(device));
+    auto* c = new hmat_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    HM_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
+    HM_CUDA(exec_occupancy(&c->blocks_per_sm));
+    if (c->blocks_per_sm < 1) c->blocks_per_sm = 1;
+    *out = c;
+  });
+}
+
+hmat_status hmat_ctx_destroy(hmat_ctx* ctx) {
+  return guarded([&] { delete ctx; });
+}
+
+hmat_status hmat_clustertree_build(hmat_ctx* ctx, const double* coords, int64_t n, int d, int64_t leaf_size,
+                                   hmat_ctree** out) {
+  return guarded([&] {
+    (void)ctx;
+    require(coords && out && n > 0 && (d == 2 || d == 3) && leaf_size >= 1, "cluster tree: bad arguments");
+    auto* T = new hmat_ctree();
+    T->d = d;
+    std::vector<int64_t> idx((size_t)n), tmp((size_t)n);
+    for (int64_t i = 0; i < n; ++i) idx[(size_t)i] = i;
+    try {
+      ct_rec(*T, coords, idx, tmp, 0, n, 0, -1, leaf_size);
+    } catch (...) {
+      delete T;
+      throw;
+    }
+    T->perm = std::move(idx);
+    *out = T;
+  });
+}
+
+hmat_status hmat_clustertree_perm(const hmat_ctree* ct, int64_t* perm) {
+  return guarded([&] {
+    require(ct && perm, "null argument");
+    std::memcpy(perm, ct->perm.data(), ct->perm.size() * sizeof(int64_t));
+  });
+}
+
+int64_t hmat_clustertree_size(const hmat_ctree* ct) { return ct ? (int64_t)ct->nodes.size() : 0; }
+
+hmat_status hmat_clustertree_nodes(const hmat_ctree* ct, int64_t* off, int64_t* size, int* level, int* parent,
+                                   int* nsons) {
+  return guarded([&] {
+    require(ct && off && size && level && parent && nsons, "null argument");
+    for (size_t i = 0; i < ct->nodes.size(); ++i) {
+      off[i] = ct->nodes[i].off;
+      size[i] = ct->nodes[i].size;
+      level[i] = ct->nodes[i].level;
+      parent[i] = ct->nodes[i].parent;
+      nsons[i] = ct->nodes[i].nsons;
+    }
+  });
+}
+
+hmat_status hmat_ctree_destroy(hmat_ctree* ct) {
+  return guarded([&] { delete ct; });
+}
+
+hmat_status hmat_blocktree_build(hmat_ctx* ctx, const hmat_ctree* rows, const hmat_ctree* cols, double eta,
+                                 hmat_btree** out) {
+  return guarded([&] {
+    (void)ctx;
+    require(rows && cols && out && rows->d == cols->d && eta > 0, "block tree: bad arguments");
+    auto* B = new hmat_btree();
+    B->R = rows;
+    B->C = cols;
+    bt_rec(*B, 0, 0, 0, -1, eta);
+    *out = B;
+  });
+}
+
+int64_t hmat_blocktree_size(const hmat_btree* bt) { return bt ? (int64_t)bt->nodes.size() : 0; }
+
+hmat_status hmat_blocktree_nodes(const hmat_btree* bt, int* t, int* s, int* level, int* parent, int* kind) {
+  return guarded([&] {
+    require(bt && t && s && level && parent && kind, "null argument");
+    for (size_t i = 0; i < bt->nodes.size(); ++i) {
+      t[i] = bt->nodes[i].t;
+      s[i] = bt->nodes[i].s;
+      level[i] = bt->nodes[i].level;
+      parent[i] = bt->nodes[i].parent;
+      kind[i] = bt->nodes[i].kind;
+    }
+  });
+}
+
+hmat_status hmat_btree_destroy(hmat_btree* bt) {
+  return guarded([&] { delete bt; });
+}
+
+hmat_status hmat_create_from_csr(hmat_ctx* ctx, const hmat_btree* bt, int64_t n, const int64_t* rowptr,
+                                 const int64_t* colidx, const double* val, hmat** out) {
+  return guarded([&] {
+    check_ctx(ctx);
+    require(bt && rowptr && colidx && val && out, "null argument");
+    require((int64_t)bt->R->perm.size() == n && (int64_t)bt->C->perm.size() == n, "csr: size does not match the trees");
+    std::unique_ptr<hmat> H(new hmat());
+    H->ctx = ctx;
+    H->bt = bt;
+    H->n = n;
+    size_t nb = bt->nodes.size();
+    H->loc.assign(nb, -1);
+    H->vloc.assign(nb, -1);
+    H->cap.assign(nb, 0);
+    H->slot.assign(nb, -1);
+    H->zero.assign(nb, 1);
+    int64_t off = 0;
+    std::vector<DenseLeafDesc> dl;
+    for (size_t b = 0; b < nb; ++b) {
+      int kind = bt->nodes[b].kind;
+      int64_t m = H->rows((int)b), k = H->cols((int)b);
+      if (kind == 1) {
+        H->loc[b] = off;
+        DenseLeafDesc d;
+        d.off = off;
+        d.roff = H->tc((int)b).off;
+        d.coff = H->sc((int)b).off;
+        d.rows = (int)m;
+        d.cols = (int)k;
+        dl.push_back(d);
+        off += m * k;
+      } else if (kind == 2) {
+        int c = (int)std::min<int64_t>(std::min(m, k), H->max_rank);
+        H->cap[b] = c;
+        H->loc[b] = off;
+        off += m * c;
+        H->vloc[b] = off;
+        off += k * c;
+        H->slot[b] = H->nslots++;
+      }
+    }
+    H->store_doubles = off;
+    cudaStream_t st = ctx->stream;
+    H->store.alloc((size_t)std::max<int64_t>(off, 1) * sizeof(double));
+    HM_CUDA(cudaMemsetAsync(H->store.p, 0, (size_t)std::max<int64_t>(off, 1) * sizeof(double), st));
+    H->ranks.alloc((size_t)std::max(H->nslots, 1) * sizeof(int));
+    HM_CUDA(cudaMemsetAsync(H->ranks.p, 0, (size_t)std::max(H->nslots, 1) * sizeof(int), st));
+    // host: inverse permutation, statically nonzero dense leaves
+    const std::vector<int64_t>& perm = bt->R->perm;
+    std::vector<int64_t> iperm((size_t)n);
+    for (int64_t i = 0; i < n; ++i) iperm[(size_t)bt->C->perm[(size_t)i]] = i;
+    int64_t nnz = rowptr[n];
+    for (size_t b = 0; b < nb; ++b) {
+      if (bt->nodes[b].kind != 1) continue;
+      const CNodeH& t = H->tc((int)b);
+      const CNodeH& s = H->sc((int)b);
+      bool any = false;
+      for (int64_t i = 0; i < t.size && !any; ++i) {
+        int64_t p = perm[(size_t)(t.off + i)];
+        for (int64_t e = rowptr[p]; e < rowptr[p + 1]; ++e) {
+          int64_t j = iperm[(size_t)colidx[e]];
+          if (j >= s.off && j < s.off + s.size && val[e] != 0.0) {
+            any = true;
+            break;
+          }
+        }
+      }
+      H->zero[b] = any ? 0 : 1;
+    }
+    DevBuf drp, dci, dva, dperm, diperm, ddl, dplaced;
+    upload(drp, std::vector<int64_t>(rowptr, rowptr + n + 1), st);
+    upload(dci, std::vector<int64_t>(colidx, colidx + nnz), st);
+    upload(dva, std::vector<double>(val, val + nnz), st);
+    upload(dperm, perm, st);
+    upload(diperm, iperm, st);
+    upload(ddl, dl, st);
+    dplaced.alloc(sizeof(unsigned long long));
+    HM_CUDA(cudaMemsetAsync(dplaced.p, 0, sizeof(unsigned long long), st));
+    HM_CUDA(launch_csr_scatter(ddl.as<DenseLeafDesc>(), (int)dl.size(), drp.as<int64_t>(), dci.as<int64_t>(),
+                               dva.as<double>(), dperm.as<int64_t>(), diperm.as<int64_t>(), H->store.as<double>(),
+                               dplaced.as<unsigned long long>(), st));
+    unsigned long long placed = 0;
+    HM_CUDA(cudaMemcpyAsync(&placed, dplaced.p, sizeof(placed), cudaMemcpyDeviceToHost, st));
+    HM_CUDA(cudaStreamSynchronize(st));
+    require((int64_t)placed == nnz, "csr: entries inside admissible blocks (rank > 0) are not supported");
+    H->st.n = n;
+    H->st.blocks = (int64_t)nb;
+    for (size_t b = 0; b < nb; ++b) {
+      if (bt->nodes[b].kind == 1) H->st.dense_leaves++;
+      if (bt->nodes[b].kind == 2) H->st.lowrank_leaves++;
+    }
+    H->st.device_bytes = (int64_t)(H->store.bytes + H->ranks.bytes);
+    *out = H.release();
+  });
+}
+
+hmat_status hmat_destroy(hmat* H) {
+  return guarded([&] {
+    if (H && H->ctx) cudaSetDevice(H->ctx->device);
+    delete H;
+  });
+}
+
+hmat_status hmat_to_dense(hmat_ctx* ctx, const hmat* H, double* out) {
+  return guarded([&] {
+    check_ctx(ctx);
+    require(H && out, "null argument");
+    std::vector<LeafRef> L;
+    for (size_t b = 0; b < H->bt->nodes.size(); ++b) {
+      int kind = H->bt->nodes[b].kind;
+      if (kind == 0) continue;
+      LeafRef r;
+      std::memset(&r, 0, sizeof(r));
+      r.kind = kind;
+      r.rows = (int)H->rows((int)b);
+      r.cols = (int)H->cols((int)b);
+      r.roff = (int)H->tc((int)b).off;
+      r.coff = (int)H->sc((int)b).off;
+      r.lda = r.rows;
+      r.ldb = r.cols;
+      r.a = H->loc[b];
+      r.b = H->vloc[b];
+      r.rank_slot = H->slot[b];
+      L.push_back(r);
+    }
+    DevBuf dl;
+    upload(dl, L, ctx->stream);
+    HM_CUDA(launch_to_dense(dl.as<LeafRef>(), (int)L.size(), H->store.as<double>(), H->ranks.as<int>(), out, H->n,
+                            ctx->stream));
+    HM_CUDA(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+hmat_status hmat_addeval(hmat_ctx* ctx, const hmat* H, double alpha, int trans, int64_t ncol, const double* X,
+                         double* Y) {
+  return guarded([&] {
+    check_ctx(ctx);
+    require(H && X && Y && ncol >= 0, "addeval: bad arguments");
+    if (ncol == 0) return;
+    Sched S;
+    S.next_slot = H->nslots;
+    Sym sym(S, *H->bt->R, *H->bt->C, H->max_rank);
+    sym.add_matrix(H);
+    int xobj = S.new_obj(), yobj_base = (int)S.objs.size();
+    // Output rows are split by the clusters of the shallowest level at which
+    // leaves start, so that independent CTAs write disjoint rows.
+    const hmat_btree& B = *H->bt;
+    int lmin = 1 << 30;
+    for (const BNodeH& nd : B.nodes)
+      if (nd.kind != 0) lmin = std::min(lmin, trans ? B.C->nodes[(size_t)nd.s].level : B.R->nodes[(size_t)nd.t].level);
+    const hmat_ctree& OT = trans ? *B.C : *B.R;
+    std::vector<int> groups;
+    for (size_t c = 0; c < OT.nodes.size(); ++c)
+      if (OT.nodes[c].level == lmin || (OT.nodes[c].level < lmin && OT.nodes[c].nsons == 0)) groups.push_back((int)c);
+    std::vector<std::vector<LeafRef>> per((size_t)OT.nodes.size());
+    std::vector<std::vector<int>> reads((size_t)OT.nodes.size());
+    std::vector<int> owner(OT.nodes.size(), -1);
+    for (int g : groups) {
+      // every descendant maps to its group
+      std::vector<int> st{g};
+      while (!st.empty()) {
+        int c = st.back();
+        st.pop_back();
+        owner[(size_t)c] = g;
+        for (int k = 0; k < OT.nodes[(size_t)c].nsons; ++k) st.push_back(OT.nodes[(size_t)c].son[k]);
+      }
+    }
+    std::vector<LeafRef> all;
+    std::vector<int> objs;
+    sym.collect(H, 0, 0, 0, true, all, objs);
+    for (size_t i = 0; i < all.size(); ++i) {
+      // find the leaf's output cluster by its offset
+      const LeafRef& L = all[i];
+      int64_t o = trans ? L.coff : L.roff;
+      int g = -1;
+      for (int c : groups)
+        if (OT.nodes[(size_t)c].off <= o && o < OT.nodes[(size_t)c].off + OT.nodes[(size_t)c].size) g = c;
+      per[(size_t)g].push_back(L);
+      reads[(size_t)g].push_back(objs[i]);
+    }
+    (void)owner;
+    for (int g : groups) {
+      if (per[(size_t)g].empty()) continue;
+      HTask t = blank(T_HMV);
+      t.flags = trans ? F_TRANS : 0;
+      t.m = (int)OT.nodes[(size_t)g].size;
+      t.alpha = alpha;
+      t.b = tag_ext(0, 0);
+      t.ldb = (int)H->n;
+      t.c = tag_ext(1, 0);
+      t.ldc = (int)H->n;
+      t.wa = (int)ncol;
+      t.list_begin = (int)S.leaves.size();
+      t.list_len = (int)per[(size_t)g].size();
+      S.leaves.insert(S.leaves.end(), per[(size_t)g].begin(), per[(size_t)g].end());
+      std::vector<int> rd = reads[(size_t)g];
+      rd.push_back(xobj);
+      int yo = S.new_obj();
+      S.emit(t, rd, {yo});
+    }
+    (void)yobj_base;
+    RunResult rr = run_tasks(ctx, S, H->store.as<double>(), H->ranks.as<int>(), 0.0, 0, (double*)X, Y);
+    if (rr.status) throw HmError(rr.status, "addeval: device status");
+  });
+}
+
+hmat_status hmat_lu(hmat_ctx* ctx, hmat* H, const hmat_opts* opts) {
+  return guarded([&] {
+    check_ctx(ctx);
+    require(H != nullptr, "null H-matrix");
+    double eps = opts ? opts->eps : 0.0;
+    int64_t mr = (opts && opts->max_rank > 0) ? std::min<int64_t>(opts->max_rank, H->max_rank) : H->max_rank;
+    int64_t spin = opts ? opts->spin_limit : 0;
+    require(eps >= 0.0, "eps must be >= 0");
+    auto t0 = std::chrono::steady_clock::now();
+    Sched S;
+    S.next_slot = H->nslots;
+    Sym sym(S, *H->bt->R, *H->bt->C, mr);
+    sym.add_matrix(H);
+    SAcc root = sym.acc_new(0, 0);
+    sym.lu(H, 0, root);
+    auto t1 = std::chrono::steady_clock::now();
+    // rank slots beyond the leaves' live in a per-call array
+    DevBuf allranks((size_t)std::max(S.next_slot, 1) * sizeof(int));
+    HM_CUDA(cudaMemcpyAsync(allranks.p, H->ranks.p, (size_t)H->nslots * sizeof(int), cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+    RunResult rr = run_tasks(ctx, S, H->store.as<double>(), allranks.as<int>(), eps, spin, nullptr, nullptr);
+    HM_CUDA(cudaMemcpyAsync(H->ranks.p, allranks.p, (size_t)H->nslots * sizeof(int), cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+    HM_CUDA(cudaStreamSynchronize(ctx->stream));
+    H->st.tasks = (int64_t)S.tasks.size();
+    H->st.truncations = (int64_t)rr.truncations;
+    H->st.factor_seconds = rr.ms * 1e-3;
+    H->st.schedule_seconds = std::chrono::duration<double>(t1 - t0).count();
+    H->st.status = rr.status;
+    H->st.device_bytes = (int64_t)(H->store.bytes + H->ranks.bytes) + S.ws_top * 8;
+    if (rr.status) throw HmError(rr.status, "hmat_lu: device status " + std::to_string(rr.status));
+  });
+}
+
+hmat_status hmat_solve(hmat_ctx* ctx, const hmat* LU, int trans, int64_t nrhs, double* B, int64_t ldb) {
+  return guarded([&] {
+    check_ctx(ctx);
+    require(LU && B && nrhs >= 0 && ldb >= LU->n, "solve: bad arguments");
+    if (nrhs == 0) return;
+    Sched S;
+    S.next_slot = LU->nslots;
+    Sym sym(S, *LU->bt->R, *LU->bt->C, LU->max_rank);
+    sym.add_matrix(LU);
+    int bobj = S.new_obj();
+    int64_t x = tag_ext(0, 0);
+    if (!trans) {
+      sym.hsolve(LU, 0, TRSM_L, x, (int)ldb, bobj, (int)nrhs);
+      sym.hsolve(LU, 0, TRSM_U, x, (int)ldb, bobj, (int)nrhs);
+    } else {
+      sym.hsolve(LU, 0, TRSM_UT, x, (int)ldb, bobj, (int)nrhs);
+      sym.hsolve(LU, 0, TRSM_LT, x, (int)ldb, bobj, (int)nrhs);
+    }
+    RunResult rr = run_tasks(ctx, S, LU->store.as<double>(), LU->ranks.as<int>(), 0.0, 0, B, nullptr);
+    if (rr.status) throw HmError(rr.status, "solve: device status");
+  });
+}
+
+hmat_status trunc_lowrank_batched(hmat_ctx* ctx, int64_t count, const int64_t* m, const int64_t* n, const int64_t* k,
+                                  double* const* U, double* const* V, double eps, int64_t* k_new) {
+  return guarded([&] {
+    check_ctx(ctx);
+    require(count >= 0 && (count == 0 || (m && n && k && U && V && k_new)), "trunc_lowrank_batched: bad arguments");
+    if (count == 0) return;
+    int64_t total = 0;
+    std::vector<TruncProblem> P((size_t)count);
+    for (int64_t i = 0; i < count; ++i) {
+      require(m[i] >= 0 && n[i] >= 0 && k[i] >= 0 && k[i] <= HM_LMAX_HOST, "trunc_lowrank: k must be <= 256");
+      total += (2 * m[i] + n[i]) * k[i] + 2 * k[i] * k[i] + 64;
+    }
+    DevBuf ws((size_t)total * sizeof(double));
+    int64_t off = 0;
+    for (int64_t i = 0; i < count; ++i) {
+      TruncProblem& p = P[(size_t)i];
+      p.m = (int)m[i];
+      p.n = (int)n[i];
+      p.k = (int)k[i];
+      p.ldu = (int)std::max<int64_t>(m[i], 1);
+      p.ldv = (int)std::max<int64_t>(n[i], 1);
+      p.U = U[i];
+      p.V = V[i];
+      p.ws = ws.as<double>() + off;
+      p.k_new = k_new + i;
+      off += (2 * m[i] + n[i]) * k[i] + 2 * k[i] * k[i] + 64;
+    }
+    DevBuf dp, dst(sizeof(int));
+    upload(dp, P, ctx->stream);
+    HM_CUDA(cudaMemsetAsync(dst.p, 0, sizeof(int), ctx->stream));
+    HM_CUDA(launch_trunc_batched(dp.as<TruncProblem>(), (int)count, eps, dst.as<int>(), ctx->stream));
+    int status = 0;
+    HM_CUDA(cudaMemcpyAsync(&status, dst.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    HM_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (status) throw HmError(status, "trunc_lowrank: device status");
+  });
+}
+
+hmat_status trunc_lowrank(hmat_ctx* ctx, int64_t m, int64_t n, int64_t k, double* U, int64_t ldu, double* V,
+                          int64_t ldv, double eps, int64_t* k_new) {
+  return guarded([&] {
+    check_ctx(ctx);
+    require(U && V && k_new && ldu >= m && ldv >= n, "trunc_lowrank: bad arguments");
+    require(ldu == std::max<int64_t>(m, 1) && ldv == std::max<int64_t>(n, 1), "trunc_lowrank: ld must equal the row count");
+    DevBuf dk(sizeof(int64_t));
+    double* Up = U;
+    double* Vp = V;
+    hmat_status s = trunc_lowrank_batched(ctx, 1, &m, &n, &k, &Up, &Vp, eps, dk.as<int64_t>());
+    if (s != HMAT_OK) throw HmError(s, g_last_error);
+    HM_CUDA(cudaMemcpy(k_new, dk.p, sizeof(int64_t), cudaMemcpyDeviceToHost));
+  });
+}
+
+hmat_status hmat_stats_get(const hmat* H, hmat_stats* out) {
+  return guarded([&] {
+    require(H && out, "null argument");
+    hmat_stats s = H->st;
+    std::vector<int> r((size_t)std::max(H->nslots, 1));
+    HM_CUDA(cudaMemcpy(r.data(), H->ranks.p, (size_t)H->nslots * sizeof(int), cudaMemcpyDeviceToHost));
+    int64_t mx = 0;
+    double sum = 0;
+    for (int i = 0; i < H->nslots; ++i) {
+      mx = std::max<int64_t>(mx, r[(size_t)i]);
+      sum += r[(size_t)i];
+    }
+    s.max_rank = mx;
+    s.mean_rank = H->nslots ? sum / H->nslots : 0.0;
+    *out = s;
+  });
+}
+
+hmat_status hmat_ranks(const hmat* H, int64_t* ranks) {
+  return guarded([&] {
+    require(H && ranks, "null argument");
+    std::vector<int> r((size_t)std::max(H->nslots, 1));
+    HM_CUDA(cudaMemcpy(r.data(), H->ranks.p, (size_t)H->nslots * sizeof(int), cudaMemcpyDeviceToHost));
+    for (size_t b = 0; b < H->bt->nodes.size(); ++b)
+      ranks[b] = H->bt->nodes[b].kind == 2 ? r[(size_t)H->slot[b]] : -1;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,463 @@
+// hmat_kernels.cu -- device side of the H-matrix library (sm_103a).
+//
+//  * exec_tasks: one persistent kernel that runs a dependency-ordered task
+//    list (the unrolled H-LU / H-solve / H x thin-dense recursions).  CTAs take
+//    tasks in list order from a global counter; a task waits (bounded, acquire
+//    loads) until its predecessors are marked done, runs on the whole CTA, and
+//    marks itself done with a release store.  Because tasks are taken in a
+//    topological order and every CTA of the grid is resident, the lowest
+//    unfinished task always has its predecessors finished: no deadlock.  A
+//    wait that exceeds its limit writes HMAT_ERR_TIMEOUT into the status word;
+//    once the status is non-zero every remaining task is skipped and marked
+//    done, so the kernel always terminates.
+//  * trunc_batched: Section 3 "Truncation" of independent low-rank matrices,
+//    one CTA each.
+//  * csr_scatter / to_dense: H-matrix construction and dense export.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hmat_device.cuh"
+#include "hmat_kernels.h"
+
+namespace hm {
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Locations: bits 60-61 select the base (0 H storage, 1 workspace, 2 and 3
+// caller buffers), the rest is an offset in doubles.
+__device__ __forceinline__ double* loc(const ExecEnv& e, int64_t l) {
+  if (l < 0) return nullptr;
+  int64_t off = l & ((WS_BIT)-1);
+  switch ((int)((l >> 60) & 3)) {
+    case 0: return e.hbase + off;
+    case 1: return e.wsbase + off;
+    case 2: return e.ext0 + off;
+    default: return e.ext1 + off;
+  }
+}
+__device__ __forceinline__ int width_of(const ExecEnv& e, int w) { return w >= 0 ? w : e.ranks[-w - 1]; }
+
+// true iff every entry of the m x n matrix (ld) is zero
+__device__ bool cta_all_zero(const double* A, int ld, int m, int n, Smem& s) {
+  int nz = 0;
+  for (int idx = threadIdx.x; idx < m * n; idx += HM_THREADS)
+    if (A[(int64_t)(idx / m) * ld + idx % m] != 0.0) nz = 1;
+  nz = __syncthreads_or(nz);
+  return !nz;
+}
+
+__device__ void cta_copy(double* C, int ldc, const double* A, int lda, int m, int n, bool trans, double alpha) {
+  for (int idx = threadIdx.x; idx < m * n; idx += HM_THREADS) {
+    int i = idx % m, j = idx / m;
+    double v = trans ? A[(int64_t)i * lda + j] : A[(int64_t)j * lda + i];
+    C[(int64_t)j * ldc + i] = alpha * v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Task bodies
+// ---------------------------------------------------------------------------
+__device__ void task_hmv(const ExecEnv& e, const HTask& t, Smem& s) {
+  bool trans = t.flags & F_TRANS;
+  int w = width_of(e, t.wa);
+  double* out = loc(e, t.c);
+  const double* in = loc(e, t.b);
+  if (t.flags & F_ZERO_OUT) {
+    for (int idx = threadIdx.x; idx < t.m * w; idx += HM_THREADS)
+      out[(int64_t)(idx / t.m) * t.ldc + idx % t.m] = 0.0;
+    __syncthreads();
+  }
+  if (w <= 0) return;
+  for (int li = 0; li < t.list_len; ++li) {
+    const LeafRef L = e.leaves[t.list_begin + li];
+    int orow = trans ? L.coff : L.roff;
+    int irow = trans ? L.roff : L.coff;
+    int orows = trans ? L.cols : L.rows;
+    int irows = trans ? L.rows : L.cols;
+    if (L.kind == 1) {
+      const double* N = loc(e, L.a);
+      cta_gemm(out + orow, t.ldc, orows, w, irows, t.alpha, N, L.lda, trans, in + irow, t.ldb, false, false);
+      __syncthreads();
+    } else {
+      int k = e.ranks[L.rank_slot];
+      if (k <= 0) continue;
+      const double* Fin = loc(e, trans ? L.a : L.b);   // factor multiplying the input
+      const double* Fout = loc(e, trans ? L.b : L.a);  // factor producing the output
+      int ldin = trans ? L.lda : L.ldb;
+      int ldout = trans ? L.ldb : L.lda;
+      // chunk the columns so that Zhat (k x wc) fits in shared memory
+      int wc = HM_JAC_SMEM / k;
+      if (wc > w) wc = w;
+      for (int c0 = 0; c0 < w; c0 += wc) {
+        int cw = w - c0 < wc ? w - c0 : wc;
+        cta_gemm(s.jac, k, k, cw, irows, t.alpha, Fin, ldin, true, in + irow + (int64_t)c0 * t.ldb, t.ldb, false,
+                 true);
+        __syncthreads();
+        cta_gemm(out + orow + (int64_t)c0 * t.ldc, t.ldc, orows, cw, k, 1.0, Fout, ldout, false, s.jac, k, false,
+                 false);
+        __syncthreads();
+      }
+    }
+  }
+}
+
+__device__ void task_densify(const ExecEnv& e, const HTask& t, Smem& s) {
+  bool trans = t.flags & F_TRANS;
+  double* out = loc(e, t.c);
+  for (int li = 0; li < t.list_len; ++li) {
+    const LeafRef L = e.leaves[t.list_begin + li];
+    int orow = trans ? L.coff : L.roff;
+    int ocol = trans ? L.roff : L.coff;
+    int orows = trans ? L.cols : L.rows;
+    int ocols = trans ? L.rows : L.cols;
+    double* o = out + orow + (int64_t)ocol * t.ldc;
+    if (L.kind == 1) {
+      cta_copy(o, t.ldc, loc(e, L.a), L.lda, orows, ocols, trans, 1.0);
+    } else {
+      int k = e.ranks[L.rank_slot];
+      const double* U = loc(e, L.a);
+      const double* V = loc(e, L.b);
+      if (!trans) cta_gemm(o, t.ldc, orows, ocols, k, 1.0, U, L.lda, false, V, L.ldb, true, true);
+      else cta_gemm(o, t.ldc, orows, ocols, k, 1.0, V, L.ldb, false, U, L.lda, true, true);
+    }
+    __syncthreads();
+  }
+}
+
+__device__ void task_rkadd(const ExecEnv& e, const HTask& t, Smem& s) {
+  int m = t.m, n = t.n;
+  bool aid = t.flags & F_A_IDENT, bid = t.flags & F_B_IDENT, btr = t.flags & F_B_TRANS;
+  int w = aid ? m : (bid ? n : width_of(e, t.wa));
+  int kin = t.rin >= 0 ? e.ranks[t.rin] : 0;
+  const double* A = loc(e, t.a);
+  const double* B = loc(e, t.b);
+  const double* Uin = loc(e, t.c);
+  const double* Vin = loc(e, t.d);
+  double* Uout = loc(e, t.e);
+  double* Vout = loc(e, t.f);
+  bool zero = (w == 0);
+  if (!zero && (t.flags & F_CHECK_ZERO)) {
+    bool za = aid ? false : cta_all_zero(A, t.lda, m, w, s);
+    bool zb = bid ? false : (btr ? cta_all_zero(B, t.ldb, w, n, s) : cta_all_zero(B, t.ldb, n, w, s));
+    zero = za || zb;
+  }
+  if (zero) {
+    if (Uout != Uin && kin > 0) {
+      cta_copy(Uout, t.lde, Uin, t.ldc, m, kin, false, 1.0);
+      cta_copy(Vout, t.ldf, Vin, t.ldd, n, kin, false, 1.0);
+    }
+    if (threadIdx.x == 0 && t.rout >= 0) e.ranks[t.rout] = kin;
+    return;
+  }
+  int l = w + kin;
+  if (l > HM_LMAX) {
+    if (threadIdx.x == 0) set_status(e.status, DS_INTERNAL);
+    return;
+  }
+  double* ws = loc(e, t.ws);
+  double* SA = ws;
+  double* SB = SA + (int64_t)m * l;
+  double* W = SB + (int64_t)n * l;
+  double* Jg = W + (int64_t)m * l;
+  for (int idx = threadIdx.x; idx < m * l; idx += HM_THREADS) {
+    int i = idx % m, j = idx / m;
+    double v;
+    if (j < w) v = t.alpha * (aid ? (i == j ? 1.0 : 0.0) : A[(int64_t)j * t.lda + i]);
+    else v = Uin[(int64_t)(j - w) * t.ldc + i];
+    SA[idx] = v;
+  }
+  for (int idx = threadIdx.x; idx < n * l; idx += HM_THREADS) {
+    int i = idx % n, j = idx / n;
+    double v;
+    if (j < w) v = bid ? (i == j ? 1.0 : 0.0) : (btr ? B[(int64_t)i * t.ldb + j] : B[(int64_t)j * t.ldb + i]);
+    else v = Vin[(int64_t)(j - w) * t.ldd + i];
+    SB[idx] = v;
+  }
+  __syncthreads();
+  TruncIn in;
+  in.nb = 1;
+  in.m = m;
+  in.n[0] = n;
+  in.k[0] = l;
+  in.SA[0] = SA;
+  in.SB[0] = SB;
+  in.W = W;
+  in.Jg = Jg;
+  int k = trunc_core(in, e.eps, t.cap, Uout, t.lde, Vout, t.ldf, e.status, s);
+  if (threadIdx.x == 0) {
+    if (t.rout >= 0) e.ranks[t.rout] = k;
+    atomicAdd(e.counters, 1ull);
+  }
+}
+
+__device__ void task_rowmerge(const ExecEnv& e, const HTask& t, Smem& s) {
+  int m = t.m;
+  int n0 = t.p, n1 = t.q;
+  int k0 = width_of(e, t.wa), k1 = width_of(e, t.wb);
+  double* Uout = loc(e, t.e);
+  double* Vout = loc(e, t.f);
+  if (k0 + k1 > HM_LMAX) {
+    if (threadIdx.x == 0) set_status(e.status, DS_INTERNAL);
+    return;
+  }
+  if (k0 + k1 == 0) {
+    if (threadIdx.x == 0 && t.rout >= 0) e.ranks[t.rout] = 0;
+    return;
+  }
+  double* ws = loc(e, t.ws);
+  double* SA0 = ws;
+  double* SA1 = SA0 + (int64_t)m * k0;
+  double* SB0 = SA1 + (int64_t)m * k1;
+  double* SB1 = SB0 + (int64_t)n0 * k0;
+  double* W = SB1 + (int64_t)n1 * k1;
+  double* Jg = W + (int64_t)m * (k0 + k1);
+  cta_copy(SA0, m, loc(e, t.a), t.lda, m, k0, false, 1.0);
+  cta_copy(SB0, n0, loc(e, t.b), t.ldb, n0, k0, false, 1.0);
+  cta_copy(SA1, m, loc(e, t.c), t.ldc, m, k1, false, 1.0);
+  cta_copy(SB1, n1, loc(e, t.d), t.ldd, n1, k1, false, 1.0);
+  __syncthreads();
+  TruncIn in;
+  in.nb = 2;
+  in.m = m;
+  in.n[0] = n0;
+  in.n[1] = n1;
+  in.k[0] = k0;
+  in.k[1] = k1;
+  in.SA[0] = SA0;
+  in.SA[1] = SA1;
+  in.SB[0] = SB0;
+  in.SB[1] = SB1;
+  in.W = W;
+  in.Jg = Jg;
+  int k = trunc_core(in, e.eps, t.cap, Uout, t.lde, Vout, t.ldf, e.status, s);
+  if (threadIdx.x == 0) {
+    if (t.rout >= 0) e.ranks[t.rout] = k;
+    atomicAdd(e.counters, 1ull);
+  }
+}
+
+__device__ void run_task(const ExecEnv& e, const HTask& t, Smem& s) {
+  switch (t.type) {
+    case T_NOP:
+      break;
+    case T_LU:
+      cta_lu(loc(e, t.a), t.lda, t.m, e.status);
+      break;
+    case T_TRSM:
+      cta_trsm(t.p, loc(e, t.a), t.lda, t.m, loc(e, t.b), t.ldb, width_of(e, t.wa));
+      break;
+    case T_HMV:
+      task_hmv(e, t, s);
+      break;
+    case T_DENSIFY:
+      task_densify(e, t, s);
+      break;
+    case T_GEMM: {
+      int w = width_of(e, t.wa);
+      bool zero = t.flags & F_ZERO_OUT;
+      if (w > 0 || zero)
+        cta_gemm(loc(e, t.c), t.ldc, t.m, t.n, w, t.alpha, loc(e, t.a), t.lda, false, loc(e, t.b), t.ldb,
+                 !(t.flags & F_B_TRANS), zero);
+      break;
+    }
+    case T_ADD: {
+      double* C = loc(e, t.c);
+      const double* A = loc(e, t.a);
+      bool tr = t.flags & F_TRANS;
+      for (int idx = threadIdx.x; idx < t.m * t.n; idx += HM_THREADS) {
+        int i = idx % t.m, j = idx / t.m;
+        C[(int64_t)j * t.ldc + i] += t.alpha * (tr ? A[(int64_t)i * t.lda + j] : A[(int64_t)j * t.lda + i]);
+      }
+      break;
+    }
+    case T_COPY:
+      cta_copy(loc(e, t.c), t.ldc, loc(e, t.a), t.lda, t.m, t.n, t.flags & F_TRANS, 1.0);
+      break;
+    case T_ZERO: {
+      double* C = loc(e, t.c);
+      for (int idx = threadIdx.x; idx < t.m * t.n; idx += HM_THREADS) C[(int64_t)(idx / t.m) * t.ldc + idx % t.m] = 0.0;
+      break;
+    }
+    case T_RANKSET:
+      if (threadIdx.x == 0) e.ranks[t.rout] = width_of(e, t.wa);
+      break;
+    case T_RKADD:
+      task_rkadd(e, t, s);
+      break;
+    case T_ROWMERGE:
+      task_rowmerge(e, t, s);
+      break;
+    default:
+      if (threadIdx.x == 0) set_status(e.status, DS_INTERNAL);
+  }
+}
+
+__global__ void __launch_bounds__(HM_THREADS) exec_tasks(ExecEnv e) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& s = *reinterpret_cast<Smem*>(smem_raw);
+  __shared__ long long cur;
+  __shared__ int skip;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      cur = (long long)atomicAdd(e.head, 1ull);
+      skip = 0;
+      if (cur < e.ntasks) {
+        // bounded wait on every predecessor
+        int64_t d0 = e.dep_ptr[cur], d1 = e.dep_ptr[cur + 1];
+        uint64_t t0 = global_ns();
+        for (int64_t d = d0; d < d1 && !skip; ++d) {
+          const int* flag = e.done + e.dep_idx[d];
+          int64_t it = 0;
+          while (ld_acquire(flag) == 0) {
+            if (++it > e.spin_iters || global_ns() - t0 > e.spin_ns) {
+              set_status(e.status, DS_TIMEOUT);
+              skip = 1;
+              break;
+            }
+            __nanosleep(64);
+          }
+        }
+        if (ld_acquire(e.status) != 0) skip = 1;
+      }
+    }
+    __syncthreads();
+    long long t = cur;
+    if (t >= e.ntasks) break;
+    if (!skip) {
+      HTask task = e.tasks[t];
+      run_task(e, task, s);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release(e.done + t, 1);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Batched truncation of independent low-rank matrices in place.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(HM_THREADS) trunc_batched(const TruncProblem* probs, double eps, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& s = *reinterpret_cast<Smem*>(smem_raw);
+  const TruncProblem P = probs[blockIdx.x];
+  int m = P.m, n = P.n, l = P.k;
+  if (l > HM_LMAX) {
+    if (threadIdx.x == 0) set_status(status, DS_INTERNAL);
+    return;
+  }
+  double* SA = P.ws;
+  double* SB = SA + (int64_t)m * l;
+  double* W = SB + (int64_t)n * l;
+  double* Jg = W + (int64_t)m * l;
+  cta_copy(SA, m, P.U, P.ldu, m, l, false, 1.0);
+  cta_copy(SB, n, P.V, P.ldv, n, l, false, 1.0);
+  __syncthreads();
+  TruncIn in;
+  in.nb = 1;
+  in.m = m;
+  in.n[0] = n;
+  in.k[0] = l;
+  in.SA[0] = SA;
+  in.SB[0] = SB;
+  in.W = W;
+  in.Jg = Jg;
+  int cap = l < m ? l : m;
+  if (n < cap) cap = n;
+  int k = trunc_core(in, eps, cap, P.U, P.ldu, P.V, P.ldv, status, s);
+  if (threadIdx.x == 0) P.k_new[0] = k;
+}
+
+// ---------------------------------------------------------------------------
+// Construction from CSR (original ordering) and dense export.
+// ---------------------------------------------------------------------------
+__global__ void csr_scatter(const DenseLeafDesc* leaves, int nleaves, const int64_t* rowptr, const int64_t* colidx,
+                            const double* val, const int64_t* perm, const int64_t* iperm, double* hbase,
+                            unsigned long long* placed) {
+  int b = blockIdx.x;
+  if (b >= nleaves) return;
+  DenseLeafDesc L = leaves[b];
+  unsigned long long cnt = 0;
+  for (int i = threadIdx.x; i < L.rows; i += blockDim.x) {
+    int64_t p = perm[L.roff + i];
+    for (int64_t e = rowptr[p]; e < rowptr[p + 1]; ++e) {
+      int64_t j = iperm[colidx[e]] - L.coff;
+      if (j >= 0 && j < L.cols) {
+        hbase[L.off + i + j * (int64_t)L.rows] += val[e];
+        ++cnt;
+      }
+    }
+  }
+  if (cnt) atomicAdd(placed, cnt);
+}
+
+__global__ void to_dense_kernel(const LeafRef* leaves, int nleaves, const double* hbase, const int* ranks,
+                                double* out, int64_t ldo) {
+  int b = blockIdx.x;
+  if (b >= nleaves) return;
+  LeafRef L = leaves[b];
+  for (int idx = threadIdx.x; idx < L.rows * L.cols; idx += blockDim.x) {
+    int i = idx % L.rows, j = idx / L.rows;
+    double v = 0.0;
+    if (L.kind == 1) {
+      v = hbase[L.a + i + (int64_t)j * L.lda];
+    } else {
+      int k = ranks[L.rank_slot];
+      for (int l = 0; l < k; ++l) v += hbase[L.a + i + (int64_t)l * L.lda] * hbase[L.b + j + (int64_t)l * L.ldb];
+    }
+    out[(L.roff + i) + (int64_t)(L.coff + j) * ldo] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+size_t smem_bytes() { return sizeof(Smem); }
+
+cudaError_t launch_exec(const ExecEnv& env, int grid, cudaStream_t st) {
+  exec_tasks<<<grid, HM_THREADS, sizeof(Smem), st>>>(env);
+  return cudaGetLastError();
+}
+
+cudaError_t exec_occupancy(int* blocks_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(exec_tasks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, exec_tasks, HM_THREADS, sizeof(Smem));
+}
+
+cudaError_t launch_trunc_batched(const TruncProblem* probs, int count, double eps, int* status, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(trunc_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+  if (e != cudaSuccess) return e;
+  trunc_batched<<<count, HM_THREADS, sizeof(Smem), st>>>(probs, eps, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_csr_scatter(const DenseLeafDesc* leaves, int nleaves, const int64_t* rowptr, const int64_t* colidx,
+                               const double* val, const int64_t* perm, const int64_t* iperm, double* hbase,
+                               unsigned long long* placed, cudaStream_t st) {
+  if (nleaves == 0) return cudaSuccess;
+  csr_scatter<<<nleaves, 128, 0, st>>>(leaves, nleaves, rowptr, colidx, val, perm, iperm, hbase, placed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_dense(const LeafRef* leaves, int nleaves, const double* hbase, const int* ranks, double* out,
+                            int64_t ldo, cudaStream_t st) {
+  if (nleaves == 0) return cudaSuccess;
+  to_dense_kernel<<<nleaves, 256, 0, st>>>(leaves, nleaves, hbase, ranks, out, ldo);
+  return cudaGetLastError();
+}
+
+}  // namespace hm

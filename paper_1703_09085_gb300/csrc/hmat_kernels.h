@@ -1,0 +1,56 @@
+// hmat_kernels.h -- host-visible declarations of the device side.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hmat_tasks.h"
+
+namespace hm {
+
+// Everything the persistent executor reads.
+struct ExecEnv {
+  double* hbase;              // H-matrix storage
+  double* wsbase;             // workspace arena of this task list
+  double* ext0;               // caller buffers addressed by tagged locations
+  double* ext1;
+  int* ranks;                 // rank slots
+  const HTask* tasks;
+  long long ntasks;
+  const int64_t* dep_ptr;     // predecessors of task i: dep_idx[dep_ptr[i] .. dep_ptr[i+1])
+  const int32_t* dep_idx;
+  const LeafRef* leaves;
+  int* done;                  // per task, 0 -> 1 when finished
+  unsigned long long* head;   // next task to take
+  int* status;                // device status word (hmat_status numbering)
+  unsigned long long* counters;  // [0] truncations run
+  double eps;
+  long long spin_iters;       // bounded waits: iteration limit
+  unsigned long long spin_ns; //                 and time limit
+};
+
+struct TruncProblem {
+  int m, n, k;
+  int ldu, ldv;
+  double* U;
+  double* V;
+  double* ws;       // (2m + n) k + 2 k^2 doubles
+  int64_t* k_new;
+};
+
+struct DenseLeafDesc {
+  int64_t off;      // offset of N in the H storage
+  int64_t roff, coff;
+  int rows, cols;
+};
+
+size_t smem_bytes();
+cudaError_t exec_occupancy(int* blocks_per_sm);
+cudaError_t launch_exec(const ExecEnv& env, int grid, cudaStream_t st);
+cudaError_t launch_trunc_batched(const TruncProblem* probs, int count, double eps, int* status, cudaStream_t st);
+cudaError_t launch_csr_scatter(const DenseLeafDesc* leaves, int nleaves, const int64_t* rowptr,
+                               const int64_t* colidx, const double* val, const int64_t* perm, const int64_t* iperm,
+                               double* hbase, unsigned long long* placed, cudaStream_t st);
+cudaError_t launch_to_dense(const LeafRef* leaves, int nleaves, const double* hbase, const int* ranks, double* out,
+                            int64_t ldo, cudaStream_t st);
+
+}  // namespace hm

@@ -1,0 +1,62 @@
+"""C-ABI library on the CPU: it loads, exports every symbol include/hmat.h
+declares, and its host-side tree builders agree bit-exactly with the oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import hmat_synth as hs
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def hm():
+    from paper_1703_09085_gb300 import build
+    build.build()
+    import paper_1703_09085_gb300 as g
+    return g
+
+
+class _NullCtx:
+    h = None
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "hmat.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:hmat_status|size_t|int64_t)\s+(\w+)\s*\(", src, flags=re.M)))
+
+
+def test_exports_every_declared_symbol(hm):
+    decl = declared_symbols()
+    assert len(decl) >= 20
+    L = hm.lib()
+    for name in decl:
+        assert hasattr(L, name), name
+    assert sorted(hm.EXPORTS) == decl
+
+
+@pytest.mark.parametrize("N,d,leaf", [(4, 2, 4), (64, 2, 32), (16, 3, 64), (13, 2, 8), (21, 3, 32), (32, 3, 64)])
+def test_trees_bit_exact_vs_oracle(hm, N, d, leaf):
+    x = hs.grid_coords(N, d)
+    ct = hm.ClusterTree(_NullCtx(), x, leaf)
+    oc = oracle.ClusterTree(x, leaf)
+    assert np.array_equal(ct.perm(), oc.perm())
+    a, b = ct.nodes(), oc.nodes()
+    for key in ("off", "size", "level", "parent", "nsons"):
+        assert np.array_equal(a[key], b[key]), key
+    bt = hm.BlockTree(_NullCtx(), ct, ct, 2.0)
+    ob = oracle.BlockTree(oc, oc, 2.0)
+    a, b = bt.nodes(), ob.nodes()
+    for key in ("t", "s", "level", "parent", "kind"):
+        assert np.array_equal(a[key], b[key]), key
+
+
+def test_tree_rejects_bad_input(hm):
+    with pytest.raises(hm.HmatError):
+        hm.ClusterTree(_NullCtx(), np.zeros((4, 2)), 1)  # duplicate points cannot be bisected
+    with pytest.raises(hm.HmatError):
+        hm.ClusterTree(_NullCtx(), np.zeros((4, 5)), 2)  # d must be 2 or 3

@@ -1,0 +1,93 @@
+"""GPU H-LU with accumulated updates, H-solve and H x thin-dense product
+against the oracle and against dense linear algebra."""
+import numpy as np
+import pytest
+
+import hmat_synth as hs
+import oracle
+from gpu_util import GpuProblem, from_dev, hm, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return hm().Context(0)
+
+
+def dense_lu_nopivot(A):
+    M = A.copy()
+    for k in range(M.shape[0]):
+        M[k + 1:, k] /= M[k, k]
+        M[k + 1:, k + 1:] -= np.outer(M[k + 1:, k], M[k, k + 1:])
+    return M
+
+
+def test_create_from_csr_matches_permuted_matrix(ctx):
+    gp = GpuProblem(ctx, hs.small_laplace(16, 2, 8, 0.0))
+    A = gp.csr.to_dense()[np.ix_(gp.perm, gp.perm)]
+    assert np.array_equal(gp.dense(), A)
+
+
+@pytest.mark.parametrize("N,d,leaf", [(32, 2, 16), (16, 2, 8), (8, 3, 16), (10, 3, 32), (24, 2, 32)])
+def test_hlu_eps0_equals_dense_lu(ctx, N, d, leaf):
+    gp = GpuProblem(ctx, hs.small_laplace(N, d, leaf, 0.0))
+    A = gp.csr.to_dense()[np.ix_(gp.perm, gp.perm)]
+    gp.H.lu(0.0)
+    D = gp.dense()
+    ref = dense_lu_nopivot(A)
+    assert np.abs(D - ref).max() <= 1e-10 * np.abs(ref).max()
+    # the oracle's H-LU gives the same factors
+    op = hs.small_laplace(N, d, leaf, 0.0)
+    ct, bt, csr, H = oracle.setup(op)
+    H.lu(0.0, True)
+    assert np.abs(D - H.to_dense()).max() <= 1e-10 * np.abs(ref).max()
+
+
+def test_solve_after_exact_lu(ctx):
+    gp = GpuProblem(ctx, hs.small_laplace(32, 2, 16, 0.0))
+    A = gp.csr.to_dense()[np.ix_(gp.perm, gp.perm)]
+    gp.H.lu(0.0)
+    b = hs.normal(3, 1024 * 3).reshape(1024, 3)
+    t = to_dev(b)
+    gp.H.solve(t)
+    x = from_dev(t)
+    assert np.abs(A @ x - b).max() <= 1e-10 * np.abs(b).max()
+    t = to_dev(b)
+    gp.H.solve(t, trans=True)
+    assert np.abs(A.T @ from_dev(t) - b).max() <= 1e-10 * np.abs(b).max()
+
+
+def test_addeval_after_lu(ctx):
+    gp = GpuProblem(ctx, hs.small_laplace(32, 2, 16, 1e-6))
+    gp.H.lu(1e-6)
+    D = gp.dense()
+    X = hs.normal(5, 1024 * 4).reshape(1024, 4)
+    Y0 = hs.normal(6, 1024 * 4).reshape(1024, 4)
+    for trans in (False, True):
+        y = to_dev(Y0)
+        gp.H.addeval(-0.5, to_dev(X), y, trans=trans)
+        ref = Y0 - 0.5 * (D.T if trans else D) @ X
+        assert np.abs(from_dev(y) - ref).max() <= 1e-12 * np.abs(ref).max() * 10
+
+
+@pytest.mark.parametrize("prob", ["laplace2d_64", "laplace3d_16"])
+def test_hlu_truncated_matches_oracle_quality(ctx, prob):
+    p = hs.laplace2d_64() if prob == "laplace2d_64" else hs.small_laplace(16, 3, 64, 1e-4)
+    gp = GpuProblem(ctx, p)
+    gp.H.lu(p.eps)
+    st = gp.H.stats()
+    assert st["status"] == 0 and st["truncations"] > 0
+    v0 = hs.start_vector(p.n, 0)
+    err_gpu = gp.precond_error(v0[gp.perm])
+    ct, bt, csr, H = oracle.setup(p)
+    H.lu(p.eps, True)
+    err_orc, _ = H.precond_error(csr, v0)
+    # preconditioner quality within 2x of the oracle at the same eps
+    assert err_gpu <= 2.0 * err_orc and err_orc <= 2.0 * err_gpu
+    # ranks of the admissible leaves agree closely
+    rg, ro = gp.H.ranks(), H.ranks()
+    adm = rg >= 0
+    assert np.array_equal(adm, ro >= 0)
+    assert np.abs(rg[adm] - ro[adm]).max() <= 2
+    assert abs(rg[adm].mean() - ro[adm].mean()) <= 0.1
