@@ -1,0 +1,348 @@
+"""Benchmark of the H-LU setup with accumulated updates on GB300.
+
+One step = one H-LU factorisation (the whole hot path: accumulated products,
+truncations, flushes, leaf LU/TRSM) of the workload's matrix, starting from a
+fresh device copy of the unfactored H-matrix.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--impl ours|reference]
+
+--impl reference times the CPU oracle (oracle/, serial FP64) on a bounded
+sample of the workload instead.  Under torchrun every rank factors its own
+replica (the path does not shard); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import hmat_synth as hs  # noqa: E402
+
+METRIC = "H-LU setup truncations/s (accumulated updates) vs plain FP64 at equal ||I-(LU)^-1 A||"
+UNIT = "truncations/s"
+TASK_NAMES = ["NOP", "LU", "TRSM", "HMV", "DENSIFY", "GEMM", "ADD", "RKADD", "ROWMERGE", "COPY", "ZERO", "RANKSET"]
+FP64_PEAK_TFLOPS = 1.25     # GB300 nominal FP64 (vector and tensor) rate, 152 SMs at up to 2070 MHz
+WORKLOADS = {"laplace3d_32": hs.laplace3d_32, "laplace3d_64": hs.laplace3d_64, "laplace2d_64": hs.laplace2d_64}
+# bounded oracle sample: the same operator family, tolerance and leaf size at 16^3
+SAMPLE = {"laplace3d_32": lambda: hs.small_laplace(16, 3, 64, 1e-4),
+          "laplace3d_64": lambda: hs.small_laplace(16, 3, 64, 1e-4),
+          "laplace2d_64": hs.laplace2d_64}
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def cpu_sample(workload: str, min_seconds: float = 10.0) -> dict:
+    """The oracle as it stands, serial, on the bounded sample, repeated until
+    at least min_seconds of CPU work."""
+    import oracle
+    oracle.build()
+    p = SAMPLE[workload]()
+    trunc = 0
+    el = 0.0
+    runs = 0
+    while el < min_seconds or runs == 0:
+        ct, bt, csr, H = oracle.setup(p)
+        oracle.stats_reset()
+        t0 = time.perf_counter()
+        H.lu(p.eps, True)
+        el += time.perf_counter() - t0
+        trunc += oracle.stats()["truncations"]
+        runs += 1
+    return {"value": trunc / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{runs} x serial FP64 oracle H-LU (accumulated) of {p.name} (n={p.n}, leaf {p.leaf}, "
+                      f"eps {p.eps:g}), {el:.1f} s, {trunc} truncations"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        reasons = set()
+        for r in rows:
+            for name, col in (("hw_slowdown", 5), ("hw_thermal_slowdown", 6), ("sw_thermal_slowdown", 7),
+                              ("sw_power_cap", 8)):
+                if r[col].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    if rank != 0:
+        return
+    p = SAMPLE[args.workload]()
+    import oracle
+    oracle.build()
+    times, truncs = [], []
+    for i in range(args.warmup + args.steps):
+        ct, bt, csr, H = oracle.setup(p)
+        oracle.stats_reset()
+        t0 = time.perf_counter()
+        H.lu(p.eps, True)
+        el = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(el)
+            truncs.append(oracle.stats()["truncations"])
+    value = sum(truncs) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": p.name, "n": p.n, "leaf": p.leaf, "eta": p.eta,
+                                            "eps": p.eps, "note": "bounded CPU sample of " + args.workload},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} timed serial oracle H-LUs of {p.name}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank: int, world: int, local_rank: int) -> None:
+    import torch
+    import paper_1703_09085_gb300 as g
+    from paper_1703_09085_gb300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    p = WORKLOADS[args.workload]()
+    coords, csr = p.coords(), p.matrix()
+    ctx = g.Context(local_rank, stream)
+    t0 = time.perf_counter()
+    ct = g.ClusterTree(ctx, coords, p.leaf)
+    bt = g.BlockTree(ctx, ct, ct, p.eta)
+    tree_s = time.perf_counter() - t0
+    pristine = g.HMatrix(ctx, bt, csr)
+    work = g.HMatrix(ctx, bt, csr)
+    flush = torch.empty(int(256 * 2**20) // 4, dtype=torch.float32, device=dev)
+
+    prec = g.HMAT_MIXED if args.precision == "mixed" else g.HMAT_FP64
+
+    def step(precision=prec):
+        work.copy_values_from(pristine)
+        work.lu(p.eps, max_rank=args.max_rank, precision=precision)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    step_ms, kern_ms, flops, truncs, tasks, sched = [], [], [], [], [], []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # L2 flush between timed steps (outside the events)
+        ev0.record(stream)
+        step()
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        st = work.stats()
+        kern_ms.append(1e3 * st["factor_seconds"])
+        flops.append(st["flops"])
+        truncs.append(st["truncations"])
+        tasks.append(st["tasks"])
+        sched.append(st["schedule_seconds"])
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop() if clocks else None
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * sum(truncs) / total_s
+    st = work.stats()
+
+    # end to end through the public API with host buffers: CSR -> device,
+    # factorisation, ranks back to the host, every step
+    h2d = 8 * (csr.rowptr.size + csr.colidx.size + csr.val.size) + 16 * csr.n
+    nblocks = g.lib().hmat_blocktree_size(bt.h)
+    d2h = 8 * nblocks
+    e2e_times = []
+    for i in range(1 + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        H = g.HMatrix(ctx, bt, csr)
+        H.lu(p.eps, max_rank=args.max_rank, precision=prec)
+        H.ranks()
+        torch.cuda.synchronize()
+        if i >= 1:
+            e2e_times.append(time.perf_counter() - t0)
+        del H
+    e2e_s = sum(e2e_times)
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * sum(truncs) / e2e_s
+
+    if rank != 0:
+        return
+    # preconditioner quality of the last factorisation (power iteration with the GPU solves)
+    perr = precond_error(g, work, ct, csr, p)
+    types = {name: {"count": st["type_count"][i], "cta_s": st["type_seconds"][i]}
+             for i, name in enumerate(TASK_NAMES) if st["type_count"][i]}
+    # the plain FP64 accumulated form on the same GPU, same matrix: the comparator
+    fp64 = None
+    if args.precision == "mixed" and not args.no_fp64:
+        ev0.record(stream)
+        step(g.HMAT_FP64)
+        ev1.record(stream)
+        ev1.synchronize()
+        s64 = work.stats()
+        fp64 = {"setup_s": ev0.elapsed_time(ev1) / 1e3, "truncations": s64["truncations"],
+                "value": s64["truncations"] / (ev0.elapsed_time(ev1) / 1e3),
+                "precond_error": precond_error(g, work, ct, csr, p),
+                "kernel_s": s64["factor_seconds"], "flops": s64["flops"]}
+        fp64["speedup_of_chosen_form"] = fp64["setup_s"] / (statistics.mean(step_ms) / 1e3)
+    peaks = measured_peaks()
+    avg_kern_s = statistics.mean(kern_ms) / 1e3
+    achieved = statistics.mean(flops) / avg_kern_s / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f64+f32sketch", "data": "synthetic",
+        "config": {"workload": p.name, "n": p.n, "leaf": p.leaf, "eta": p.eta, "eps": p.eps,
+                   "precision": args.precision,
+                   "max_rank": args.max_rank or 64, "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": f"replicas{world}"},
+        "setup_s": statistics.mean(step_ms) / 1e3,
+        "truncations_per_step": int(statistics.mean(truncs)),
+        "tasks_per_step": int(statistics.mean(tasks)),
+        "schedule_s": statistics.mean(sched),
+        "tree_build_s": tree_s,
+        "precond_error": perr,
+        "randomised_truncations": st["rand_truncations"], "randomised_fallbacks": st["rand_fallbacks"],
+        "plain_fp64": fp64,
+        "task_types": types,
+        "critical_path_tasks": st["levels"],
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "exec_tasks", "kernel_ms": statistics.mean(kern_ms),
+                     "flops_per_launch": statistics.mean(flops),
+                     "peak_note": "FP64 nominal (no measured FP64 peak in MEASURED_PEAKS.json)"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": 1e3 * e2e_s / args.steps},
+        "clocks": clk,
+        "device_bytes": st["device_bytes"],
+        "peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")},
+    }
+    if world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_sample(args.workload)
+    print(json.dumps(line), flush=True)
+
+
+def precond_error(g, H, ct, csr, p, maxit=50, rtol=1e-3) -> float:
+    import torch
+    perm = ct.perm()
+    v = hs.start_vector(p.n, 0)[perm]
+    v = v / np.linalg.norm(v)
+
+    def Ap(x):
+        y = np.zeros(p.n)
+        y[perm] = x
+        return csr.matvec(y)[perm]
+
+    def solve(b, trans):
+        t = torch.from_numpy(b.copy()).cuda()
+        H.solve(t, trans=trans)
+        return t.cpu().numpy()
+
+    est = 0.0
+    for it in range(maxit):
+        w = v - solve(Ap(v), False)
+        new = float(np.linalg.norm(w))
+        z = w - Ap(solve(w, True))
+        done = it > 0 and abs(new - est) <= rtol * new
+        est = new
+        nz = np.linalg.norm(z)
+        if nz == 0 or done:
+            break
+        v = z / nz
+    return est
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="laplace3d_32", choices=sorted(WORKLOADS))
+    ap.add_argument("--max-rank", type=int, default=0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparator")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

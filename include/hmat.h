@@ -75,10 +75,19 @@ typedef struct {
   double mean_rank;
   int64_t tasks;          /* device tasks of the last hmat_lu schedule          */
   int64_t truncations;    /* rank-revealing factorisations of the last hmat_lu  */
+  double flops;           /* FP64 operations counted by the tasks of the last hmat_lu */
   double factor_seconds;  /* device time of the last hmat_lu numeric phase      */
   double schedule_seconds;/* host time of the last hmat_lu symbolic phase       */
   int64_t device_bytes;   /* device memory held by the H-matrix and its arena   */
   int status;             /* device status word of the last hmat_lu             */
+  int64_t levels;         /* longest dependency chain of the schedule (tasks)   */
+  double critical_flops;  /* estimated flops on the longest dependency chain    */
+  double est_flops;       /* estimated flops of all tasks (static ranks)        */
+  double type_seconds[16];/* summed CTA time per task type of the last hmat_lu  */
+  int64_t type_count[16]; /* tasks run per task type                            */
+  double wait_seconds;    /* summed CTA time waiting on predecessors            */
+  int64_t rand_truncations; /* truncations done by the randomised path (MIXED)  */
+  int64_t rand_fallbacks;   /* randomised attempts that fell back to QR + SVD   */
 } hmat_stats;
 
 /* Message of the last failure on this thread, copied into buf (NUL-terminated,
@@ -129,6 +138,11 @@ hmat_status hmat_create_from_csr(hmat_ctx* ctx, const hmat_btree* bt, int64_t n,
                                  const int64_t* colidx, const double* val, hmat** out);
 hmat_status hmat_destroy(hmat* H);
 
+/* dst <- src, leaf values and ranks, for two H-matrices created on the same
+ * block tree (device-to-device copy on the context stream).  Lets a caller
+ * keep an unfactored matrix and factor fresh copies of it. */
+hmat_status hmat_copy_values(hmat_ctx* ctx, hmat* dst, const hmat* src);
+
 /* Dense copy of H in the permuted ordering into out (device, n x n, ld n). */
 hmat_status hmat_to_dense(hmat_ctx* ctx, const hmat* H, double* out);
 
@@ -149,6 +163,13 @@ hmat_status hmat_addeval(hmat_ctx* ctx, const hmat* H, double alpha, int trans, 
  * leaf LU.  Returns the device status (HMAT_ERR_SINGULAR, _RANK, _TIMEOUT,
  * _NONFINITE) after synchronising the stream. */
 hmat_status hmat_lu(hmat_ctx* ctx, hmat* H, const hmat_opts* opts);
+
+/* Host-only analysis of the schedule hmat_lu would run for this matrix (no
+ * device is touched): fills tasks, levels (longest dependency chain),
+ * critical_flops / est_flops (static estimates with rank 8 for unknown
+ * ranks), schedule_seconds and the workspace size in device_bytes. */
+hmat_status hmat_analyze_lu(const hmat_btree* bt, int64_t n, const int64_t* rowptr, const int64_t* colidx,
+                            const double* val, const hmat_opts* opts, hmat_stats* out);
 
 /* B <- (LU)^{-1} B (trans = 0) or (LU)^{-T} B (trans = 1) with the factors of
  * hmat_lu; B: device, n x nrhs, leading dimension ldb, permuted ordering. */

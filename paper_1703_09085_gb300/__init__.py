@@ -34,7 +34,8 @@ EXPORTS = ["hmat_last_error", "hmat_ctx_create", "hmat_ctx_destroy", "hmat_clust
            "hmat_clustertree_perm", "hmat_clustertree_size", "hmat_clustertree_nodes", "hmat_ctree_destroy",
            "hmat_blocktree_build", "hmat_blocktree_size", "hmat_blocktree_nodes", "hmat_btree_destroy",
            "hmat_create_from_csr", "hmat_destroy", "hmat_to_dense", "hmat_addeval", "hmat_lu", "hmat_solve",
-           "trunc_lowrank", "trunc_lowrank_batched", "hmat_stats_get", "hmat_ranks"]
+           "trunc_lowrank", "trunc_lowrank_batched", "hmat_stats_get", "hmat_ranks", "hmat_copy_values",
+           "hmat_analyze_lu"]
 
 
 class HmatError(RuntimeError):
@@ -51,11 +52,20 @@ class Opts(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("blocks", ctypes.c_int64), ("dense_leaves", ctypes.c_int64),
                 ("lowrank_leaves", ctypes.c_int64), ("max_rank", ctypes.c_int64), ("mean_rank", ctypes.c_double),
-                ("tasks", ctypes.c_int64), ("truncations", ctypes.c_int64), ("factor_seconds", ctypes.c_double),
-                ("schedule_seconds", ctypes.c_double), ("device_bytes", ctypes.c_int64), ("status", ctypes.c_int)]
+                ("tasks", ctypes.c_int64), ("truncations", ctypes.c_int64), ("flops", ctypes.c_double),
+                ("factor_seconds", ctypes.c_double),
+                ("schedule_seconds", ctypes.c_double), ("device_bytes", ctypes.c_int64), ("status", ctypes.c_int),
+                ("levels", ctypes.c_int64), ("critical_flops", ctypes.c_double), ("est_flops", ctypes.c_double),
+                ("type_seconds", ctypes.c_double * 16), ("type_count", ctypes.c_int64 * 16),
+                ("wait_seconds", ctypes.c_double), ("rand_truncations", ctypes.c_int64),
+                ("rand_fallbacks", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        d = {}
+        for f, _ in self._fields_:
+            v = getattr(self, f)
+            d[f] = list(v) if f in ("type_seconds", "type_count") else v
+        return d
 
 
 def lib():
@@ -188,6 +198,9 @@ class HMatrix:
             lib().hmat_destroy(self.h)
             self.h = None
 
+    def copy_values_from(self, src: "HMatrix"):
+        _check(lib().hmat_copy_values(self.ctx.h, self.h, src.h))
+
     def lu(self, eps: float, max_rank: int = 0, precision: int = HMAT_FP64, spin_limit: int = 0):
         o = Opts(eps, max_rank, precision, spin_limit)
         _check(lib().hmat_lu(self.ctx.h, self.h, ctypes.byref(o)))
@@ -214,6 +227,18 @@ class HMatrix:
         r = np.zeros(lib().hmat_blocktree_size(self.bt.h), np.int64)
         _check(lib().hmat_ranks(self.h, _hp(r, I64P)))
         return r
+
+
+def analyze_lu(bt: BlockTree, csr, eps: float = 0.0, max_rank: int = 0) -> dict:
+    """Host-only analysis of the H-LU schedule (hmat_analyze_lu)."""
+    rp = np.ascontiguousarray(csr.rowptr, np.int64)
+    ci = np.ascontiguousarray(csr.colidx, np.int64)
+    va = np.ascontiguousarray(csr.val, np.float64)
+    o = Opts(eps, max_rank, HMAT_FP64, 0)
+    s = Stats()
+    _check(lib().hmat_analyze_lu(bt.h, ctypes.c_int64(csr.n), _hp(rp, I64P), _hp(ci, I64P), _hp(va, F64P),
+                                 ctypes.byref(o), ctypes.byref(s)))
+    return s.as_dict()
 
 
 def trunc_lowrank(ctx: Context, U, V, eps: float) -> int:

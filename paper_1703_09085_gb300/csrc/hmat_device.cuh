@@ -155,15 +155,23 @@ __device__ void cta_apply_q(const double* V, int ldv, int rows, int q, const dou
 // Vr (c x c, ld c): on return J's columns are mutually orthogonal and
 // J_in Vr = J_out.
 // ---------------------------------------------------------------------------
+// s.ivals[2] receives the sweeps run, s.ivals[3] the rotations applied.
 __device__ void cta_jacobi(double* J, int p, int c, double* Vr, Smem& s) {
   int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int idx = tid; idx < c * c; idx += HM_THREADS) Vr[idx] = (idx % c == idx / c) ? 1.0 : 0.0;
+  if (tid == 0) {
+    s.ivals[2] = 0;
+    s.ivals[3] = 0;
+  }
   __syncthreads();
   if (c < 2) return;
   int N = c + (c & 1);
   const double tol = 1e-15;
   for (int sweep = 0; sweep < 60; ++sweep) {
-    if (tid == 0) s.ivals[0] = 0;
+    if (tid == 0) {
+      s.ivals[0] = 0;
+      s.ivals[2] += 1;
+    }
     __syncthreads();
     for (int r = 0; r < N - 1; ++r) {
       for (int k = warp; k < N / 2; k += HM_WARPS) {
@@ -211,7 +219,10 @@ __device__ void cta_jacobi(double* J, int p, int c, double* Vr, Smem& s) {
           va[i] = cs * x - sn * y;
           vb[i] = sn * x + cs * y;
         }
-        if (lane == 0) s.ivals[0] = 1;
+        if (lane == 0) {
+          s.ivals[0] = 1;
+          atomicAdd(&s.ivals[3], 1);
+        }
       }
       __syncthreads();
     }
@@ -293,8 +304,13 @@ struct TruncIn {
   double* Jg;       // global fallback for the Jacobi core (p*c + c*c doubles)
 };
 
+// Householder QR flops of a rows x cols matrix (Golub & Van Loan count).
+__device__ __forceinline__ double qr_flops(double rows, double cols) {
+  return rows >= cols ? 2.0 * cols * cols * (rows - cols / 3.0) : 2.0 * rows * rows * (cols - rows / 3.0);
+}
+
 __device__ int trunc_core(const TruncIn& in, double eps, int cap, double* U, int ldu, double* V, int ldv,
-                          int* status, Smem& s) {
+                          int* status, Smem& s, double* flops = nullptr) {
   int tid = threadIdx.x;
   int m = in.m;
   int q[2] = {0, 0};
@@ -348,6 +364,19 @@ __device__ int trunc_core(const TruncIn& in, double eps, int cap, double* U, int
   cta_jacobi(J, p, c, Vr, s);
   cta_sort_sigma(J, p, c, s);
   int k = cta_choose_rank(c, eps, s);
+  if (flops && tid == 0) {
+    double f = 0.0;
+    for (int j = 0; j < in.nb; ++j) {
+      f += qr_flops(in.n[j], in.k[j]);                       // QR of the stacked B factors
+      f += (double)m * q[j] * (2.0 * in.k[j] - q[j]);        // Ahat = A R^T (triangular)
+      f += 4.0 * in.n[j] * q[j] * (k < cap ? k : cap);       // V = Q_B (Vhat Sigma)
+    }
+    f += qr_flops(m, qs);                                    // QR of Ahat
+    f += (double)s.ivals[2] * 0.5 * c * (c - 1) * 6.0 * p;   // Jacobi: column products per sweep
+    f += (double)s.ivals[3] * 6.0 * (p + c);                 // Jacobi: rotations
+    f += 4.0 * m * qa * (k < cap ? k : cap);                 // U = Q_A U_c
+    *flops += f;
+  }
   if (k > cap) {
     if (tid == 0) set_status(status, DS_RANK);
     k = cap;
@@ -392,6 +421,230 @@ __device__ int trunc_core(const TruncIn& in, double eps, int cap, double* U, int
     voff += in.n[j];
   }
   return k;
+}
+
+// ---------------------------------------------------------------------------
+// Randomised truncation: the range finder of Halko, Martinsson and Tropp
+// (SIAM Review 2011, Alg. 4.1) with an exact a-posteriori check of the
+// truncation rule.  M (m x n) is given explicitly (Md, ld m) or as SA SB^T
+// (m x l, n x l).  For a sketch width r:
+//   Y = M Omega            (Rademacher Omega, FP32 -- only picks a subspace)
+//   Q = orth(Y)            (FP64 Householder, explicit m x r)
+//   J = M^T Q = (Q^T M)^T  (FP64)
+//   one-sided Jacobi on J  -> singular triplets of Q^T M
+//   res^2 = ||M||_F^2 - ||Q^T M||_F^2  (FP64, exact for orthonormal Q)
+// The rank k is the smallest with res^2 + sum_{i>k} sigma_i^2 <= eps^2 ||M||_F^2,
+// so the result meets the same Frobenius rule as the exact truncation (its
+// rank can exceed the optimal one by what the subspace missed).  If even
+// k = r fails, r doubles up to rmax; then the caller falls back to the exact
+// QR + SVD path.  C = Q Vr(:, order), D = J(:, order) as in Fig. rkadd.
+// ---------------------------------------------------------------------------
+#define HM_RMAX 32
+
+struct RandIn {
+  int m, n, l;
+  const double* Md;   // explicit M (ld m) or nullptr
+  const double* SA;   // m x l (ld m)
+  const double* SB;   // n x l (ld n)
+  double* ws;         // rand_ws_doubles(m, n, l) doubles
+  uint64_t seed;
+  int r0;             // first sketch width
+};
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ int trunc_rand(const RandIn& in, double eps, int cap, double* U, int ldu, double* V, int ldv,
+                          int* status, Smem& s, double* flops, int* ok) {
+  int tid = threadIdx.x;
+  int m = in.m, n = in.n, l = in.l;
+  bool factored = (in.Md == nullptr);
+  int rmax = HM_RMAX;
+  if (rmax > m) rmax = m;
+  if (rmax > n) rmax = n;
+  if (factored && rmax > l) rmax = l;
+  double* Y = in.ws;                          // m x RMAX (sketch, then reflectors)
+  double* Qx = Y + (int64_t)m * HM_RMAX;      // m x RMAX
+  double* J = Qx + (int64_t)m * HM_RMAX;      // n x RMAX
+  double* Vr = J + (int64_t)n * HM_RMAX;      // RMAX x RMAX
+  uint32_t* Om = (uint32_t*)(Vr + HM_RMAX * HM_RMAX);  // n sign words
+  double* G = Vr + HM_RMAX * HM_RMAX + (n + 1) / 2 + 1;  // 2 l x l Grams, or T (l x RMAX floats)
+  double f = 0.0;
+  // ||M||_F^2
+  double total;
+  if (!factored) {
+    double acc = 0.0;
+    for (int64_t idx = tid; idx < (int64_t)m * n; idx += HM_THREADS) {
+      double x = in.Md[idx];
+      acc += x * x;
+    }
+    total = block_sum(acc, s);
+    f += 2.0 * m * n;
+  } else {
+    double* GA = G;
+    double* GB = G + (int64_t)l * l;
+    for (int idx = tid; idx < l * l; idx += HM_THREADS) {
+      int i = idx % l, j = idx / l;
+      double a = 0.0, b = 0.0;
+      if (i <= j) {
+        for (int r = 0; r < m; ++r) a += in.SA[(int64_t)i * m + r] * in.SA[(int64_t)j * m + r];
+        for (int r = 0; r < n; ++r) b += in.SB[(int64_t)i * n + r] * in.SB[(int64_t)j * n + r];
+      }
+      GA[idx] = a;
+      GB[idx] = b;
+    }
+    __syncthreads();
+    double acc = 0.0;
+    for (int idx = tid; idx < l * l; idx += HM_THREADS) {
+      int i = idx % l, j = idx / l;
+      if (i <= j) acc += (i == j ? 1.0 : 2.0) * GA[idx] * GB[idx];
+    }
+    total = block_sum(acc, s);
+    f += (double)(m + n) * l * (l + 1);
+  }
+  double bound = eps * eps * total;
+  if (total == 0.0) {
+    *ok = 1;
+    return 0;
+  }
+  int r = in.r0 < 2 ? 2 : in.r0;
+  if (r > rmax) r = rmax;
+  for (;;) {
+    // Rademacher signs, one 32-bit word per row of Omega
+    for (int i = tid; i < n; i += HM_THREADS) Om[i] = (uint32_t)mix64(in.seed ^ ((uint64_t)i * 0xD1B54A32D192ED03ull));
+    __syncthreads();
+    // sketch Y = M Omega in FP32
+    if (!factored) {
+      for (int idx = tid; idx < m * r; idx += HM_THREADS) {
+        int i = idx % m, j = idx / m;
+        float acc = 0.f;
+        for (int c = 0; c < n; ++c) {
+          float x = (float)in.Md[(int64_t)c * m + i];
+          acc += ((Om[c] >> j) & 1u) ? x : -x;
+        }
+        Y[(int64_t)j * m + i] = (double)acc;
+      }
+    } else {
+      float* T = (float*)G;  // l x r, reuses the Gram space (no longer needed)
+      for (int idx = tid; idx < l * r; idx += HM_THREADS) {
+        int i = idx % l, j = idx / l;
+        float acc = 0.f;
+        for (int c = 0; c < n; ++c) {
+          float x = (float)in.SB[(int64_t)i * n + c];
+          acc += ((Om[c] >> j) & 1u) ? x : -x;
+        }
+        T[idx] = acc;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < m * r; idx += HM_THREADS) {
+        int i = idx % m, j = idx / m;
+        float acc = 0.f;
+        for (int c = 0; c < l; ++c) acc += (float)in.SA[(int64_t)c * m + i] * T[(int64_t)j * l + c];
+        Y[(int64_t)j * m + i] = (double)acc;
+      }
+    }
+    __syncthreads();
+    // Q = orth(Y): Householder, then explicit Q = P_0 ... P_{r-1} [I; 0]
+    int rr = r < m ? r : m;
+    cta_qr(Y, m, m, r, s.tauA, s.rdiagA, s);
+    for (int idx = tid; idx < m * rr; idx += HM_THREADS) Qx[idx] = (idx % m == idx / m) ? 1.0 : 0.0;
+    __syncthreads();
+    cta_apply_q(Y, m, m, rr, s.tauA, Qx, m, rr);
+    // J = M^T Q (n x rr) in FP64
+    if (!factored) {
+      for (int idx = tid; idx < n * rr; idx += HM_THREADS) {
+        int c = idx % n, j = idx / n;
+        double acc = 0.0;
+        for (int i = 0; i < m; ++i) acc += in.Md[(int64_t)c * m + i] * Qx[(int64_t)j * m + i];
+        J[idx] = acc;
+      }
+      f += 2.0 * m * n * rr;
+    } else {
+      double* P = G;  // rr x l
+      for (int idx = tid; idx < rr * l; idx += HM_THREADS) {
+        int j = idx % rr, c = idx / rr;
+        double acc = 0.0;
+        for (int i = 0; i < m; ++i) acc += Qx[(int64_t)j * m + i] * in.SA[(int64_t)c * m + i];
+        P[idx] = acc;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < n * rr; idx += HM_THREADS) {
+        int c = idx % n, j = idx / n;
+        double acc = 0.0;
+        for (int i = 0; i < l; ++i) acc += in.SB[(int64_t)i * n + c] * P[(int64_t)i * rr + j];
+        J[idx] = acc;
+      }
+      f += 2.0 * (m + n) * (double)l * rr;
+    }
+    __syncthreads();
+    cta_jacobi(J, n, rr, Vr, s);
+    cta_sort_sigma(J, n, rr, s);
+    f += qr_flops(m, r) + 4.0 * m * rr * rr;
+    f += (double)s.ivals[2] * 0.5 * rr * (rr - 1) * 6.0 * n + (double)s.ivals[3] * 6.0 * (n + rr);
+    if (tid == 0) {
+      double sum = 0.0;
+      for (int i = 0; i < rr; ++i) sum += s.sigma[i] * s.sigma[i];
+      double res2 = total - sum;
+      if (res2 < 0.0) res2 = 0.0;
+      int k = -1;
+      if (res2 <= bound) {
+        double tail = res2;
+        k = rr;
+        while (k > 0) {
+          double x = s.sigma[s.order[k - 1]];
+          if (tail + x * x <= bound) {
+            tail += x * x;
+            --k;
+          } else {
+            break;
+          }
+        }
+      }
+      s.ivals[4] = k;
+    }
+    __syncthreads();
+    int k = s.ivals[4];
+    __syncthreads();
+    if (k < 0) {
+      if (r >= rmax) {
+        if (flops && tid == 0) *flops += f;
+        *ok = 0;
+        return 0;
+      }
+      r = 2 * r > rmax ? rmax : 2 * r;
+      continue;
+    }
+    if (k > cap) {
+      if (tid == 0) set_status(status, DS_RANK);
+      k = cap;
+    }
+    for (int idx = tid; idx < m * k; idx += HM_THREADS) {
+      int i = idx % m, jj = idx / m;
+      int col = s.order[jj];
+      double acc = 0.0;
+      for (int j = 0; j < rr; ++j) acc += Qx[(int64_t)j * m + i] * Vr[(int64_t)col * rr + j];
+      U[(int64_t)jj * ldu + i] = acc;
+    }
+    for (int idx = tid; idx < n * k; idx += HM_THREADS) {
+      int i = idx % n, jj = idx / n;
+      V[(int64_t)jj * ldv + i] = J[(int64_t)s.order[jj] * n + i];
+    }
+    f += 2.0 * m * rr * k;
+    if (flops && tid == 0) *flops += f;
+    *ok = 1;
+    return k;
+  }
+}
+
+// Doubles of scratch trunc_rand needs.
+__host__ __device__ inline int64_t rand_ws_doubles(int64_t m, int64_t n, int64_t l) {
+  int64_t g = 2 * l * l;
+  if (g < l * HM_RMAX) g = l * HM_RMAX;
+  return 2 * m * HM_RMAX + n * HM_RMAX + HM_RMAX * HM_RMAX + (n + 1) / 2 + 1 + g + 64;
 }
 
 // ---------------------------------------------------------------------------

@@ -295,6 +295,42 @@ struct Sched {
   std::vector<std::deque<int>> freelist = std::vector<std::deque<int>>(64);
   int64_t ws_top = 0;
   std::vector<int32_t> depbuf;
+  std::vector<int32_t> level;   // longest chain of predecessors (ASAP level)
+  std::vector<double> cpath;    // estimated flops of the longest chain ending here
+  double est_total = 0.0;
+
+  // Rough static cost of a task (ranks unknown on the host: a typical rank 8).
+  double est_cost(const HTask& t) const {
+    auto w = [](int x) { return x >= 0 ? (double)x : 8.0; };
+    switch (t.type) {
+      case T_LU: return 2.0 / 3.0 * t.m * (double)t.m * t.m;
+      case T_TRSM: return (double)t.m * t.m * w(t.wa);
+      case T_GEMM: return 2.0 * t.m * (double)t.n * w(t.wa);
+      case T_ADD: case T_COPY: case T_ZERO: return (double)t.m * t.n;
+      case T_HMV: {
+        double f = 0.0;
+        for (int i = 0; i < t.list_len; ++i) {
+          const LeafRef& L = leaves[(size_t)(t.list_begin + i)];
+          f += L.kind == 1 ? 2.0 * L.rows * L.cols * w(t.wa) : 16.0 * (L.rows + L.cols) * w(t.wa);
+        }
+        return f;
+      }
+      case T_DENSIFY: {
+        double f = 0.0;
+        for (int i = 0; i < t.list_len; ++i) f += (double)leaves[(size_t)(t.list_begin + i)].rows * leaves[(size_t)(t.list_begin + i)].cols;
+        return f;
+      }
+      case T_RKADD: {
+        double l = (t.flags & F_A_IDENT ? t.m : t.flags & F_B_IDENT ? t.n : w(t.wa)) + (t.rin >= 0 ? 8.0 : 0.0);
+        return 4.0 * (t.m + t.n) * l * l + 30.0 * l * l * l;
+      }
+      case T_ROWMERGE: {
+        double l = w(t.wa) + w(t.wb);
+        return 4.0 * (t.m + t.p + t.q) * l * l + 30.0 * l * l * l;
+      }
+      default: return 0.0;
+    }
+  }
 
   int new_obj() {
     objs.emplace_back();
@@ -349,6 +385,16 @@ struct Sched {
     depbuf.erase(std::unique(depbuf.begin(), depbuf.end()), depbuf.end());
     dep_idx.insert(dep_idx.end(), depbuf.begin(), depbuf.end());
     dep_ptr.push_back((int64_t)dep_idx.size());
+    int32_t lv = 0;
+    double cp = 0.0;
+    for (int32_t d : depbuf) {
+      lv = std::max(lv, level[(size_t)d] + 1);
+      cp = std::max(cp, cpath[(size_t)d]);
+    }
+    level.push_back(lv);
+    double c = est_cost(t);
+    cpath.push_back(cp + c);
+    est_total += c;
     for (int r : reads) {
       Obj& o = objs[(size_t)r];
       if (o.readers.empty() || o.readers.back() != id) o.readers.push_back(id);
@@ -360,6 +406,49 @@ struct Sched {
     }
     tasks.push_back(t);
     return id;
+  }
+
+  // Reorder the list by ASAP level (stable): still a topological order, and
+  // tasks that can run together sit next to each other, so the in-order
+  // dequeue of the executor sees the available parallelism.
+  void order_by_level() {
+    size_t n = tasks.size();
+    std::vector<int32_t> ord(n);
+    for (size_t i = 0; i < n; ++i) ord[i] = (int32_t)i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return level[(size_t)a] < level[(size_t)b]; });
+    std::vector<int32_t> pos(n);
+    for (size_t i = 0; i < n; ++i) pos[(size_t)ord[i]] = (int32_t)i;
+    std::vector<HTask> t2(n);
+    std::vector<int64_t> p2(n + 1, 0);
+    std::vector<int32_t> d2;
+    d2.reserve(dep_idx.size());
+    for (size_t i = 0; i < n; ++i) {
+      int32_t o = ord[i];
+      t2[i] = tasks[(size_t)o];
+      for (int64_t k = dep_ptr[(size_t)o]; k < dep_ptr[(size_t)o + 1]; ++k) d2.push_back(pos[(size_t)dep_idx[(size_t)k]]);
+      p2[i + 1] = (int64_t)d2.size();
+    }
+    tasks.swap(t2);
+    dep_ptr.swap(p2);
+    dep_idx.swap(d2);
+    std::vector<int32_t> l2(n);
+    std::vector<double> c2(n);
+    for (size_t i = 0; i < n; ++i) {
+      l2[i] = level[(size_t)ord[i]];
+      c2[i] = cpath[(size_t)ord[i]];
+    }
+    level.swap(l2);
+    cpath.swap(c2);
+  }
+  int32_t levels() const {
+    int32_t m = 0;
+    for (int32_t l : level) m = std::max(m, l + 1);
+    return m;
+  }
+  double critical_flops() const {
+    double m = 0.0;
+    for (double c : cpath) m = std::max(m, c);
+    return m;
   }
 };
 
@@ -381,6 +470,16 @@ HTask blank(int type) {
 }
 
 int64_t rk_ws(int64_t m, int64_t n, int64_t l) { return (2 * m + n) * l + 2 * l * l + 64; }
+
+// Extra scratch of the randomised truncation (explicit M when it is the
+// smaller form, sketch, Q, J, rotations, signs, Grams) -- the device layout of
+// task_rkadd / trunc_rand.
+const int64_t RMAX = 32;
+int64_t rand_ws(int64_t m, int64_t n, int64_t l) {
+  int64_t g = std::max(2 * l * l, l * RMAX);
+  int64_t mx = (m * n <= (m + n) * l) ? m * n : 0;
+  return mx + 2 * m * RMAX + n * RMAX + RMAX * RMAX + (n + 1) / 2 + 1 + g + 64;
+}
 
 // ===========================================================================
 // Symbolic arithmetic: the paper's procedures emitting tasks
@@ -447,6 +546,7 @@ struct Sym {
   const hmat_ctree& RT;
   const hmat_ctree& CT;
   int64_t maxrank;
+  bool mixed = false;
   std::vector<const hmat*> mats;
   std::vector<int> objbase;
 
@@ -770,7 +870,7 @@ struct Sym {
     int64_t l = (int64_t)P.wcap + (rin >= 0 ? Z.wmax : 0);
     if (l > HM_LMAX_HOST) throw HmError(HMAT_ERR_RANK, "stacked width exceeds the truncation limit");
     int inmax = Z.wmax;
-    int ws = S.alloc(rk_ws(m, n, l));
+    int ws = S.alloc(rk_ws(m, n, l) + (mixed ? rand_ws(m, n, l) : 0));
     t.ws = S.chunk_loc(ws);
     std::vector<int> reads = P.objs;
     if (rin >= 0 && inobj >= 0 && inobj != Z.obj) reads.push_back(inobj);
@@ -1266,10 +1366,13 @@ struct RunResult {
   int status = 0;
   double ms = 0.0;
   unsigned long long truncations = 0;
+  double flops = 0.0;
+  unsigned long long type_ns[16] = {0}, type_cnt[16] = {0}, wait_ns = 0;
+  unsigned long long rand_ok = 0, rand_fail = 0;
 };
 
 RunResult run_tasks(hmat_ctx* ctx, const Sched& S, double* hbase, int* ranks, double eps, int64_t spin_limit,
-                    double* ext0, double* ext1) {
+                    double* ext0, double* ext1, bool mixed = false) {
   RunResult rr;
   if (S.tasks.empty()) return rr;
   cudaStream_t st = ctx->stream;
@@ -1281,8 +1384,8 @@ RunResult run_tasks(hmat_ctx* ctx, const Sched& S, double* hbase, int* ranks, do
   ddone.alloc(S.tasks.size() * sizeof(int));
   HM_CUDA(cudaMemsetAsync(ddone.p, 0, S.tasks.size() * sizeof(int), st));
   dws.alloc((size_t)std::max<int64_t>(S.ws_top, 1) * sizeof(double));
-  dmisc.alloc(64);
-  HM_CUDA(cudaMemsetAsync(dmisc.p, 0, 64, st));
+  dmisc.alloc(64 * 8);
+  HM_CUDA(cudaMemsetAsync(dmisc.p, 0, 64 * 8, st));
   ExecEnv e;
   e.hbase = hbase;
   e.wsbase = dws.as<double>();
@@ -1296,9 +1399,16 @@ RunResult run_tasks(hmat_ctx* ctx, const Sched& S, double* hbase, int* ranks, do
   e.leaves = dleaves.as<LeafRef>();
   e.done = ddone.as<int>();
   e.head = (unsigned long long*)dmisc.p;
-  e.counters = (unsigned long long*)dmisc.p + 1;
+  e.counters = (unsigned long long*)dmisc.p + 44;
   e.status = (int*)((unsigned long long*)dmisc.p + 2);
+  e.flops = (double*)((unsigned long long*)dmisc.p + 3);
+  e.type_ns = (unsigned long long*)dmisc.p + 8;
+  e.type_cnt = (unsigned long long*)dmisc.p + 24;
+  e.wait_ns = (unsigned long long*)dmisc.p + 40;
   e.eps = eps;
+  e.mixed = mixed ? 1 : 0;
+  e.rand_min_l = 24;
+  e.seed = 0x5EEDull;
   e.spin_iters = spin_limit > 0 ? spin_limit : (1ll << 28);
   e.spin_ns = 20ull * 1000000000ull;
   int grid = ctx->num_sms * ctx->blocks_per_sm;
@@ -1308,16 +1418,24 @@ RunResult run_tasks(hmat_ctx* ctx, const Sched& S, double* hbase, int* ranks, do
   HM_CUDA(cudaEventRecord(e0, st));
   HM_CUDA(launch_exec(e, grid, st));
   HM_CUDA(cudaEventRecord(e1, st));
-  unsigned long long misc[3];
+  unsigned long long misc[48];
   HM_CUDA(cudaMemcpyAsync(misc, dmisc.p, sizeof(misc), cudaMemcpyDeviceToHost, st));
+  for (int i = 0; i < 16; ++i) {
+    rr.type_ns[i] = misc[8 + i];
+    rr.type_cnt[i] = misc[24 + i];
+  }
+  rr.wait_ns = misc[40];
   HM_CUDA(cudaStreamSynchronize(st));
   float ms = 0.f;
   HM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   rr.ms = ms;
-  rr.truncations = misc[1];
+  rr.truncations = misc[44];
+  rr.rand_ok = misc[45];
+  rr.rand_fail = misc[46];
   rr.status = (int)(misc[2] & 0xffffffffu);
+  std::memcpy(&rr.flops, &misc[3], sizeof(double));
   return rr;
 }
 
@@ -1443,14 +1561,13 @@ hmat_status hmat_btree_destroy(hmat_btree* bt) {
   return guarded([&] { delete bt; });
 }
 
-hmat_status hmat_create_from_csr(hmat_ctx* ctx, const hmat_btree* bt, int64_t n, const int64_t* rowptr,
-                                 const int64_t* colidx, const double* val, hmat** out) {
-  return guarded([&] {
-    check_ctx(ctx);
-    require(bt && rowptr && colidx && val && out, "null argument");
-    require((int64_t)bt->R->perm.size() == n && (int64_t)bt->C->perm.size() == n, "csr: size does not match the trees");
-    std::unique_ptr<hmat> H(new hmat());
-    H->ctx = ctx;
+}  // extern "C"
+
+namespace {
+// Host metadata of an H-matrix: storage layout of every leaf, rank slots, and
+// which dense leaves hold entries of the sparse matrix.
+std::vector<DenseLeafDesc> layout_from_csr(hmat* H, const hmat_btree* bt, int64_t n, const int64_t* rowptr,
+                                           const int64_t* colidx, const double* val) {
     H->bt = bt;
     H->n = n;
     size_t nb = bt->nodes.size();
@@ -1485,16 +1602,9 @@ hmat_status hmat_create_from_csr(hmat_ctx* ctx, const hmat_btree* bt, int64_t n,
       }
     }
     H->store_doubles = off;
-    cudaStream_t st = ctx->stream;
-    H->store.alloc((size_t)std::max<int64_t>(off, 1) * sizeof(double));
-    HM_CUDA(cudaMemsetAsync(H->store.p, 0, (size_t)std::max<int64_t>(off, 1) * sizeof(double), st));
-    H->ranks.alloc((size_t)std::max(H->nslots, 1) * sizeof(int));
-    HM_CUDA(cudaMemsetAsync(H->ranks.p, 0, (size_t)std::max(H->nslots, 1) * sizeof(int), st));
-    // host: inverse permutation, statically nonzero dense leaves
     const std::vector<int64_t>& perm = bt->R->perm;
     std::vector<int64_t> iperm((size_t)n);
     for (int64_t i = 0; i < n; ++i) iperm[(size_t)bt->C->perm[(size_t)i]] = i;
-    int64_t nnz = rowptr[n];
     for (size_t b = 0; b < nb; ++b) {
       if (bt->nodes[b].kind != 1) continue;
       const CNodeH& t = H->tc((int)b);
@@ -1512,6 +1622,72 @@ hmat_status hmat_create_from_csr(hmat_ctx* ctx, const hmat_btree* bt, int64_t n,
       }
       H->zero[b] = any ? 0 : 1;
     }
+    H->st.n = n;
+    H->st.blocks = (int64_t)nb;
+    for (size_t b = 0; b < nb; ++b) {
+      if (bt->nodes[b].kind == 1) H->st.dense_leaves++;
+      if (bt->nodes[b].kind == 2) H->st.lowrank_leaves++;
+    }
+    return dl;
+}
+
+// Symbolic H-LU of H into S (ordered by level); returns host seconds.
+double schedule_lu(hmat* H, int64_t max_rank, bool mixed, Sched& S) {
+  auto t0 = std::chrono::steady_clock::now();
+  S.next_slot = H->nslots;
+  Sym sym(S, *H->bt->R, *H->bt->C, max_rank);
+  sym.mixed = mixed;
+  sym.add_matrix(H);
+  SAcc root = sym.acc_new(0, 0);
+  sym.lu(H, 0, root);
+  S.order_by_level();
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+}  // namespace
+
+extern "C" {
+
+hmat_status hmat_analyze_lu(const hmat_btree* bt, int64_t n, const int64_t* rowptr, const int64_t* colidx,
+                            const double* val, const hmat_opts* opts, hmat_stats* out) {
+  return guarded([&] {
+    require(bt && rowptr && colidx && val && out, "null argument");
+    require((int64_t)bt->R->perm.size() == n && (int64_t)bt->C->perm.size() == n, "csr: size does not match the trees");
+    hmat H;
+    layout_from_csr(&H, bt, n, rowptr, colidx, val);
+    int64_t mr = (opts && opts->max_rank > 0) ? std::min<int64_t>(opts->max_rank, H.max_rank) : H.max_rank;
+    Sched S;
+    double secs = schedule_lu(&H, mr, opts && opts->precision == HMAT_MIXED, S);
+    hmat_stats s = H.st;
+    s.tasks = (int64_t)S.tasks.size();
+    s.schedule_seconds = secs;
+    s.levels = S.levels();
+    s.critical_flops = S.critical_flops();
+    s.est_flops = S.est_total;
+    s.device_bytes = H.store_doubles * 8 + S.ws_top * 8;
+    *out = s;
+  });
+}
+
+hmat_status hmat_create_from_csr(hmat_ctx* ctx, const hmat_btree* bt, int64_t n, const int64_t* rowptr,
+                                 const int64_t* colidx, const double* val, hmat** out) {
+  return guarded([&] {
+    check_ctx(ctx);
+    require(bt && rowptr && colidx && val && out, "null argument");
+    require((int64_t)bt->R->perm.size() == n && (int64_t)bt->C->perm.size() == n, "csr: size does not match the trees");
+    std::unique_ptr<hmat> H(new hmat());
+    H->ctx = ctx;
+    std::vector<DenseLeafDesc> dl = layout_from_csr(H.get(), bt, n, rowptr, colidx, val);
+    int64_t off = H->store_doubles;
+    size_t nb = bt->nodes.size();
+    cudaStream_t st = ctx->stream;
+    H->store.alloc((size_t)std::max<int64_t>(off, 1) * sizeof(double));
+    HM_CUDA(cudaMemsetAsync(H->store.p, 0, (size_t)std::max<int64_t>(off, 1) * sizeof(double), st));
+    H->ranks.alloc((size_t)std::max(H->nslots, 1) * sizeof(int));
+    HM_CUDA(cudaMemsetAsync(H->ranks.p, 0, (size_t)std::max(H->nslots, 1) * sizeof(int), st));
+    const std::vector<int64_t>& perm = bt->R->perm;
+    std::vector<int64_t> iperm((size_t)n);
+    for (int64_t i = 0; i < n; ++i) iperm[(size_t)bt->C->perm[(size_t)i]] = i;
+    int64_t nnz = rowptr[n];
     DevBuf drp, dci, dva, dperm, diperm, ddl, dplaced;
     upload(drp, std::vector<int64_t>(rowptr, rowptr + n + 1), st);
     upload(dci, std::vector<int64_t>(colidx, colidx + nnz), st);
@@ -1528,12 +1704,7 @@ hmat_status hmat_create_from_csr(hmat_ctx* ctx, const hmat_btree* bt, int64_t n,
     HM_CUDA(cudaMemcpyAsync(&placed, dplaced.p, sizeof(placed), cudaMemcpyDeviceToHost, st));
     HM_CUDA(cudaStreamSynchronize(st));
     require((int64_t)placed == nnz, "csr: entries inside admissible blocks (rank > 0) are not supported");
-    H->st.n = n;
-    H->st.blocks = (int64_t)nb;
-    for (size_t b = 0; b < nb; ++b) {
-      if (bt->nodes[b].kind == 1) H->st.dense_leaves++;
-      if (bt->nodes[b].kind == 2) H->st.lowrank_leaves++;
-    }
+    (void)nb;
     H->st.device_bytes = (int64_t)(H->store.bytes + H->ranks.bytes);
     *out = H.release();
   });
@@ -1543,6 +1714,18 @@ hmat_status hmat_destroy(hmat* H) {
   return guarded([&] {
     if (H && H->ctx) cudaSetDevice(H->ctx->device);
     delete H;
+  });
+}
+
+hmat_status hmat_copy_values(hmat_ctx* ctx, hmat* dst, const hmat* src) {
+  return guarded([&] {
+    check_ctx(ctx);
+    require(dst && src && dst->bt == src->bt && dst->store_doubles == src->store_doubles, "copy_values: different trees");
+    HM_CUDA(cudaMemcpyAsync(dst->store.p, src->store.p, (size_t)src->store_doubles * sizeof(double),
+                            cudaMemcpyDeviceToDevice, ctx->stream));
+    HM_CUDA(cudaMemcpyAsync(dst->ranks.p, src->ranks.p, (size_t)src->nslots * sizeof(int), cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+    dst->zero = src->zero;
   });
 }
 
@@ -1657,27 +1840,33 @@ hmat_status hmat_lu(hmat_ctx* ctx, hmat* H, const hmat_opts* opts) {
     int64_t mr = (opts && opts->max_rank > 0) ? std::min<int64_t>(opts->max_rank, H->max_rank) : H->max_rank;
     int64_t spin = opts ? opts->spin_limit : 0;
     require(eps >= 0.0, "eps must be >= 0");
-    auto t0 = std::chrono::steady_clock::now();
     Sched S;
-    S.next_slot = H->nslots;
-    Sym sym(S, *H->bt->R, *H->bt->C, mr);
-    sym.add_matrix(H);
-    SAcc root = sym.acc_new(0, 0);
-    sym.lu(H, 0, root);
-    auto t1 = std::chrono::steady_clock::now();
+    bool mixed = opts && opts->precision == HMAT_MIXED;
+    double sched_s = schedule_lu(H, mr, mixed, S);
     // rank slots beyond the leaves' live in a per-call array
     DevBuf allranks((size_t)std::max(S.next_slot, 1) * sizeof(int));
     HM_CUDA(cudaMemcpyAsync(allranks.p, H->ranks.p, (size_t)H->nslots * sizeof(int), cudaMemcpyDeviceToDevice,
                             ctx->stream));
-    RunResult rr = run_tasks(ctx, S, H->store.as<double>(), allranks.as<int>(), eps, spin, nullptr, nullptr);
+    RunResult rr = run_tasks(ctx, S, H->store.as<double>(), allranks.as<int>(), eps, spin, nullptr, nullptr, mixed);
     HM_CUDA(cudaMemcpyAsync(H->ranks.p, allranks.p, (size_t)H->nslots * sizeof(int), cudaMemcpyDeviceToDevice,
                             ctx->stream));
     HM_CUDA(cudaStreamSynchronize(ctx->stream));
     H->st.tasks = (int64_t)S.tasks.size();
     H->st.truncations = (int64_t)rr.truncations;
+    H->st.flops = rr.flops;
+    H->st.rand_truncations = (int64_t)rr.rand_ok;
+    H->st.rand_fallbacks = (int64_t)rr.rand_fail;
+    for (int i = 0; i < 16; ++i) {
+      H->st.type_seconds[i] = rr.type_ns[i] * 1e-9;
+      H->st.type_count[i] = (int64_t)rr.type_cnt[i];
+    }
+    H->st.wait_seconds = rr.wait_ns * 1e-9;
     H->st.factor_seconds = rr.ms * 1e-3;
-    H->st.schedule_seconds = std::chrono::duration<double>(t1 - t0).count();
+    H->st.schedule_seconds = sched_s;
     H->st.status = rr.status;
+    H->st.levels = S.levels();
+    H->st.critical_flops = S.critical_flops();
+    H->st.est_flops = S.est_total;
     H->st.device_bytes = (int64_t)(H->store.bytes + H->ranks.bytes) + S.ws_top * 8;
     if (rr.status) throw HmError(rr.status, "hmat_lu: device status " + std::to_string(rr.status));
   });

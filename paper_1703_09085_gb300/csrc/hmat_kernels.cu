@@ -186,6 +186,57 @@ __device__ void task_rkadd(const ExecEnv& e, const HTask& t, Smem& s) {
     SB[idx] = v;
   }
   __syncthreads();
+  double f = 0.0;
+  if (e.mixed && e.eps > 0.0 && l >= e.rand_min_l) {
+    // Randomised truncation; M explicit when that is the smaller form.
+    double* R = Jg + 2 * (int64_t)l * l;
+    const double* Md = nullptr;
+    if ((int64_t)m * n <= (int64_t)(m + n) * l) {
+      double* Mx = R;
+      R += (int64_t)m * n;
+      for (int idx = threadIdx.x; idx < m * n; idx += HM_THREADS) {
+        int i = idx % m, c = idx / m;
+        double v;
+        if (aid) v = btr ? B[(int64_t)c * t.ldb + i] : B[(int64_t)i * t.ldb + c];   // alpha Bhat^T
+        else if (bid) v = A[(int64_t)c * t.lda + i];                                // alpha Ahat
+        else {
+          v = 0.0;
+          for (int j = 0; j < w; ++j)
+            v += A[(int64_t)j * t.lda + i] * (btr ? B[(int64_t)c * t.ldb + j] : B[(int64_t)j * t.ldb + c]);
+        }
+        v *= t.alpha;
+        for (int j = 0; j < kin; ++j) v += Uin[(int64_t)j * t.ldc + i] * Vin[(int64_t)j * t.ldd + c];
+        Mx[idx] = v;
+      }
+      __syncthreads();
+      Md = Mx;
+      f += 2.0 * m * n * (double)(kin + ((aid || bid) ? 0 : w));
+    }
+    RandIn ri;
+    ri.m = m;
+    ri.n = n;
+    ri.l = l;
+    ri.Md = Md;
+    ri.SA = SA;
+    ri.SB = SB;
+    ri.ws = R;
+    ri.seed = e.seed ^ ((uint64_t)blockIdx.x << 40) ^ (uint64_t)(t.rout + 1) * 0x9E3779B97F4A7C15ull;
+    int r0 = kin + 6;
+    if (r0 < 8) r0 = 8;
+    ri.r0 = r0;
+    int ok = 0;
+    int k = trunc_rand(ri, e.eps, t.cap, Uout, t.lde, Vout, t.ldf, e.status, s, &f, &ok);
+    if (ok) {
+      if (threadIdx.x == 0) {
+        if (t.rout >= 0) e.ranks[t.rout] = k;
+        atomicAdd(e.counters, 1ull);
+        atomicAdd(e.counters + 1, 1ull);
+        atomicAdd(e.flops, f);
+      }
+      return;
+    }
+    if (threadIdx.x == 0) atomicAdd(e.counters + 2, 1ull);
+  }
   TruncIn in;
   in.nb = 1;
   in.m = m;
@@ -195,10 +246,11 @@ __device__ void task_rkadd(const ExecEnv& e, const HTask& t, Smem& s) {
   in.SB[0] = SB;
   in.W = W;
   in.Jg = Jg;
-  int k = trunc_core(in, e.eps, t.cap, Uout, t.lde, Vout, t.ldf, e.status, s);
+  int k = trunc_core(in, e.eps, t.cap, Uout, t.lde, Vout, t.ldf, e.status, s, &f);
   if (threadIdx.x == 0) {
     if (t.rout >= 0) e.ranks[t.rout] = k;
     atomicAdd(e.counters, 1ull);
+    atomicAdd(e.flops, f);
   }
 }
 
@@ -241,10 +293,45 @@ __device__ void task_rowmerge(const ExecEnv& e, const HTask& t, Smem& s) {
   in.SB[1] = SB1;
   in.W = W;
   in.Jg = Jg;
-  int k = trunc_core(in, e.eps, t.cap, Uout, t.lde, Vout, t.ldf, e.status, s);
+  double f = 0.0;
+  int k = trunc_core(in, e.eps, t.cap, Uout, t.lde, Vout, t.ldf, e.status, s, &f);
   if (threadIdx.x == 0) {
     if (t.rout >= 0) e.ranks[t.rout] = k;
     atomicAdd(e.counters, 1ull);
+    atomicAdd(e.flops, f);
+  }
+}
+
+// FP64 operations of the non-truncation tasks (counted by thread 0).
+__device__ double task_flops(const ExecEnv& e, const HTask& t) {
+  switch (t.type) {
+    case T_LU:
+      return 2.0 / 3.0 * (double)t.m * t.m * t.m;
+    case T_TRSM:
+      return (double)t.m * t.m * width_of(e, t.wa);
+    case T_GEMM:
+      return 2.0 * t.m * t.n * (double)width_of(e, t.wa);
+    case T_ADD:
+      return (double)t.m * t.n;
+    case T_HMV: {
+      double w = width_of(e, t.wa), f = 0.0;
+      for (int li = 0; li < t.list_len; ++li) {
+        const LeafRef& L = e.leaves[t.list_begin + li];
+        if (L.kind == 1) f += 2.0 * L.rows * L.cols * w;
+        else f += 2.0 * e.ranks[L.rank_slot] * (double)(L.rows + L.cols) * w;
+      }
+      return f;
+    }
+    case T_DENSIFY: {
+      double f = 0.0;
+      for (int li = 0; li < t.list_len; ++li) {
+        const LeafRef& L = e.leaves[t.list_begin + li];
+        if (L.kind == 2) f += 2.0 * e.ranks[L.rank_slot] * (double)L.rows * L.cols;
+      }
+      return f;
+    }
+    default:
+      return 0.0;
   }
 }
 
@@ -309,6 +396,7 @@ __global__ void __launch_bounds__(HM_THREADS) exec_tasks(ExecEnv e) {
   Smem& s = *reinterpret_cast<Smem*>(smem_raw);
   __shared__ long long cur;
   __shared__ int skip;
+  __shared__ uint64_t cur_t0;
   for (;;) {
     if (threadIdx.x == 0) {
       cur = (long long)atomicAdd(e.head, 1ull);
@@ -317,6 +405,7 @@ __global__ void __launch_bounds__(HM_THREADS) exec_tasks(ExecEnv e) {
         // bounded wait on every predecessor
         int64_t d0 = e.dep_ptr[cur], d1 = e.dep_ptr[cur + 1];
         uint64_t t0 = global_ns();
+        s.ivals[8] = (int)(t0 & 0x7fffffff);
         for (int64_t d = d0; d < d1 && !skip; ++d) {
           const int* flag = e.done + e.dep_idx[d];
           int64_t it = 0;
@@ -330,6 +419,9 @@ __global__ void __launch_bounds__(HM_THREADS) exec_tasks(ExecEnv e) {
           }
         }
         if (ld_acquire(e.status) != 0) skip = 1;
+        uint64_t t1 = global_ns();
+        atomicAdd(e.wait_ns, (unsigned long long)(t1 - t0));
+        cur_t0 = t1;
       }
     }
     __syncthreads();
@@ -337,7 +429,16 @@ __global__ void __launch_bounds__(HM_THREADS) exec_tasks(ExecEnv e) {
     if (t >= e.ntasks) break;
     if (!skip) {
       HTask task = e.tasks[t];
+      if (threadIdx.x == 0 && task.type != T_RKADD && task.type != T_ROWMERGE) {
+        double f = task_flops(e, task);
+        if (f > 0.0) atomicAdd(e.flops, f);
+      }
       run_task(e, task, s);
+      __syncthreads();
+      if (threadIdx.x == 0 && task.type >= 0 && task.type < 16) {
+        atomicAdd(e.type_ns + task.type, (unsigned long long)(global_ns() - cur_t0));
+        atomicAdd(e.type_cnt + task.type, 1ull);
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -22,8 +22,15 @@ struct ExecEnv {
   int* done;                  // per task, 0 -> 1 when finished
   unsigned long long* head;   // next task to take
   int* status;                // device status word (hmat_status numbering)
-  unsigned long long* counters;  // [0] truncations run
+  unsigned long long* counters;  // [0] truncations run, [1] randomised, [2] randomised fell back
+  double* flops;              // FP64 operations counted by the tasks
+  unsigned long long* type_ns;   // per task type: summed execution time (ns)
+  unsigned long long* type_cnt;  // per task type: tasks run
+  unsigned long long* wait_ns;   // summed time CTAs spent waiting on predecessors
   double eps;
+  int mixed;                  // randomised truncation path on
+  int rand_min_l;             // smallest stacked width that takes it
+  unsigned long long seed;
   long long spin_iters;       // bounded waits: iteration limit
   unsigned long long spin_ns; //                 and time limit
 };

@@ -71,11 +71,12 @@ def test_addeval_after_lu(ctx):
         assert np.abs(from_dev(y) - ref).max() <= 1e-12 * np.abs(ref).max() * 10
 
 
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
 @pytest.mark.parametrize("prob", ["laplace2d_64", "laplace3d_16"])
-def test_hlu_truncated_matches_oracle_quality(ctx, prob):
+def test_hlu_truncated_matches_oracle_quality(ctx, prob, precision):
     p = hs.laplace2d_64() if prob == "laplace2d_64" else hs.small_laplace(16, 3, 64, 1e-4)
     gp = GpuProblem(ctx, p)
-    gp.H.lu(p.eps)
+    gp.H.lu(p.eps, precision=precision)
     st = gp.H.stats()
     assert st["status"] == 0 and st["truncations"] > 0
     v0 = hs.start_vector(p.n, 0)
@@ -89,5 +90,11 @@ def test_hlu_truncated_matches_oracle_quality(ctx, prob):
     rg, ro = gp.H.ranks(), H.ranks()
     adm = rg >= 0
     assert np.array_equal(adm, ro >= 0)
-    assert np.abs(rg[adm] - ro[adm]).max() <= 2
-    assert abs(rg[adm].mean() - ro[adm].mean()) <= 0.1
+    if precision == 0:
+        assert np.abs(rg[adm] - ro[adm]).max() <= 2
+        assert abs(rg[adm].mean() - ro[adm].mean()) <= 0.1
+    else:
+        # the randomised truncation meets the same error rule; its ranks may
+        # exceed the optimal ones by what the sketch missed
+        assert rg[adm].mean() <= ro[adm].mean() + 1.0
+        assert st["rand_truncations"] > 0
