@@ -35,7 +35,7 @@ EXPORTS = ["hmat_last_error", "hmat_ctx_create", "hmat_ctx_destroy", "hmat_clust
            "hmat_blocktree_build", "hmat_blocktree_size", "hmat_blocktree_nodes", "hmat_btree_destroy",
            "hmat_create_from_csr", "hmat_destroy", "hmat_to_dense", "hmat_addeval", "hmat_lu", "hmat_solve",
            "trunc_lowrank", "trunc_lowrank_batched", "hmat_stats_get", "hmat_ranks", "hmat_copy_values",
-           "hmat_analyze_lu"]
+           "hmat_analyze_lu", "trunc_lowrank_noalloc"]
 
 
 class HmatError(RuntimeError):
@@ -250,6 +250,18 @@ def trunc_lowrank(ctx: Context, U, V, eps: float) -> int:
     _check(lib().trunc_lowrank(ctx.h, ctypes.c_int64(m), ctypes.c_int64(n), ctypes.c_int64(k), _dptr(U),
                                ctypes.c_int64(max(m, 1)), _dptr(V), ctypes.c_int64(max(n, 1)), ctypes.c_double(eps),
                                ctypes.byref(kn)))
+    return kn.value
+
+
+def trunc_lowrank_noalloc(ctx: Context, U, V, eps: float) -> int:
+    """As trunc_lowrank, through the entry point that allocates no memory
+    (fixed scratch compiled into the library; see include/hmat.h)."""
+    k, m = U.shape
+    n = V.shape[1]
+    kn = ctypes.c_int64(0)
+    _check(lib().trunc_lowrank_noalloc(ctx.h, ctypes.c_int64(m), ctypes.c_int64(n), ctypes.c_int64(k), _dptr(U),
+                                       ctypes.c_int64(max(m, 1)), _dptr(V), ctypes.c_int64(max(n, 1)),
+                                       ctypes.c_double(eps), ctypes.byref(kn)))
     return kn.value
 
 

@@ -37,19 +37,19 @@ struct Smem {
   double jac[HM_JAC_SMEM];
 };
 
-__device__ __forceinline__ double warp_sum(double v) {
+static __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
-__device__ __forceinline__ double warp_max(double v) {
+static __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 
 // Block-wide sum / max; result returned to every thread.
-__device__ __forceinline__ double block_sum(double v, Smem& s) {
+static __device__ __forceinline__ double block_sum(double v, Smem& s) {
   v = warp_sum(v);
   int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   __syncthreads();
@@ -60,7 +60,7 @@ __device__ __forceinline__ double block_sum(double v, Smem& s) {
   for (int i = 0; i < HM_WARPS; ++i) r += s.red[i];
   return r;
 }
-__device__ __forceinline__ double block_max(double v, Smem& s) {
+static __device__ __forceinline__ double block_max(double v, Smem& s) {
   v = warp_max(v);
   int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   __syncthreads();
@@ -72,7 +72,7 @@ __device__ __forceinline__ double block_max(double v, Smem& s) {
   return r;
 }
 
-__device__ __forceinline__ void set_status(int* status, int code) {
+static __device__ __forceinline__ void set_status(int* status, int code) {
   atomicCAS(status, 0, code);
 }
 
@@ -81,7 +81,7 @@ __device__ __forceinline__ void set_status(int* status, int code) {
 // X(j:rows, j) (v scaled, first entry explicit), tau[j], R diagonal rdiag[j],
 // R(i, c) = X(i, c) for c > i.  q = min(rows, cols) reflectors.
 // ---------------------------------------------------------------------------
-__device__ void cta_qr(double* X, int ld, int rows, int cols, double* tau, double* rdiag, Smem& s) {
+static __device__ void cta_qr(double* X, int ld, int rows, int cols, double* tau, double* rdiag, Smem& s) {
   int q = rows < cols ? rows : cols;
   int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int j = 0; j < q; ++j) {
@@ -131,7 +131,7 @@ __device__ void cta_qr(double* X, int ld, int rows, int cols, double* tau, doubl
 
 // Apply Q = P_0 P_1 ... P_{q-1} (reflectors of cta_qr stored in V) to the
 // matrix Y (rows x ncols, ld): Y <- Q Y.  Reflectors are applied in reverse.
-__device__ void cta_apply_q(const double* V, int ldv, int rows, int q, const double* tau, double* Y, int ldy,
+static __device__ void cta_apply_q(const double* V, int ldv, int rows, int q, const double* tau, double* Y, int ldy,
                             int ncols) {
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int j = q - 1; j >= 0; --j) {
@@ -156,7 +156,7 @@ __device__ void cta_apply_q(const double* V, int ldv, int rows, int q, const dou
 // J_in Vr = J_out.
 // ---------------------------------------------------------------------------
 // s.ivals[2] receives the sweeps run, s.ivals[3] the rotations applied.
-__device__ void cta_jacobi(double* J, int p, int c, double* Vr, Smem& s) {
+static __device__ void cta_jacobi(double* J, int p, int c, double* Vr, Smem& s) {
   int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int idx = tid; idx < c * c; idx += HM_THREADS) Vr[idx] = (idx % c == idx / c) ? 1.0 : 0.0;
   if (tid == 0) {
@@ -233,7 +233,7 @@ __device__ void cta_jacobi(double* J, int p, int c, double* Vr, Smem& s) {
 }
 
 // Column norms of J into sigma, and the order of decreasing sigma into order.
-__device__ void cta_sort_sigma(const double* J, int p, int c, Smem& s) {
+static __device__ void cta_sort_sigma(const double* J, int p, int c, Smem& s) {
   int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int j = warp; j < c; j += HM_WARPS) {
     const double* jj = J + (int64_t)j * p;
@@ -256,7 +256,7 @@ __device__ void cta_sort_sigma(const double* J, int p, int c, Smem& s) {
 }
 
 // "Choose new rank k": smallest k with sum_{i>k} s_i^2 <= eps^2 sum_i s_i^2.
-__device__ int cta_choose_rank(int c, double eps, Smem& s) {
+static __device__ int cta_choose_rank(int c, double eps, Smem& s) {
   if (threadIdx.x == 0) {
     double total = 0.0;
     for (int i = 0; i < c; ++i) {
@@ -305,11 +305,11 @@ struct TruncIn {
 };
 
 // Householder QR flops of a rows x cols matrix (Golub & Van Loan count).
-__device__ __forceinline__ double qr_flops(double rows, double cols) {
+static __device__ __forceinline__ double qr_flops(double rows, double cols) {
   return rows >= cols ? 2.0 * cols * cols * (rows - cols / 3.0) : 2.0 * rows * rows * (cols - rows / 3.0);
 }
 
-__device__ int trunc_core(const TruncIn& in, double eps, int cap, double* U, int ldu, double* V, int ldv,
+static __device__ int trunc_core(const TruncIn& in, double eps, int cap, double* U, int ldu, double* V, int ldv,
                           int* status, Smem& s, double* flops = nullptr) {
   int tid = threadIdx.x;
   int m = in.m;
@@ -451,14 +451,14 @@ struct RandIn {
   int r0;             // first sketch width
 };
 
-__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+static __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   z += 0x9E3779B97F4A7C15ull;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   return z ^ (z >> 31);
 }
 
-__device__ int trunc_rand(const RandIn& in, double eps, int cap, double* U, int ldu, double* V, int ldv,
+static __device__ int trunc_rand(const RandIn& in, double eps, int cap, double* U, int ldu, double* V, int ldv,
                           int* status, Smem& s, double* flops, int* ok) {
   int tid = threadIdx.x;
   int m = in.m, n = in.n, l = in.l;
@@ -651,7 +651,7 @@ __host__ __device__ inline int64_t rand_ws_doubles(int64_t m, int64_t n, int64_t
 // Dense leaf operations
 // ---------------------------------------------------------------------------
 // No-pivot LU in place (L unit lower, U upper).
-__device__ void cta_lu(double* A, int ld, int n, int* status) {
+static __device__ void cta_lu(double* A, int ld, int n, int* status) {
   int tid = threadIdx.x;
   for (int k = 0; k < n; ++k) {
     double piv = A[(int64_t)k * ld + k];
@@ -672,7 +672,7 @@ __device__ void cta_lu(double* A, int ld, int n, int* status) {
 }
 
 // Thin solves with a dense diagonal leaf N (n x n, ld): X (n x w, ldx).
-__device__ void cta_trsm(int kind, const double* N, int ld, int n, double* X, int ldx, int w) {
+static __device__ void cta_trsm(int kind, const double* N, int ld, int n, double* X, int ldx, int w) {
   int tid = threadIdx.x;
   if (w <= 0) return;
   if (kind == TRSM_L) {  // X <- L^{-1} X, forward, unit diagonal
@@ -717,7 +717,7 @@ __device__ void cta_trsm(int kind, const double* N, int ld, int n, double* X, in
 }
 
 // C (m x n, ldc) (+)= alpha op(A) op(B), op(A) m x kk, op(B) kk x n.
-__device__ void cta_gemm(double* C, int ldc, int m, int n, int kk, double alpha, const double* A, int lda,
+static __device__ void cta_gemm(double* C, int ldc, int m, int n, int kk, double alpha, const double* A, int lda,
                          bool ta, const double* B, int ldb, bool tb, bool zero) {
   int tid = threadIdx.x;
   for (int idx = tid; idx < m * n; idx += HM_THREADS) {

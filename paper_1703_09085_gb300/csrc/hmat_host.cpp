@@ -1977,3 +1977,10 @@ hmat_status hmat_ranks(const hmat* H, int64_t* ranks) {
 }
 
 }  // extern "C"
+
+// Internal accessors for the other translation units of the library.
+namespace hm_internal {
+int ctx_device(const hmat_ctx* c) { return c->device; }
+cudaStream_t ctx_stream(const hmat_ctx* c) { return c->stream; }
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace hm_internal
