@@ -88,6 +88,11 @@ typedef struct {
   double wait_seconds;    /* summed CTA time waiting on predecessors            */
   int64_t rand_truncations; /* truncations done by the randomised path (MIXED)  */
   int64_t rand_fallbacks;   /* randomised attempts that fell back to QR + SVD   */
+  /* Filled when the environment sets HMAT_PROFILE_TASKS=1: the measured
+   * critical path (longest chain of task durations) and its make-up. */
+  double cp_seconds;
+  double cp_type_seconds[16];
+  int64_t cp_type_count[16];
 } hmat_stats;
 
 /* Message of the last failure on this thread, copied into buf (NUL-terminated,
@@ -188,10 +193,16 @@ hmat_status trunc_lowrank(hmat_ctx* ctx, int64_t m, int64_t n, int64_t k, double
  * m[i], n[i], k[i] (host arrays, k[i] <= 256) and factors at the device
  * pointers U[i] (ld m[i]) and V[i] (ld n[i]) (host array of device pointers).
  * k_new is a DEVICE array of count entries receiving the new ranks.  One CTA
- * per problem; the call synchronises the context stream before returning. */
+ * per problem; the call synchronises the context stream before returning.
+ * precision HMAT_MIXED (eps > 0, m n <= 2^20) first tries the randomised
+ * range finder with an FP32 sketch and projection and an FP64 core, keeping
+ * the same Frobenius rule (its rank may exceed the optimal one by what the
+ * sketch missed); a problem whose sketch misses too much falls back to the
+ * exact QR + SVD.  *randomised (host, may be NULL) receives how many problems
+ * the randomised path finished. */
 hmat_status trunc_lowrank_batched(hmat_ctx* ctx, int64_t count, const int64_t* m, const int64_t* n,
                                   const int64_t* k, double* const* U, double* const* V, double eps,
-                                  int64_t* k_new);
+                                  int64_t* k_new, int precision, int64_t* randomised);
 
 /* trunc_lowrank without any memory allocation (the paper has no counterpart:
  * this serves callers that cannot let the library allocate device memory,

@@ -58,13 +58,14 @@ class Stats(ctypes.Structure):
                 ("levels", ctypes.c_int64), ("critical_flops", ctypes.c_double), ("est_flops", ctypes.c_double),
                 ("type_seconds", ctypes.c_double * 16), ("type_count", ctypes.c_int64 * 16),
                 ("wait_seconds", ctypes.c_double), ("rand_truncations", ctypes.c_int64),
-                ("rand_fallbacks", ctypes.c_int64)]
+                ("rand_fallbacks", ctypes.c_int64), ("cp_seconds", ctypes.c_double),
+                ("cp_type_seconds", ctypes.c_double * 16), ("cp_type_count", ctypes.c_int64 * 16)]
 
     def as_dict(self) -> dict:
         d = {}
         for f, _ in self._fields_:
             v = getattr(self, f)
-            d[f] = list(v) if f in ("type_seconds", "type_count") else v
+            d[f] = list(v) if f in ("type_seconds", "type_count", "cp_type_seconds", "cp_type_count") else v
         return d
 
 
@@ -265,14 +266,18 @@ def trunc_lowrank_noalloc(ctx: Context, U, V, eps: float) -> int:
     return kn.value
 
 
-def trunc_lowrank_batched(ctx: Context, Us, Vs, eps: float, k_new) -> None:
+def trunc_lowrank_batched(ctx: Context, Us, Vs, eps: float, k_new, precision: int = HMAT_FP64) -> int:
     """Batched in-place truncation; Us[i]: (k_i, m_i) tensors, Vs[i]: (k_i, n_i),
-    k_new: int64 CUDA tensor of len(Us) receiving the new ranks."""
+    k_new: int64 CUDA tensor of len(Us) receiving the new ranks.  Returns how
+    many problems the randomised path (precision=HMAT_MIXED) finished."""
     cnt = len(Us)
     m = np.array([u.shape[1] for u in Us], np.int64)
     k = np.array([u.shape[0] for u in Us], np.int64)
     n = np.array([v.shape[1] for v in Vs], np.int64)
     up = (ctypes.c_void_p * cnt)(*[_dptr(u).value for u in Us])
     vp = (ctypes.c_void_p * cnt)(*[_dptr(v).value for v in Vs])
+    rnd = ctypes.c_int64(0)
     _check(lib().trunc_lowrank_batched(ctx.h, ctypes.c_int64(cnt), _hp(m, I64P), _hp(n, I64P), _hp(k, I64P), up, vp,
-                                       ctypes.c_double(eps), ctypes.c_void_p(k_new.data_ptr())))
+                                       ctypes.c_double(eps), ctypes.c_void_p(k_new.data_ptr()), ctypes.c_int(precision),
+                                       ctypes.byref(rnd)))
+    return rnd.value

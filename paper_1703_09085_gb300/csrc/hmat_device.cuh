@@ -89,7 +89,7 @@ static __device__ void cta_qr(double* X, int ld, int rows, int cols, double* tau
     double mx = 0.0;
     for (int i = j + tid; i < rows; i += HM_THREADS) mx = fmax(mx, fabs(xj[i]));
     mx = block_max(mx, s);
-    if (mx == 0.0) {
+    if (mx < 1e-290) {  // nothing left in this column (1/mx would overflow)
       if (tid == 0) {
         tau[j] = 0.0;
         rdiag[j] = 0.0;
@@ -129,25 +129,90 @@ static __device__ void cta_qr(double* X, int ld, int rows, int cols, double* tau
   }
 }
 
+// The same factorisation by warp 0 alone (no CTA barriers), for short
+// panels where barrier latency dominates.  The caller synchronises the CTA
+// before and after.  Butterfly (xor) reductions leave bit-identical sums on
+// every lane, so all lanes agree on every reflector.
+static __device__ void warp_qr(double* X, int ld, int rows, int cols, double* tau, double* rdiag) {
+  if ((threadIdx.x >> 5) != 0) return;
+  int lane = threadIdx.x & 31;
+  int q = rows < cols ? rows : cols;
+  for (int j = 0; j < q; ++j) {
+    double* xj = X + (int64_t)j * ld;
+    double mx = 0.0;
+    for (int i = j + lane; i < rows; i += 32) mx = fmax(mx, fabs(xj[i]));
+    mx = warp_max(mx);
+    if (mx < 1e-290) {  // nothing left in this column (1/mx would overflow)
+      if (lane == 0) {
+        tau[j] = 0.0;
+        rdiag[j] = 0.0;
+      }
+      __syncwarp();
+      continue;
+    }
+    double inv = 1.0 / mx;
+    double tail = 0.0;
+    for (int i = j + 1 + lane; i < rows; i += 32) {
+      double v = xj[i] * inv;
+      tail += v * v;
+    }
+    tail = warp_sum(tail);
+    double v0 = xj[j] * inv;
+    double xn = sqrt(tail + v0 * v0);
+    double alpha = v0 >= 0.0 ? -xn : xn;
+    double v0n = v0 - alpha;
+    double tj = 2.0 / (tail + v0n * v0n);
+    __syncwarp();
+    for (int i = j + 1 + lane; i < rows; i += 32) xj[i] *= inv;
+    if (lane == 0) {
+      xj[j] = v0n;
+      tau[j] = tj;
+      rdiag[j] = alpha * mx;
+    }
+    __syncwarp();
+    for (int c = j + 1; c < cols; ++c) {
+      double* xc = X + (int64_t)c * ld;
+      double d = 0.0;
+      for (int i = j + lane; i < rows; i += 32) d += xj[i] * xc[i];
+      d = warp_sum(d) * tj;
+      for (int i = j + lane; i < rows; i += 32) xc[i] -= d * xj[i];
+    }
+    __syncwarp();
+  }
+}
+
+// QR of a panel: warp-level for short panels, CTA-wide otherwise.
+static __device__ void panel_qr(double* X, int ld, int rows, int cols, double* tau, double* rdiag, Smem& s) {
+  if (rows <= 256) {
+    __syncthreads();
+    warp_qr(X, ld, rows, cols, tau, rdiag);
+    __syncthreads();
+  } else {
+    cta_qr(X, ld, rows, cols, tau, rdiag, s);
+  }
+}
+
 // Apply Q = P_0 P_1 ... P_{q-1} (reflectors of cta_qr stored in V) to the
-// matrix Y (rows x ncols, ld): Y <- Q Y.  Reflectors are applied in reverse.
+// matrix Y (rows x ncols, ld): Y <- Q Y.  Columns are independent, so each
+// warp applies every reflector (in reverse) to its own columns.
 static __device__ void cta_apply_q(const double* V, int ldv, int rows, int q, const double* tau, double* Y, int ldy,
                             int ncols) {
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int j = q - 1; j >= 0; --j) {
-    double tj = tau[j];
-    if (tj != 0.0) {
+  __syncthreads();
+  for (int c = warp; c < ncols; c += HM_WARPS) {
+    double* yc = Y + (int64_t)c * ldy;
+    for (int j = q - 1; j >= 0; --j) {
+      double tj = tau[j];
+      if (tj == 0.0) continue;
       const double* vj = V + (int64_t)j * ldv;
-      for (int c = warp; c < ncols; c += HM_WARPS) {
-        double* yc = Y + (int64_t)c * ldy;
-        double d = 0.0;
-        for (int i = j + lane; i < rows; i += 32) d += vj[i] * yc[i];
-        d = warp_sum(d) * tj;
-        for (int i = j + lane; i < rows; i += 32) yc[i] -= d * vj[i];
-      }
+      double d = 0.0;
+      for (int i = j + lane; i < rows; i += 32) d += vj[i] * yc[i];
+      d = warp_sum(d) * tj;
+      for (int i = j + lane; i < rows; i += 32) yc[i] -= d * vj[i];
+      __syncwarp();
     }
-    __syncthreads();
   }
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -156,7 +221,7 @@ static __device__ void cta_apply_q(const double* V, int ldv, int rows, int q, co
 // J_in Vr = J_out.
 // ---------------------------------------------------------------------------
 // s.ivals[2] receives the sweeps run, s.ivals[3] the rotations applied.
-static __device__ void cta_jacobi(double* J, int p, int c, double* Vr, Smem& s) {
+static __device__ void cta_jacobi(double* J, int p, int c, double* Vr, Smem& s, double tol = 1e-15) {
   int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int idx = tid; idx < c * c; idx += HM_THREADS) Vr[idx] = (idx % c == idx / c) ? 1.0 : 0.0;
   if (tid == 0) {
@@ -166,7 +231,6 @@ static __device__ void cta_jacobi(double* J, int p, int c, double* Vr, Smem& s) 
   __syncthreads();
   if (c < 2) return;
   int N = c + (c & 1);
-  const double tol = 1e-15;
   for (int sweep = 0; sweep < 60; ++sweep) {
     if (tid == 0) {
       s.ivals[0] = 0;
@@ -320,7 +384,7 @@ static __device__ int trunc_core(const TruncIn& in, double eps, int cap, double*
   int qs = q[0] + (in.nb > 1 ? q[1] : 0);
   // tauB / rdiagB hold both blocks' reflectors at offsets qoff.
   for (int j = 0; j < in.nb; ++j)
-    cta_qr(in.SB[j], in.n[j], in.n[j], in.k[j], s.tauB + qoff[j], s.rdiagB + qoff[j], s);
+    panel_qr(in.SB[j], in.n[j], in.n[j], in.k[j], s.tauB + qoff[j], s.rdiagB + qoff[j], s);
   if (m == 0 || qs == 0) return 0;
   // Ahat = [SA_0 R_0^T, SA_1 R_1^T]  (m x qs)
   for (int j = 0; j < in.nb; ++j) {
@@ -336,7 +400,7 @@ static __device__ int trunc_core(const TruncIn& in, double eps, int cap, double*
   }
   __syncthreads();
   // QR of Ahat
-  cta_qr(in.W, m, m, qs, s.tauA, s.rdiagA, s);
+  panel_qr(in.W, m, m, qs, s.tauA, s.rdiagA, s);
   int qa = m < qs ? m : qs;
   // Jacobi core: case A (qa == qs): J = R_A (qs x qs); case B: J = R_A^T (qs x qa)
   bool caseA = (qa == qs);
@@ -467,12 +531,19 @@ static __device__ int trunc_rand(const RandIn& in, double eps, int cap, double* 
   if (rmax > m) rmax = m;
   if (rmax > n) rmax = n;
   if (factored && rmax > l) rmax = l;
-  double* Y = in.ws;                          // m x RMAX (sketch, then reflectors)
-  double* Qx = Y + (int64_t)m * HM_RMAX;      // m x RMAX
-  double* J = Qx + (int64_t)m * HM_RMAX;      // n x RMAX
-  double* Vr = J + (int64_t)n * HM_RMAX;      // RMAX x RMAX
-  uint32_t* Om = (uint32_t*)(Vr + HM_RMAX * HM_RMAX);  // n sign words
-  double* G = Vr + HM_RMAX * HM_RMAX + (n + 1) / 2 + 1;  // 2 l x l Grams, or T (l x RMAX floats)
+  // Y (m x RMAX: sketch, then reflectors), Qx (m x RMAX), J (n x RMAX) and
+  // Vr (RMAX x RMAX) live in shared memory when they fit (the sequential
+  // steps of the QR and the Jacobi rounds then avoid L2 round trips), else in
+  // the scratch.  Signs and Grams always use the scratch.
+  bool in_smem = (int64_t)(2 * m + n) * rmax + (int64_t)rmax * rmax <= HM_JAC_SMEM;
+  int R = in_smem ? rmax : HM_RMAX;
+  double* Y = in_smem ? s.jac : in.ws;
+  double* Qx = Y + (int64_t)m * R;
+  double* J = Qx + (int64_t)m * R;
+  double* Vr = J + (int64_t)n * R;
+  double* gws = in.ws + (int64_t)(2 * m + n) * HM_RMAX + HM_RMAX * HM_RMAX;
+  uint32_t* Om = (uint32_t*)gws;                          // n sign words
+  double* G = gws + (n + 1) / 2 + 1;                       // 2 l x l Grams, or T (l x RMAX floats)
   double f = 0.0;
   // ||M||_F^2
   double total;
@@ -550,7 +621,7 @@ static __device__ int trunc_rand(const RandIn& in, double eps, int cap, double* 
     __syncthreads();
     // Q = orth(Y): Householder, then explicit Q = P_0 ... P_{r-1} [I; 0]
     int rr = r < m ? r : m;
-    cta_qr(Y, m, m, r, s.tauA, s.rdiagA, s);
+    panel_qr(Y, m, m, r, s.tauA, s.rdiagA, s);
     for (int idx = tid; idx < m * rr; idx += HM_THREADS) Qx[idx] = (idx % m == idx / m) ? 1.0 : 0.0;
     __syncthreads();
     cta_apply_q(Y, m, m, rr, s.tauA, Qx, m, rr);
@@ -581,7 +652,7 @@ static __device__ int trunc_rand(const RandIn& in, double eps, int cap, double* 
       f += 2.0 * (m + n) * (double)l * rr;
     }
     __syncthreads();
-    cta_jacobi(J, n, rr, Vr, s);
+    cta_jacobi(J, n, rr, Vr, s, 1e-10);
     cta_sort_sigma(J, n, rr, s);
     f += qr_flops(m, r) + 4.0 * m * rr * rr;
     f += (double)s.ivals[2] * 0.5 * rr * (rr - 1) * 6.0 * n + (double)s.ivals[3] * 6.0 * (n + rr);
@@ -640,6 +711,232 @@ static __device__ int trunc_rand(const RandIn& in, double eps, int cap, double* 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Mixed-precision randomised truncation of an explicit M (m x n, FP32 copy,
+// ld m).  The sketch Y = M Omega, Q = orth(Y) and the projection J = M^T Q
+// run in FP32; the residual ||M - Q J^T||_F^2 is formed entry by entry (FP32
+// differences, FP64 sum), which stays accurate where the difference of the
+// two squared norms would cancel.  The small core is FP64: J = Q_J R_J (FP32
+// QR), one-sided Jacobi on R_J in FP64 gives R_J Vr = W with orthogonal
+// columns, so J Vr has orthogonal columns of norms sigma and
+//   C = Q Vr(:, order), D = J Vr(:, order)  (Fig. rkadd's C, D).
+// Rank rule as trunc_rand: res^2 + tail <= eps^2 ||M||_F^2.
+// M arrives scaled by 1/scale (largest entry 1, clear of the FP32 range
+// limits); the rule is scale invariant and D is multiplied back by scale.
+// Float work space fw: 2 m R + 2 n R floats (R = min(32, m, n)); Om: n words;
+// the FP64 core (2 R^2 doubles) sits at s.jac + HM_F32_SMEM / 2.
+// ---------------------------------------------------------------------------
+#define HM_F32_SMEM 14336  // floats of s.jac the FP32 work space may use
+#define HM_F32_MAX_MN (1 << 20)  // largest m n truncated through the FP32 path
+#define HM_F32_MIN_EPS 1e-5      // FP32 rounding (~1e-7) stays well below eps from here on
+
+static __device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+static __device__ __forceinline__ float warp_max_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Warp 0: Householder QR of a float panel (conventions of warp_qr; tau and
+// the R diagonal are returned in FP64 arrays).
+static __device__ void warp_qr_f(float* X, int ld, int rows, int cols, double* tau, double* rdiag) {
+  if ((threadIdx.x >> 5) != 0) return;
+  int lane = threadIdx.x & 31;
+  int q = rows < cols ? rows : cols;
+  for (int j = 0; j < q; ++j) {
+    float* xj = X + (int64_t)j * ld;
+    float mx = 0.f;
+    for (int i = j + lane; i < rows; i += 32) mx = fmaxf(mx, fabsf(xj[i]));
+    mx = warp_max_f(mx);
+    if (mx < 1e-30f) {  // nothing left in this column (1/mx would overflow FP32)
+      if (lane == 0) {
+        tau[j] = 0.0;
+        rdiag[j] = 0.0;
+      }
+      __syncwarp();
+      continue;
+    }
+    float inv = 1.f / mx;
+    float tail = 0.f;
+    for (int i = j + 1 + lane; i < rows; i += 32) {
+      float v = xj[i] * inv;
+      tail += v * v;
+    }
+    tail = warp_sum_f(tail);
+    float v0 = xj[j] * inv;
+    float xn = sqrtf(tail + v0 * v0);
+    float alpha = v0 >= 0.f ? -xn : xn;
+    float v0n = v0 - alpha;
+    float tj = 2.f / (tail + v0n * v0n);
+    __syncwarp();
+    for (int i = j + 1 + lane; i < rows; i += 32) xj[i] *= inv;
+    if (lane == 0) {
+      xj[j] = v0n;
+      tau[j] = tj;
+      rdiag[j] = (double)alpha * mx;
+    }
+    __syncwarp();
+    for (int c = j + 1; c < cols; ++c) {
+      float* xc = X + (int64_t)c * ld;
+      float d = 0.f;
+      for (int i = j + lane; i < rows; i += 32) d += xj[i] * xc[i];
+      d = warp_sum_f(d) * tj;
+      for (int i = j + lane; i < rows; i += 32) xc[i] -= d * xj[i];
+    }
+    __syncwarp();
+  }
+}
+
+// Q = P_0 ... P_{q-1} [I; 0] (rows x q, ld ldq) from warp_qr_f reflectors;
+// each warp builds its own columns (P_j e_c needs only j <= c).
+static __device__ void form_q_f(const float* V, int ldv, int rows, int q, const double* tau, float* Q, int ldq) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  for (int c = warp; c < q; c += HM_WARPS) {
+    float* qc = Q + (int64_t)c * ldq;
+    for (int i = lane; i < rows; i += 32) qc[i] = (i == c) ? 1.f : 0.f;
+    __syncwarp();
+    for (int j = c; j >= 0; --j) {
+      float tj = (float)tau[j];
+      if (tj == 0.f) continue;
+      const float* vj = V + (int64_t)j * ldv;
+      float d = 0.f;
+      for (int i = j + lane; i < rows; i += 32) d += vj[i] * qc[i];
+      d = warp_sum_f(d) * tj;
+      for (int i = j + lane; i < rows; i += 32) qc[i] -= d * vj[i];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
+static __device__ int trunc_rand32(const float* M, int m, int n, double scale, float* fw, uint32_t* Om, double eps,
+                                   int cap, double* U, int ldu, double* V, int ldv, int* status, Smem& s,
+                                   double* flops, int* ok, uint64_t seed, int r0) {
+  int tid = threadIdx.x;
+  int rmax = HM_RMAX;
+  if (rmax > m) rmax = m;
+  if (rmax > n) rmax = n;
+  int R = rmax;
+  float* Y = fw;                      // m x R: sketch, then reflectors
+  float* Qf = Y + (int64_t)m * R;     // m x R
+  float* J = Qf + (int64_t)m * R;     // n x R
+  float* Jq = J + (int64_t)n * R;     // n x R: QR of J
+  double* R64 = s.jac + HM_F32_SMEM / 2;  // R x R
+  double* Vr = R64 + R * R;               // R x R
+  double acc = 0.0;
+  for (int64_t idx = tid; idx < (int64_t)m * n; idx += HM_THREADS) {
+    double x = M[idx];
+    acc += x * x;
+  }
+  double total = block_sum(acc, s);
+  if (total == 0.0) {
+    *ok = 1;
+    return 0;
+  }
+  double bound = eps * eps * total;
+  double f = 0.0;
+  for (int i = tid; i < n; i += HM_THREADS) Om[i] = (uint32_t)mix64(seed ^ ((uint64_t)i * 0xD1B54A32D192ED03ull));
+  int r = r0 < 2 ? 2 : r0;
+  if (r > rmax) r = rmax;
+  for (;;) {
+    __syncthreads();
+    for (int idx = tid; idx < m * r; idx += HM_THREADS) {
+      int i = idx % m, j = idx / m;
+      float a = 0.f;
+      for (int c = 0; c < n; ++c) {
+        float x = M[(int64_t)c * m + i];
+        a += ((Om[c] >> j) & 1u) ? x : -x;
+      }
+      Y[(int64_t)j * m + i] = a;
+    }
+    __syncthreads();
+    warp_qr_f(Y, m, m, r, s.tauA, s.rdiagA);
+    form_q_f(Y, m, m, r, s.tauA, Qf, m);
+    for (int idx = tid; idx < n * r; idx += HM_THREADS) {
+      int c = idx % n, j = idx / n;
+      float a = 0.f;
+      const float* mc = M + (int64_t)c * m;
+      const float* qj = Qf + (int64_t)j * m;
+      for (int i = 0; i < m; ++i) a += mc[i] * qj[i];
+      J[(int64_t)j * n + c] = a;
+    }
+    __syncthreads();
+    double racc = 0.0;
+    for (int64_t idx = tid; idx < (int64_t)m * n; idx += HM_THREADS) {
+      int i = (int)(idx % m), c = (int)(idx / m);
+      float a = M[idx];
+      for (int j = 0; j < r; ++j) a -= Qf[(int64_t)j * m + i] * J[(int64_t)j * n + c];
+      racc += (double)a * (double)a;
+    }
+    double res2 = block_sum(racc, s);
+    if (!(res2 <= bound)) {  // also catches a non-finite residual
+      if (r >= rmax || !isfinite(res2)) {
+        *ok = 0;
+        return 0;
+      }
+      r = 2 * r > rmax ? rmax : 2 * r;
+      continue;
+    }
+    // FP64 core: R factor of J, then one-sided Jacobi
+    for (int idx = tid; idx < n * r; idx += HM_THREADS) Jq[idx] = J[idx];
+    __syncthreads();
+    warp_qr_f(Jq, n, n, r, s.tauB, s.rdiagB);
+    __syncthreads();
+    for (int idx = tid; idx < r * r; idx += HM_THREADS) {
+      int i = idx % r, c = idx / r;
+      R64[idx] = i > c ? 0.0 : (i == c ? s.rdiagB[i] : (double)Jq[(int64_t)c * n + i]);
+    }
+    __syncthreads();
+    cta_jacobi(R64, r, r, Vr, s, 1e-12);
+    cta_sort_sigma(R64, r, r, s);
+    f += (double)s.ivals[2] * 0.5 * r * (r - 1) * 6.0 * r + (double)s.ivals[3] * 12.0 * r;
+    if (tid == 0) {
+      double tail = res2;
+      int k = r;
+      while (k > 0) {
+        double x = s.sigma[s.order[k - 1]];
+        if (tail + x * x <= bound) {
+          tail += x * x;
+          --k;
+        } else {
+          break;
+        }
+      }
+      s.ivals[4] = k;
+    }
+    __syncthreads();
+    int k = s.ivals[4];
+    __syncthreads();
+    if (k > cap) {
+      if (tid == 0) set_status(status, DS_RANK);
+      k = cap;
+    }
+    for (int idx = tid; idx < m * k; idx += HM_THREADS) {
+      int i = idx % m, jj = idx / m;
+      const double* vc = Vr + (int64_t)s.order[jj] * r;
+      double a = 0.0;
+      for (int j = 0; j < r; ++j) a += (double)Qf[(int64_t)j * m + i] * vc[j];
+      U[(int64_t)jj * ldu + i] = a;
+    }
+    for (int idx = tid; idx < n * k; idx += HM_THREADS) {
+      int c = idx % n, jj = idx / n;
+      const double* vc = Vr + (int64_t)s.order[jj] * r;
+      double a = 0.0;
+      for (int j = 0; j < r; ++j) a += (double)J[(int64_t)j * n + c] * vc[j];
+      V[(int64_t)jj * ldv + c] = a * scale;
+    }
+    f += 2.0 * (m + n) * (double)r * k;
+    if (flops && tid == 0) *flops += f;
+    *ok = 1;
+    return k;
+  }
+}
+
 // Doubles of scratch trunc_rand needs.
 __host__ __device__ inline int64_t rand_ws_doubles(int64_t m, int64_t n, int64_t l) {
   int64_t g = 2 * l * l;
@@ -672,47 +969,61 @@ static __device__ void cta_lu(double* A, int ld, int n, int* status) {
 }
 
 // Thin solves with a dense diagonal leaf N (n x n, ld): X (n x w, ldx).
-static __device__ void cta_trsm(int kind, const double* N, int ld, int n, double* X, int ldx, int w) {
-  int tid = threadIdx.x;
+// One warp per right-hand-side column: columns are independent, so the
+// substitution needs only warp-level synchronisation.
+static __device__ void cta_trsm_cols(int kind, const double* N, int ld, int n, double* X, int ldx, int w) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c = warp; c < w; c += HM_WARPS) {
+    double* x = X + (int64_t)c * ldx;
+    if (kind == TRSM_L) {
+      for (int k = 0; k < n - 1; ++k) {
+        double xk = x[k];
+        for (int i = k + 1 + lane; i < n; i += 32) x[i] -= N[(int64_t)k * ld + i] * xk;
+        __syncwarp();
+      }
+    } else if (kind == TRSM_U) {
+      for (int k = n - 1; k >= 0; --k) {
+        double xk = x[k] / N[(int64_t)k * ld + k];
+        __syncwarp();
+        if (lane == 0) x[k] = xk;
+        for (int i = lane; i < k; i += 32) x[i] -= N[(int64_t)k * ld + i] * xk;
+        __syncwarp();
+      }
+    } else if (kind == TRSM_UT) {
+      for (int k = 0; k < n; ++k) {
+        double xk = x[k] / N[(int64_t)k * ld + k];
+        __syncwarp();
+        if (lane == 0) x[k] = xk;
+        for (int i = k + 1 + lane; i < n; i += 32) x[i] -= N[(int64_t)i * ld + k] * xk;
+        __syncwarp();
+      }
+    } else {
+      for (int k = n - 1; k > 0; --k) {
+        double xk = x[k];
+        for (int i = lane; i < k; i += 32) x[i] -= N[(int64_t)i * ld + k] * xk;
+        __syncwarp();
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Thin triangular solve: the triangle and the right-hand sides are staged in
+// shared memory when they fit (coalesced loads, then the warp substitutions
+// run on shared memory), else solved in place in global memory.
+static __device__ void cta_trsm(int kind, const double* N, int ld, int n, double* X, int ldx, int w, Smem& s) {
   if (w <= 0) return;
-  if (kind == TRSM_L) {  // X <- L^{-1} X, forward, unit diagonal
-    for (int k = 0; k < n - 1; ++k) {
-      int rem = n - k - 1;
-      for (int idx = tid; idx < rem * w; idx += HM_THREADS) {
-        int i = k + 1 + idx % rem, c = idx / rem;
-        X[(int64_t)c * ldx + i] -= N[(int64_t)k * ld + i] * X[(int64_t)c * ldx + k];
-      }
-      __syncthreads();
-    }
-  } else if (kind == TRSM_U) {  // X <- U^{-1} X, backward
-    for (int k = n - 1; k >= 0; --k) {
-      for (int c = tid; c < w; c += HM_THREADS) X[(int64_t)c * ldx + k] /= N[(int64_t)k * ld + k];
-      __syncthreads();
-      for (int idx = tid; idx < k * w; idx += HM_THREADS) {
-        int i = idx % k, c = idx / k;
-        X[(int64_t)c * ldx + i] -= N[(int64_t)k * ld + i] * X[(int64_t)c * ldx + k];
-      }
-      __syncthreads();
-    }
-  } else if (kind == TRSM_UT) {  // X <- U^{-T} X, forward
-    for (int k = 0; k < n; ++k) {
-      for (int c = tid; c < w; c += HM_THREADS) X[(int64_t)c * ldx + k] /= N[(int64_t)k * ld + k];
-      __syncthreads();
-      int rem = n - k - 1;
-      for (int idx = tid; idx < rem * w; idx += HM_THREADS) {
-        int i = k + 1 + idx % rem, c = idx / rem;
-        X[(int64_t)c * ldx + i] -= N[(int64_t)i * ld + k] * X[(int64_t)c * ldx + k];
-      }
-      __syncthreads();
-    }
-  } else {  // TRSM_LT: X <- L^{-T} X, backward, unit diagonal
-    for (int k = n - 1; k > 0; --k) {
-      for (int idx = tid; idx < k * w; idx += HM_THREADS) {
-        int i = idx % k, c = idx / k;
-        X[(int64_t)c * ldx + i] -= N[(int64_t)i * ld + k] * X[(int64_t)c * ldx + k];
-      }
-      __syncthreads();
-    }
+  if ((int64_t)n * n + (int64_t)n * w <= HM_JAC_SMEM) {
+    double* Ns = s.jac;
+    double* Xs = s.jac + (int64_t)n * n;
+    for (int idx = threadIdx.x; idx < n * n; idx += HM_THREADS) Ns[idx] = N[(int64_t)(idx / n) * ld + idx % n];
+    for (int idx = threadIdx.x; idx < n * w; idx += HM_THREADS) Xs[idx] = X[(int64_t)(idx / n) * ldx + idx % n];
+    __syncthreads();
+    cta_trsm_cols(kind, Ns, n, n, Xs, n, w);
+    for (int idx = threadIdx.x; idx < n * w; idx += HM_THREADS) X[(int64_t)(idx / n) * ldx + idx % n] = Xs[idx];
+    __syncthreads();
+  } else {
+    cta_trsm_cols(kind, N, ld, n, X, ldx, w);
   }
 }
 

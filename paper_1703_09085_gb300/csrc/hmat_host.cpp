@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -478,7 +480,9 @@ const int64_t RMAX = 32;
 int64_t rand_ws(int64_t m, int64_t n, int64_t l) {
   int64_t g = std::max(2 * l * l, l * RMAX);
   int64_t mx = (m * n <= (m + n) * l) ? m * n : 0;
-  return mx + 2 * m * RMAX + n * RMAX + RMAX * RMAX + (n + 1) / 2 + 1 + g + 64;
+  // FP32 path (m n <= 2^20): M, sketch, Q, J, QR of J as floats, then the signs
+  int64_t f32 = (m * n <= ((int64_t)1 << 20)) ? (m * n + 2 * (m + n) * RMAX + n) / 2 + 64 : 0;
+  return std::max(mx + 2 * m * RMAX + n * RMAX + RMAX * RMAX + (n + 1) / 2 + 1 + g, f32) + 64;
 }
 
 // ===========================================================================
@@ -1171,7 +1175,7 @@ struct Sym {
         t.cap = C.cap;
         int64_t l = (tmp[0][j].zero ? 0 : tmp[0][j].wmax) + (tmp[1][j].zero ? 0 : tmp[1][j].wmax);
         if (l > HM_LMAX_HOST) throw HmError(HMAT_ERR_RANK, "merged width exceeds the truncation limit");
-        int ws = S.alloc(rk_ws(nrj, m, l) + (int64_t)nrj * l);
+        int ws = S.alloc(rk_ws(nrj, m, l) + (int64_t)nrj * l + (mixed ? m * l + rand_ws(nrj, m, l) : 0));
         t.ws = S.chunk_loc(ws);
         std::vector<int> reads;
         for (int i = 0; i < 2; ++i)
@@ -1208,7 +1212,7 @@ struct Sym {
       t.cap = out.cap;
       int64_t l = (int64_t)col[0].cap + col[1].cap;
       if (l > HM_LMAX_HOST) throw HmError(HMAT_ERR_RANK, "merged width exceeds the truncation limit");
-      int ws = S.alloc(rk_ws(m, n, l) + (int64_t)m * l);
+      int ws = S.alloc(rk_ws(m, n, l) + (int64_t)m * l + (mixed ? n * l + rand_ws(m, n, l) : 0));
       t.ws = S.chunk_loc(ws);
       S.emit(t, {col[0].obj, col[1].obj}, {out.obj, S.chunk_obj(ws)});
       S.release(ws);
@@ -1369,7 +1373,46 @@ struct RunResult {
   double flops = 0.0;
   unsigned long long type_ns[16] = {0}, type_cnt[16] = {0}, wait_ns = 0;
   unsigned long long rand_ok = 0, rand_fail = 0;
+  unsigned long long bad[6] = {0, 0, 0, 0, 0, 0};
+  std::vector<uint32_t> task_ns;  // filled when profiling
 };
+
+// HMAT_PROFILE_TASKS=1 records every task's duration and reports the
+// measured critical path (longest chain of task durations) by task type.
+bool profile_tasks() {
+  const char* v = std::getenv("HMAT_PROFILE_TASKS");
+  return v && v[0] == '1';
+}
+
+void critical_path(const Sched& S, const std::vector<uint32_t>& ns, hmat_stats& st) {
+  size_t n = S.tasks.size();
+  std::vector<double> fin(n, 0.0);
+  std::vector<int32_t> from(n, -1);
+  for (size_t i = 0; i < n; ++i) {
+    double start = 0.0;
+    for (int64_t k = S.dep_ptr[i]; k < S.dep_ptr[i + 1]; ++k) {
+      int32_t d = S.dep_idx[(size_t)k];
+      if (fin[(size_t)d] > start) {
+        start = fin[(size_t)d];
+        from[i] = d;
+      }
+    }
+    fin[i] = start + ns[i] * 1e-9;
+  }
+  size_t last = 0;
+  for (size_t i = 1; i < n; ++i)
+    if (fin[i] > fin[last]) last = i;
+  st.cp_seconds = n ? fin[last] : 0.0;
+  for (int t = 0; t < 16; ++t) {
+    st.cp_type_seconds[t] = 0.0;
+    st.cp_type_count[t] = 0;
+  }
+  for (int64_t i = n ? (int64_t)last : -1; i >= 0; i = from[(size_t)i]) {
+    int ty = S.tasks[(size_t)i].type;
+    st.cp_type_seconds[ty] += ns[(size_t)i] * 1e-9;
+    st.cp_type_count[ty] += 1;
+  }
+}
 
 RunResult run_tasks(hmat_ctx* ctx, const Sched& S, double* hbase, int* ranks, double eps, int64_t spin_limit,
                     double* ext0, double* ext1, bool mixed = false) {
@@ -1405,9 +1448,16 @@ RunResult run_tasks(hmat_ctx* ctx, const Sched& S, double* hbase, int* ranks, do
   e.type_ns = (unsigned long long*)dmisc.p + 8;
   e.type_cnt = (unsigned long long*)dmisc.p + 24;
   e.wait_ns = (unsigned long long*)dmisc.p + 40;
+  DevBuf dtns;
+  e.task_ns = nullptr;
+  if (profile_tasks()) {
+    dtns.alloc(S.tasks.size() * sizeof(uint32_t));
+    HM_CUDA(cudaMemsetAsync(dtns.p, 0, S.tasks.size() * sizeof(uint32_t), st));
+    e.task_ns = dtns.as<uint32_t>();
+  }
   e.eps = eps;
   e.mixed = mixed ? 1 : 0;
-  e.rand_min_l = 24;
+  e.rand_min_l = 8;
   e.seed = 0x5EEDull;
   e.spin_iters = spin_limit > 0 ? spin_limit : (1ll << 28);
   e.spin_ns = 20ull * 1000000000ull;
@@ -1418,7 +1468,7 @@ RunResult run_tasks(hmat_ctx* ctx, const Sched& S, double* hbase, int* ranks, do
   HM_CUDA(cudaEventRecord(e0, st));
   HM_CUDA(launch_exec(e, grid, st));
   HM_CUDA(cudaEventRecord(e1, st));
-  unsigned long long misc[48];
+  unsigned long long misc[64];
   HM_CUDA(cudaMemcpyAsync(misc, dmisc.p, sizeof(misc), cudaMemcpyDeviceToHost, st));
   for (int i = 0; i < 16; ++i) {
     rr.type_ns[i] = misc[8 + i];
@@ -1434,6 +1484,11 @@ RunResult run_tasks(hmat_ctx* ctx, const Sched& S, double* hbase, int* ranks, do
   rr.truncations = misc[44];
   rr.rand_ok = misc[45];
   rr.rand_fail = misc[46];
+  for (int i = 0; i < 6; ++i) rr.bad[i] = misc[47 + i];
+  if (e.task_ns) {
+    rr.task_ns.resize(S.tasks.size());
+    HM_CUDA(cudaMemcpy(rr.task_ns.data(), dtns.p, S.tasks.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  }
   rr.status = (int)(misc[2] & 0xffffffffu);
   std::memcpy(&rr.flops, &misc[3], sizeof(double));
   return rr;
@@ -1856,6 +1911,13 @@ hmat_status hmat_lu(hmat_ctx* ctx, hmat* H, const hmat_opts* opts) {
     H->st.flops = rr.flops;
     H->st.rand_truncations = (int64_t)rr.rand_ok;
     H->st.rand_fallbacks = (int64_t)rr.rand_fail;
+    if (!rr.task_ns.empty()) critical_path(S, rr.task_ns, H->st);
+    if (rr.bad[0]) {
+      double sc;
+      std::memcpy(&sc, &rr.bad[5], sizeof(sc));
+      std::fprintf(stderr, "hmat_lu: non-finite randomised result redone exactly (path %llu, m %llu, n %llu, l %llu, k %llu, scale %g)\n",
+                   rr.bad[0], rr.bad[1], rr.bad[2], rr.bad[3], rr.bad[4], sc);
+    }
     for (int i = 0; i < 16; ++i) {
       H->st.type_seconds[i] = rr.type_ns[i] * 1e-9;
       H->st.type_count[i] = (int64_t)rr.type_cnt[i];
@@ -1896,7 +1958,8 @@ hmat_status hmat_solve(hmat_ctx* ctx, const hmat* LU, int trans, int64_t nrhs, d
 }
 
 hmat_status trunc_lowrank_batched(hmat_ctx* ctx, int64_t count, const int64_t* m, const int64_t* n, const int64_t* k,
-                                  double* const* U, double* const* V, double eps, int64_t* k_new) {
+                                  double* const* U, double* const* V, double eps, int64_t* k_new, int precision,
+                                  int64_t* randomised) {
   return guarded([&] {
     check_ctx(ctx);
     require(count >= 0 && (count == 0 || (m && n && k && U && V && k_new)), "trunc_lowrank_batched: bad arguments");
@@ -1906,6 +1969,7 @@ hmat_status trunc_lowrank_batched(hmat_ctx* ctx, int64_t count, const int64_t* m
     for (int64_t i = 0; i < count; ++i) {
       require(m[i] >= 0 && n[i] >= 0 && k[i] >= 0 && k[i] <= HM_LMAX_HOST, "trunc_lowrank: k must be <= 256");
       total += (2 * m[i] + n[i]) * k[i] + 2 * k[i] * k[i] + 64;
+      if (precision == HMAT_MIXED) total += (m[i] * n[i] + 2 * (m[i] + n[i]) * RMAX + n[i]) / 2 + 64;
     }
     DevBuf ws((size_t)total * sizeof(double));
     int64_t off = 0;
@@ -1921,15 +1985,18 @@ hmat_status trunc_lowrank_batched(hmat_ctx* ctx, int64_t count, const int64_t* m
       p.ws = ws.as<double>() + off;
       p.k_new = k_new + i;
       off += (2 * m[i] + n[i]) * k[i] + 2 * k[i] * k[i] + 64;
+      if (precision == HMAT_MIXED) off += (m[i] * n[i] + 2 * (m[i] + n[i]) * RMAX + n[i]) / 2 + 64;
     }
-    DevBuf dp, dst(sizeof(int));
+    DevBuf dp, dst(2 * sizeof(int));
     upload(dp, P, ctx->stream);
-    HM_CUDA(cudaMemsetAsync(dst.p, 0, sizeof(int), ctx->stream));
-    HM_CUDA(launch_trunc_batched(dp.as<TruncProblem>(), (int)count, eps, dst.as<int>(), ctx->stream));
-    int status = 0;
-    HM_CUDA(cudaMemcpyAsync(&status, dst.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    HM_CUDA(cudaMemsetAsync(dst.p, 0, 2 * sizeof(int), ctx->stream));
+    HM_CUDA(launch_trunc_batched(dp.as<TruncProblem>(), (int)count, eps, dst.as<int>(), precision == HMAT_MIXED ? 1 : 0,
+                                 ctx->stream));
+    int status[2] = {0, 0};
+    HM_CUDA(cudaMemcpyAsync(status, dst.p, sizeof(status), cudaMemcpyDeviceToHost, ctx->stream));
     HM_CUDA(cudaStreamSynchronize(ctx->stream));
-    if (status) throw HmError(status, "trunc_lowrank: device status");
+    if (randomised) *randomised = status[1];
+    if (status[0]) throw HmError(status[0], "trunc_lowrank: device status");
   });
 }
 
@@ -1942,7 +2009,7 @@ hmat_status trunc_lowrank(hmat_ctx* ctx, int64_t m, int64_t n, int64_t k, double
     DevBuf dk(sizeof(int64_t));
     double* Up = U;
     double* Vp = V;
-    hmat_status s = trunc_lowrank_batched(ctx, 1, &m, &n, &k, &Up, &Vp, eps, dk.as<int64_t>());
+    hmat_status s = trunc_lowrank_batched(ctx, 1, &m, &n, &k, &Up, &Vp, eps, dk.as<int64_t>(), HMAT_FP64, nullptr);
     if (s != HMAT_OK) throw HmError(s, g_last_error);
     HM_CUDA(cudaMemcpy(k_new, dk.p, sizeof(int64_t), cudaMemcpyDeviceToHost));
   });

@@ -66,6 +66,28 @@ __device__ void cta_copy(double* C, int ldc, const double* A, int lda, int m, in
   }
 }
 
+// true iff U (m x k) and V (n x k) hold only finite numbers
+__device__ bool cta_finite(const double* U, int ldu, int m, int k, const double* V, int ldv, int n) {
+  int bad = 0;
+  for (int idx = threadIdx.x; idx < m * k; idx += HM_THREADS)
+    if (!isfinite(U[(int64_t)(idx / m) * ldu + idx % m])) bad = 1;
+  for (int idx = threadIdx.x; idx < n * k; idx += HM_THREADS)
+    if (!isfinite(V[(int64_t)(idx / n) * ldv + idx % n])) bad = 1;
+  return !__syncthreads_or(bad);
+}
+
+// first randomised truncation whose result was not finite (it is then redone
+// by the exact path): path, m, n, l, k, scale
+__device__ void record_bad(const ExecEnv& e, int path, int m, int n, int l, int k, double scale) {
+  if (threadIdx.x == 0 && atomicCAS(e.counters + 3, 0ull, (unsigned long long)path) == 0ull) {
+    e.counters[4] = (unsigned long long)m;
+    e.counters[5] = (unsigned long long)n;
+    e.counters[6] = (unsigned long long)l;
+    e.counters[7] = (unsigned long long)k;
+    e.counters[8] = __double_as_longlong(scale);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Task bodies
 // ---------------------------------------------------------------------------
@@ -187,7 +209,65 @@ __device__ void task_rkadd(const ExecEnv& e, const HTask& t, Smem& s) {
   }
   __syncthreads();
   double f = 0.0;
-  if (e.mixed && e.eps > 0.0 && l >= e.rand_min_l) {
+  if (e.mixed && e.eps >= HM_F32_MIN_EPS && l >= e.rand_min_l && (int64_t)m * n <= HM_F32_MAX_MN &&
+      (int64_t)m * n <= 4 * (int64_t)(m + n) * l) {
+    // Mixed precision: M formed once (FP64 sums, FP32 copy), FP32 sketch and
+    // projections, FP64 core.
+    int Rr = m < n ? m : n;
+    if (Rr > HM_RMAX) Rr = HM_RMAX;
+    int64_t mn = (int64_t)m * n, fl = mn + 2 * (int64_t)(m + n) * Rr;
+    float* gfw = (float*)(Jg + 2 * (int64_t)l * l);
+    float* fw = fl <= HM_F32_SMEM ? (float*)s.jac : gfw;
+    uint32_t* Om = (uint32_t*)(gfw + fl);
+    float* Mf = fw;
+    // two passes: the largest entry, then the scaled FP32 copy
+    auto entry = [&](int idx) {
+      int i = idx % m, c = idx / m;
+      double v;
+      if (aid) v = btr ? B[(int64_t)c * t.ldb + i] : B[(int64_t)i * t.ldb + c];
+      else if (bid) v = A[(int64_t)c * t.lda + i];
+      else {
+        v = 0.0;
+        for (int j = 0; j < w; ++j)
+          v += A[(int64_t)j * t.lda + i] * (btr ? B[(int64_t)c * t.ldb + j] : B[(int64_t)j * t.ldb + c]);
+      }
+      v *= t.alpha;
+      for (int j = 0; j < kin; ++j) v += Uin[(int64_t)j * t.ldc + i] * Vin[(int64_t)j * t.ldd + c];
+      return v;
+    };
+    double mx = 0.0;
+    for (int idx = threadIdx.x; idx < mn; idx += HM_THREADS) mx = fmax(mx, fabs(entry(idx)));
+    mx = block_max(mx, s);
+    double inv = mx > 0.0 ? 1.0 / mx : 0.0;
+    int nonfinite = 0;
+    for (int idx = threadIdx.x; idx < mn; idx += HM_THREADS) {
+      double v = entry(idx);
+      if (!isfinite(v)) nonfinite = 1;
+      Mf[idx] = (float)(v * inv);
+    }
+    if (__syncthreads_or(nonfinite)) record_bad(e, 9, m, n, l, kin, mx);
+    f += 2.0 * m * n * (double)(kin + ((aid || bid) ? 0 : w));
+    int r0 = kin + 6;
+    if (r0 < 8) r0 = 8;
+    uint64_t seed = e.seed ^ ((uint64_t)blockIdx.x << 40) ^ (uint64_t)(t.rout + 1) * 0x9E3779B97F4A7C15ull;
+    int ok = 0;
+    int k = trunc_rand32(Mf, m, n, mx, Mf + mn, Om, e.eps, t.cap, Uout, t.lde, Vout, t.ldf, e.status, s, &f, &ok,
+                         seed, r0);
+    if (ok && !cta_finite(Uout, t.lde, m, k, Vout, t.ldf, n)) {
+      ok = 0;
+      record_bad(e, 1, m, n, l, k, mx);
+    }
+    if (ok) {
+      if (threadIdx.x == 0) {
+        if (t.rout >= 0) e.ranks[t.rout] = k;
+        atomicAdd(e.counters, 1ull);
+        atomicAdd(e.counters + 1, 1ull);
+        atomicAdd(e.flops, f);
+      }
+      return;
+    }
+    if (threadIdx.x == 0) atomicAdd(e.counters + 2, 1ull);
+  } else if (e.mixed && e.eps > 0.0 && l >= e.rand_min_l) {
     // Randomised truncation; M explicit when that is the smaller form.
     double* R = Jg + 2 * (int64_t)l * l;
     const double* Md = nullptr;
@@ -280,6 +360,110 @@ __device__ void task_rowmerge(const ExecEnv& e, const HTask& t, Smem& s) {
   cta_copy(SA1, m, loc(e, t.c), t.ldc, m, k1, false, 1.0);
   cta_copy(SB1, n1, loc(e, t.d), t.ldd, n1, k1, false, 1.0);
   __syncthreads();
+  double f = 0.0;
+  int l = k0 + k1;
+  int n = n0 + n1;
+  if (e.mixed && e.eps >= HM_F32_MIN_EPS && l >= e.rand_min_l && (int64_t)m * n <= HM_F32_MAX_MN &&
+      (int64_t)m * n <= 4 * (int64_t)(m + n) * l) {
+    int Rr = m < n ? m : n;
+    if (Rr > HM_RMAX) Rr = HM_RMAX;
+    int64_t mn = (int64_t)m * n, fl = mn + 2 * (int64_t)(m + n) * Rr;
+    float* gfw = (float*)(Jg + 2 * (int64_t)l * l);
+    float* fw = fl <= HM_F32_SMEM ? (float*)s.jac : gfw;
+    uint32_t* Om = (uint32_t*)(gfw + fl);
+    float* Mf = fw;
+    auto entry = [&](int idx) {
+      int i = idx % m, c = idx / m;
+      double v = 0.0;
+      if (c < n0) {
+        for (int j = 0; j < k0; ++j) v += SA0[(int64_t)j * m + i] * SB0[(int64_t)j * n0 + c];
+      } else {
+        for (int j = 0; j < k1; ++j) v += SA1[(int64_t)j * m + i] * SB1[(int64_t)j * n1 + (c - n0)];
+      }
+      return v;
+    };
+    double mx = 0.0;
+    for (int idx = threadIdx.x; idx < mn; idx += HM_THREADS) mx = fmax(mx, fabs(entry(idx)));
+    mx = block_max(mx, s);
+    double inv = mx > 0.0 ? 1.0 / mx : 0.0;
+    for (int idx = threadIdx.x; idx < mn; idx += HM_THREADS) Mf[idx] = (float)(entry(idx) * inv);
+    __syncthreads();
+    f += 2.0 * m * (double)(n0 * k0 + n1 * k1);
+    int r0 = (k0 > k1 ? k0 : k1) + 6;
+    if (r0 < 8) r0 = 8;
+    uint64_t seed = e.seed ^ ((uint64_t)blockIdx.x << 40) ^ (uint64_t)(t.rout + 7) * 0x9E3779B97F4A7C15ull;
+    int ok = 0;
+    int k = trunc_rand32(Mf, m, n, mx, Mf + mn, Om, e.eps, t.cap, Uout, t.lde, Vout, t.ldf, e.status, s, &f, &ok,
+                         seed, r0);
+    if (ok && !cta_finite(Uout, t.lde, m, k, Vout, t.ldf, n)) {
+      ok = 0;
+      record_bad(e, 2, m, n, l, k, mx);
+    }
+    if (ok) {
+      if (threadIdx.x == 0) {
+        if (t.rout >= 0) e.ranks[t.rout] = k;
+        atomicAdd(e.counters, 1ull);
+        atomicAdd(e.counters + 1, 1ull);
+        atomicAdd(e.flops, f);
+      }
+      return;
+    }
+    if (threadIdx.x == 0) atomicAdd(e.counters + 2, 1ull);
+  } else if (e.mixed && e.eps > 0.0 && l >= e.rand_min_l) {
+    // [A_0 A_1] blockdiag(B_0, B_1)^T with SA = [SA0 SA1] (contiguous)
+    double* SBd = Jg + 2 * (int64_t)l * l;
+    double* R = SBd + (int64_t)n * l;
+    for (int idx = threadIdx.x; idx < n * l; idx += HM_THREADS) {
+      int i = idx % n, j = idx / n;
+      double v = 0.0;
+      if (j < k0 && i < n0) v = SB0[(int64_t)j * n0 + i];
+      else if (j >= k0 && i >= n0) v = SB1[(int64_t)(j - k0) * n1 + (i - n0)];
+      SBd[idx] = v;
+    }
+    __syncthreads();
+    const double* Md = nullptr;
+    if ((int64_t)m * n <= (int64_t)(m + n) * l) {
+      double* Mx = R;
+      R += (int64_t)m * n;
+      for (int idx = threadIdx.x; idx < m * n; idx += HM_THREADS) {
+        int i = idx % m, c = idx / m;
+        double v = 0.0;
+        if (c < n0) {
+          for (int j = 0; j < k0; ++j) v += SA0[(int64_t)j * m + i] * SB0[(int64_t)j * n0 + c];
+        } else {
+          for (int j = 0; j < k1; ++j) v += SA1[(int64_t)j * m + i] * SB1[(int64_t)j * n1 + (c - n0)];
+        }
+        Mx[idx] = v;
+      }
+      __syncthreads();
+      Md = Mx;
+      f += 2.0 * m * (double)(n0 * k0 + n1 * k1);
+    }
+    RandIn ri;
+    ri.m = m;
+    ri.n = n;
+    ri.l = l;
+    ri.Md = Md;
+    ri.SA = SA0;
+    ri.SB = SBd;
+    ri.ws = R;
+    ri.seed = e.seed ^ ((uint64_t)blockIdx.x << 40) ^ (uint64_t)(t.rout + 7) * 0x9E3779B97F4A7C15ull;
+    int r0 = (k0 > k1 ? k0 : k1) + 6;
+    if (r0 < 8) r0 = 8;
+    ri.r0 = r0;
+    int ok = 0;
+    int k = trunc_rand(ri, e.eps, t.cap, Uout, t.lde, Vout, t.ldf, e.status, s, &f, &ok);
+    if (ok) {
+      if (threadIdx.x == 0) {
+        if (t.rout >= 0) e.ranks[t.rout] = k;
+        atomicAdd(e.counters, 1ull);
+        atomicAdd(e.counters + 1, 1ull);
+        atomicAdd(e.flops, f);
+      }
+      return;
+    }
+    if (threadIdx.x == 0) atomicAdd(e.counters + 2, 1ull);
+  }
   TruncIn in;
   in.nb = 2;
   in.m = m;
@@ -293,7 +477,6 @@ __device__ void task_rowmerge(const ExecEnv& e, const HTask& t, Smem& s) {
   in.SB[1] = SB1;
   in.W = W;
   in.Jg = Jg;
-  double f = 0.0;
   int k = trunc_core(in, e.eps, t.cap, Uout, t.lde, Vout, t.ldf, e.status, s, &f);
   if (threadIdx.x == 0) {
     if (t.rout >= 0) e.ranks[t.rout] = k;
@@ -343,7 +526,7 @@ __device__ void run_task(const ExecEnv& e, const HTask& t, Smem& s) {
       cta_lu(loc(e, t.a), t.lda, t.m, e.status);
       break;
     case T_TRSM:
-      cta_trsm(t.p, loc(e, t.a), t.lda, t.m, loc(e, t.b), t.ldb, width_of(e, t.wa));
+      cta_trsm(t.p, loc(e, t.a), t.lda, t.m, loc(e, t.b), t.ldb, width_of(e, t.wa), s);
       break;
     case T_HMV:
       task_hmv(e, t, s);
@@ -436,8 +619,10 @@ __global__ void __launch_bounds__(HM_THREADS) exec_tasks(ExecEnv e) {
       run_task(e, task, s);
       __syncthreads();
       if (threadIdx.x == 0 && task.type >= 0 && task.type < 16) {
-        atomicAdd(e.type_ns + task.type, (unsigned long long)(global_ns() - cur_t0));
+        uint64_t dt = global_ns() - cur_t0;
+        atomicAdd(e.type_ns + task.type, (unsigned long long)dt);
         atomicAdd(e.type_cnt + task.type, 1ull);
+        if (e.task_ns) e.task_ns[t] = (uint32_t)(dt < 0xffffffffull ? dt : 0xffffffffull);
       }
     }
     __syncthreads();
@@ -451,7 +636,8 @@ __global__ void __launch_bounds__(HM_THREADS) exec_tasks(ExecEnv e) {
 // ---------------------------------------------------------------------------
 // Batched truncation of independent low-rank matrices in place.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(HM_THREADS) trunc_batched(const TruncProblem* probs, double eps, int* status) {
+__global__ void __launch_bounds__(HM_THREADS) trunc_batched(const TruncProblem* probs, double eps, int* status,
+                                                           int mixed) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& s = *reinterpret_cast<Smem*>(smem_raw);
   const TruncProblem P = probs[blockIdx.x];
@@ -467,6 +653,38 @@ __global__ void __launch_bounds__(HM_THREADS) trunc_batched(const TruncProblem* 
   cta_copy(SA, m, P.U, P.ldu, m, l, false, 1.0);
   cta_copy(SB, n, P.V, P.ldv, n, l, false, 1.0);
   __syncthreads();
+  int cap = l < m ? l : m;
+  if (n < cap) cap = n;
+  if (mixed && eps >= HM_F32_MIN_EPS && (int64_t)m * n <= HM_F32_MAX_MN && l > 0) {
+    int Rr = m < n ? m : n;
+    if (Rr > HM_RMAX) Rr = HM_RMAX;
+    int64_t mn = (int64_t)m * n, fl = mn + 2 * (int64_t)(m + n) * Rr;
+    float* gfw = (float*)(Jg + 2 * (int64_t)l * l);
+    float* Mf = fl <= HM_F32_SMEM ? (float*)s.jac : gfw;
+    uint32_t* Om = (uint32_t*)(gfw + fl);
+    auto entry = [&](int idx) {
+      int i = idx % m, c = idx / m;
+      double v = 0.0;
+      for (int j = 0; j < l; ++j) v += SA[(int64_t)j * m + i] * SB[(int64_t)j * n + c];
+      return v;
+    };
+    double mx = 0.0;
+    for (int idx = threadIdx.x; idx < mn; idx += HM_THREADS) mx = fmax(mx, fabs(entry(idx)));
+    mx = block_max(mx, s);
+    double inv = mx > 0.0 ? 1.0 / mx : 0.0;
+    for (int idx = threadIdx.x; idx < mn; idx += HM_THREADS) Mf[idx] = (float)(entry(idx) * inv);
+    __syncthreads();
+    int ok = 0;
+    int k = trunc_rand32(Mf, m, n, mx, Mf + mn, Om, eps, cap, P.U, P.ldu, P.V, P.ldv, status, s, nullptr, &ok,
+                         0x5EEDull + blockIdx.x, 8);
+    if (ok) {
+      if (threadIdx.x == 0) {
+        P.k_new[0] = k;
+        atomicAdd(status + 1, 1);
+      }
+      return;
+    }
+  }
   TruncIn in;
   in.nb = 1;
   in.m = m;
@@ -476,8 +694,6 @@ __global__ void __launch_bounds__(HM_THREADS) trunc_batched(const TruncProblem* 
   in.SB[0] = SB;
   in.W = W;
   in.Jg = Jg;
-  int cap = l < m ? l : m;
-  if (n < cap) cap = n;
   int k = trunc_core(in, eps, cap, P.U, P.ldu, P.V, P.ldv, status, s);
   if (threadIdx.x == 0) P.k_new[0] = k;
 }
@@ -539,10 +755,11 @@ cudaError_t exec_occupancy(int* blocks_per_sm) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, exec_tasks, HM_THREADS, sizeof(Smem));
 }
 
-cudaError_t launch_trunc_batched(const TruncProblem* probs, int count, double eps, int* status, cudaStream_t st) {
+cudaError_t launch_trunc_batched(const TruncProblem* probs, int count, double eps, int* status, int mixed,
+                                 cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(trunc_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
   if (e != cudaSuccess) return e;
-  trunc_batched<<<count, HM_THREADS, sizeof(Smem), st>>>(probs, eps, status);
+  trunc_batched<<<count, HM_THREADS, sizeof(Smem), st>>>(probs, eps, status, mixed);
   return cudaGetLastError();
 }
 

@@ -27,6 +27,7 @@ struct ExecEnv {
   unsigned long long* type_ns;   // per task type: summed execution time (ns)
   unsigned long long* type_cnt;  // per task type: tasks run
   unsigned long long* wait_ns;   // summed time CTAs spent waiting on predecessors
+  uint32_t* task_ns;             // optional: execution time of every task (profiling)
   double eps;
   int mixed;                  // randomised truncation path on
   int rand_min_l;             // smallest stacked width that takes it
@@ -53,7 +54,8 @@ struct DenseLeafDesc {
 size_t smem_bytes();
 cudaError_t exec_occupancy(int* blocks_per_sm);
 cudaError_t launch_exec(const ExecEnv& env, int grid, cudaStream_t st);
-cudaError_t launch_trunc_batched(const TruncProblem* probs, int count, double eps, int* status, cudaStream_t st);
+cudaError_t launch_trunc_batched(const TruncProblem* probs, int count, double eps, int* status, int mixed,
+                                 cudaStream_t st);
 cudaError_t launch_csr_scatter(const DenseLeafDesc* leaves, int nleaves, const int64_t* rowptr,
                                const int64_t* colidx, const double* val, const int64_t* perm, const int64_t* iperm,
                                double* hbase, unsigned long long* placed, cudaStream_t st);

@@ -69,3 +69,33 @@ def test_trunc_batched(ctx):
         assert abs(k - Co.shape[1]) <= 1
         P = from_dev(Us[i], k) @ from_dev(Vs[i], k).T
         assert np.linalg.norm(P - Co @ Do.T) <= 1e-5 * np.linalg.norm(Co @ Do.T) * 2
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-4])
+def test_trunc_batched_mixed_meets_rule(ctx, eps):
+    """Randomised range finder (FP32 sketch, FP64 core): the result meets the
+    relative Frobenius rule, and its rank is the optimal rank or a little more."""
+    import torch
+    g = hm()
+    sizes = [(64, 64, 70), (64, 128, 72), (128, 300, 20), (33, 17, 12), (200, 64, 40), (512, 512, 24)]
+    Us, Vs, data = [], [], []
+    for i, (m, n, l) in enumerate(sizes):
+        A, B = hs.lowrank_stack(m, n, l, seed=300 + i, decay=0.35)
+        Us.append(to_dev(A))
+        Vs.append(to_dev(B))
+        data.append((A, B))
+    kn = torch.zeros(len(sizes), dtype=torch.int64, device="cuda")
+    nr = g.trunc_lowrank_batched(ctx, Us, Vs, eps, kn, precision=g.HMAT_MIXED)
+    assert nr >= len(sizes) - 1
+    kn = kn.cpu().numpy()
+    for i, (A, B) in enumerate(data):
+        k = int(kn[i])
+        R = A @ B.T
+        s = np.linalg.svd(R, compute_uv=False)
+        kopt = int(np.searchsorted(-np.sqrt(np.cumsum((s ** 2)[::-1])[::-1]), -eps * np.linalg.norm(R)))
+        C, D = from_dev(Us[i], k), from_dev(Vs[i], k)
+        assert np.all(np.isfinite(C)) and np.all(np.isfinite(D))
+        err = np.linalg.norm(R - C @ D.T)
+        assert err <= eps * np.linalg.norm(R) * (1 + 1e-3)
+        assert kopt - 1 <= k <= kopt + 3
+        assert np.allclose(C.T @ C, np.eye(k), atol=1e-5)
