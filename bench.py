@@ -35,11 +35,13 @@ METRIC = "H-LU setup truncations/s (accumulated updates) vs plain FP64 at equal 
 UNIT = "truncations/s"
 TASK_NAMES = ["NOP", "LU", "TRSM", "HMV", "DENSIFY", "GEMM", "ADD", "RKADD", "ROWMERGE", "COPY", "ZERO", "RANKSET"]
 FP64_PEAK_TFLOPS = 1.25     # GB300 nominal FP64 (vector and tensor) rate, 152 SMs at up to 2070 MHz
-WORKLOADS = {"laplace3d_32": hs.laplace3d_32, "laplace3d_64": hs.laplace3d_64, "laplace2d_64": hs.laplace2d_64}
+WORKLOADS = {"laplace3d_32": hs.laplace3d_32, "laplace3d_64": hs.laplace3d_64, "laplace2d_64": hs.laplace2d_64,
+             "diffusion2d_batch64": hs.diffusion2d_batch}
 # bounded oracle sample: the same operator family, tolerance and leaf size at 16^3
 SAMPLE = {"laplace3d_32": lambda: hs.small_laplace(16, 3, 64, 1e-4),
           "laplace3d_64": lambda: hs.small_laplace(16, 3, 64, 1e-4),
-          "laplace2d_64": hs.laplace2d_64}
+          "laplace2d_64": hs.laplace2d_64,
+          "diffusion2d_batch64": lambda: hs.diffusion2d_batch()[0]}
 
 
 def measured_peaks() -> dict:
@@ -152,25 +154,31 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
-    p = WORKLOADS[args.workload]()
-    coords, csr = p.coords(), p.matrix()
+    w = WORKLOADS[args.workload]()
+    probs = w if isinstance(w, list) else [w]
+    eps = probs[0].eps
+    assert all(p.eps == eps for p in probs)
+    csrs = [p.matrix() for p in probs]
     ctx = g.Context(local_rank, stream)
     t0 = time.perf_counter()
-    ct = g.ClusterTree(ctx, coords, p.leaf)
-    bt = g.BlockTree(ctx, ct, ct, p.eta)
+    cts = [g.ClusterTree(ctx, p.coords(), p.leaf) for p in probs]
+    bts = [g.BlockTree(ctx, ct, ct, p.eta) for ct, p in zip(cts, probs)]
     tree_s = time.perf_counter() - t0
-    pristine = g.HMatrix(ctx, bt, csr)
-    work = g.HMatrix(ctx, bt, csr)
+    pristine = [g.HMatrix(ctx, bt, c) for bt, c in zip(bts, csrs)]
+    work = [g.HMatrix(ctx, bt, c) for bt, c in zip(bts, csrs)]
     flush = torch.empty(int(256 * 2**20) // 4, dtype=torch.float32, device=dev)
-
     prec = g.HMAT_MIXED if args.precision == "mixed" else g.HMAT_FP64
 
     def step(precision=prec):
-        work.copy_values_from(pristine)
-        work.lu(p.eps, max_rank=args.max_rank, precision=precision)
+        for wk, pr in zip(work, pristine):
+            wk.copy_values_from(pr)
+        g.lu_batched(ctx, work, eps, max_rank=args.max_rank, precision=precision, reuse_schedule=True)
 
-    for _ in range(args.warmup):
+    sched_first = None
+    for i in range(args.warmup):
         step()
+        if i == 0:
+            sched_first = work[0].stats()["schedule_seconds"]
     torch.cuda.synchronize()
     clocks = ClockSampler(local_rank) if rank == 0 else None
     if world > 1:
@@ -186,7 +194,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         ev1.record(stream)
         ev1.synchronize()
         step_ms.append(ev0.elapsed_time(ev1))
-        st = work.stats()
+        st = work[0].stats()  # batch totals
         kern_ms.append(1e3 * st["factor_seconds"])
         flops.append(st["flops"])
         truncs.append(st["truncations"])
@@ -202,24 +210,24 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_s = float(t.item())
     value = world * sum(truncs) / total_s
-    st = work.stats()
+    st = work[0].stats()
 
     # end to end through the public API with host buffers: CSR -> device,
     # factorisation, ranks back to the host, every step
-    h2d = 8 * (csr.rowptr.size + csr.colidx.size + csr.val.size) + 16 * csr.n
-    nblocks = g.lib().hmat_blocktree_size(bt.h)
-    d2h = 8 * nblocks
+    h2d = sum(8 * (c.rowptr.size + c.colidx.size + c.val.size) + 16 * c.n for c in csrs)
+    d2h = sum(8 * g.lib().hmat_blocktree_size(bt.h) for bt in bts)
     e2e_times = []
     for i in range(1 + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        H = g.HMatrix(ctx, bt, csr)
-        H.lu(p.eps, max_rank=args.max_rank, precision=prec)
-        H.ranks()
+        Hs = [g.HMatrix(ctx, bt, c) for bt, c in zip(bts, csrs)]
+        g.lu_batched(ctx, Hs, eps, max_rank=args.max_rank, precision=prec)
+        for H in Hs:
+            H.ranks()
         torch.cuda.synchronize()
         if i >= 1:
             e2e_times.append(time.perf_counter() - t0)
-        del H
+        del Hs
     e2e_s = sum(e2e_times)
     if world > 1:
         t = torch.tensor([e2e_s], device=dev)
@@ -229,40 +237,45 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
 
     if rank != 0:
         return
-    # preconditioner quality of the last factorisation (power iteration with the GPU solves)
-    perr = precond_error(g, work, ct, csr, p)
+    # preconditioner quality of the last factorisation (power iteration with the
+    # GPU solves); batches report their first instances
+    nq = min(len(probs), 4)
+    perr = [precond_error(g, work[i], cts[i], csrs[i], probs[i]) for i in range(nq)]
     types = {name: {"count": st["type_count"][i], "cta_s": st["type_seconds"][i]}
              for i, name in enumerate(TASK_NAMES) if st["type_count"][i]}
-    # the plain FP64 accumulated form on the same GPU, same matrix: the comparator
+    # the plain FP64 accumulated form on the same GPU, same matrices: the comparator
     fp64 = None
     if args.precision == "mixed" and not args.no_fp64:
         ev0.record(stream)
         step(g.HMAT_FP64)
         ev1.record(stream)
         ev1.synchronize()
-        s64 = work.stats()
+        s64 = work[0].stats()
         fp64 = {"setup_s": ev0.elapsed_time(ev1) / 1e3, "truncations": s64["truncations"],
                 "value": s64["truncations"] / (ev0.elapsed_time(ev1) / 1e3),
-                "precond_error": precond_error(g, work, ct, csr, p),
+                "precond_error": [precond_error(g, work[i], cts[i], csrs[i], probs[i]) for i in range(nq)],
                 "kernel_s": s64["factor_seconds"], "flops": s64["flops"]}
         fp64["speedup_of_chosen_form"] = fp64["setup_s"] / (statistics.mean(step_ms) / 1e3)
     peaks = measured_peaks()
     avg_kern_s = statistics.mean(kern_ms) / 1e3
     achieved = statistics.mean(flops) / avg_kern_s / 1e12
+    name = args.workload if len(probs) > 1 else probs[0].name
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f64+f32sketch", "data": "synthetic",
-        "config": {"workload": p.name, "n": p.n, "leaf": p.leaf, "eta": p.eta, "eps": p.eps,
-                   "precision": args.precision,
+        "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
+        "config": {"workload": name, "instances": len(probs), "n": sum(p.n for p in probs), "leaf": probs[0].leaf,
+                   "eta": probs[0].eta, "eps": eps, "precision": args.precision,
                    "max_rank": args.max_rank or 64, "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"replicas{world}"},
         "setup_s": statistics.mean(step_ms) / 1e3,
         "truncations_per_step": int(statistics.mean(truncs)),
         "tasks_per_step": int(statistics.mean(tasks)),
         "schedule_s": statistics.mean(sched),
+        "schedule_s_first_call": sched_first,
+        "schedule_note": "timed steps reuse the kept schedule (reuse_schedule); e2e builds it every step",
         "tree_build_s": tree_s,
-        "precond_error": perr,
+        "precond_error": perr if len(probs) > 1 else perr[0],
         "randomised_truncations": st["rand_truncations"], "randomised_fallbacks": st["rand_fallbacks"],
         "plain_fp64": fp64,
         "task_types": types,
@@ -272,7 +285,8 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
                      "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                      "kernel": "exec_tasks", "kernel_ms": statistics.mean(kern_ms),
                      "flops_per_launch": statistics.mean(flops),
-                     "peak_note": "FP64 nominal (no measured FP64 peak in MEASURED_PEAKS.json)"},
+                     "peak_note": "FP64 nominal (no measured FP64 peak in MEASURED_PEAKS.json); "
+                                  "counts FP64 operations only"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": 1e3 * e2e_s / args.steps},
         "clocks": clk,

@@ -170,6 +170,23 @@ class RFFField:
         return out * math.sqrt(2.0 / M)
 
 
+    def grid(self, axes) -> np.ndarray:
+        """g on the tensor grid axes[0] x axes[1] (x ...), axis 0 fastest, as a
+        flat array.  cos(w.x + phi) = Re(e^{i phi} prod_a e^{i w_a x_a}), so the
+        grid of values is a complex matrix product over the M features."""
+        M = self.phi.shape[0]
+        E = [np.exp(1j * np.outer(self.omega[:, a], ax)) for a, ax in enumerate(axes)]  # (M, n_a)
+        w = np.exp(1j * self.phi)
+        if len(axes) == 2:
+            G = ((E[0] * w[:, None]).T @ E[1]).real  # (n0, n1)
+            return G.T.ravel() * math.sqrt(2.0 / M)
+        out = np.empty((len(axes[2]), len(axes[1]), len(axes[0])))
+        for k in range(len(axes[2])):
+            G = ((E[0] * (w * E[2][:, k])[:, None]).T @ E[1]).real
+            out[k] = G.T
+        return out.ravel() * math.sqrt(2.0 / M)
+
+
 def rff_field(d: int, lc: float, seed: int, M: int = 2048) -> RFFField:
     omega = normal(seed, M * d).reshape(M, d) / lc
     phi = 2.0 * math.pi * uniform(seed ^ 0x5A5A5A5A, M)
@@ -179,14 +196,25 @@ def rff_field(d: int, lc: float, seed: int, M: int = 2048) -> RFFField:
 def diffusion(N: int, d: int, field: RFFField) -> CSR:
     """-div(k grad u) with k = exp(g), g a seeded field; face coefficients are
     k at the face midpoints (between a point and its neighbour, or the boundary
-    point).  Scaled by h^2."""
+    point).  Scaled by h^2.  Each of the (N+1) N^(d-1) faces per axis is
+    evaluated once: face f along an axis sits at (f + 1/2) h."""
     h = 1.0 / (N + 1)
-    x = grid_coords(N, d)
+    ax = (np.arange(N, dtype=np.float64) + 1.0) * h
+    fx = (np.arange(N + 1, dtype=np.float64) + 0.5) * h
+    kf = []
+    for a in range(d):
+        axes = [fx if b == a else ax for b in range(d)]
+        kf.append(np.exp(field.grid(axes)))  # lexicographic, axis 0 fastest
 
     def coeff(p, a, s):
-        mid = x[p].copy()
-        mid[:, a] += 0.5 * s * h
-        return np.exp(field(mid))
+        sub = [(p // (N ** b)) % N for b in range(d)]
+        f = sub[a] + (1 if s > 0 else 0)
+        stride = 1
+        idx = np.zeros_like(p)
+        for b in range(d):
+            idx += (f if b == a else sub[b]) * stride
+            stride *= (N + 1) if b == a else N
+        return kf[a][idx]
 
     return _assemble(N, d, coeff)
 

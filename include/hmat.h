@@ -57,13 +57,20 @@ typedef struct hmat hmat;
  *             singular triplets and reports HMAT_ERR_RANK.
  *  precision  HMAT_FP64 or HMAT_MIXED (see hmat_lu).
  *  spin_limit iterations of a bounded device-side dependency wait before it
- *             gives up with HMAT_ERR_TIMEOUT (<= 0: library default). */
+ *             gives up with HMAT_ERR_TIMEOUT (<= 0: library default).
+ *  reuse_schedule  non-zero: hmat_lu keeps the task schedule it builds (host
+ *             list, device copy and scratch arena) with the first matrix and
+ *             reuses it when called again on the same matrices with the same
+ *             trees, initial zero pattern, max_rank and precision (the
+ *             schedule never depends on the values).  The kept schedule is
+ *             freed with the matrix. */
 enum { HMAT_FP64 = 0, HMAT_MIXED = 1 };
 typedef struct {
   double eps;
   int64_t max_rank;
   int precision;
   int64_t spin_limit;
+  int reuse_schedule;
 } hmat_opts;
 
 typedef struct {
@@ -86,6 +93,7 @@ typedef struct {
   double type_seconds[16];/* summed CTA time per task type of the last hmat_lu  */
   int64_t type_count[16]; /* tasks run per task type                            */
   double wait_seconds;    /* summed CTA time waiting on predecessors            */
+  int schedule_reused;    /* 1 if the last hmat_lu reused a kept schedule       */
   int64_t rand_truncations; /* truncations done by the randomised path (MIXED)  */
   int64_t rand_fallbacks;   /* randomised attempts that fell back to QR + SVD   */
   /* Filled when the environment sets HMAT_PROFILE_TASKS=1: the measured
@@ -168,6 +176,12 @@ hmat_status hmat_addeval(hmat_ctx* ctx, const hmat* H, double alpha, int trans, 
  * leaf LU.  Returns the device status (HMAT_ERR_SINGULAR, _RANK, _TIMEOUT,
  * _NONFINITE) after synchronising the stream. */
 hmat_status hmat_lu(hmat_ctx* ctx, hmat* H, const hmat_opts* opts);
+
+/* hmat_lu of count independent H-matrices (different trees and sizes allowed,
+ * same context) in one schedule and ONE persistent kernel launch, so that the
+ * instances fill the GPU together.  Each matrix is factored in place exactly
+ * as by hmat_lu; the statistics of every instance report the batch's totals. */
+hmat_status hmat_lu_batched(hmat_ctx* ctx, hmat** G, int count, const hmat_opts* opts);
 
 /* Host-only analysis of the schedule hmat_lu would run for this matrix (no
  * device is touched): fills tasks, levels (longest dependency chain),

@@ -35,7 +35,7 @@ EXPORTS = ["hmat_last_error", "hmat_ctx_create", "hmat_ctx_destroy", "hmat_clust
            "hmat_blocktree_build", "hmat_blocktree_size", "hmat_blocktree_nodes", "hmat_btree_destroy",
            "hmat_create_from_csr", "hmat_destroy", "hmat_to_dense", "hmat_addeval", "hmat_lu", "hmat_solve",
            "trunc_lowrank", "trunc_lowrank_batched", "hmat_stats_get", "hmat_ranks", "hmat_copy_values",
-           "hmat_analyze_lu", "trunc_lowrank_noalloc"]
+           "hmat_analyze_lu", "trunc_lowrank_noalloc", "hmat_lu_batched"]
 
 
 class HmatError(RuntimeError):
@@ -46,7 +46,7 @@ class HmatError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("max_rank", ctypes.c_int64), ("precision", ctypes.c_int),
-                ("spin_limit", ctypes.c_int64)]
+                ("spin_limit", ctypes.c_int64), ("reuse_schedule", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -57,7 +57,8 @@ class Stats(ctypes.Structure):
                 ("schedule_seconds", ctypes.c_double), ("device_bytes", ctypes.c_int64), ("status", ctypes.c_int),
                 ("levels", ctypes.c_int64), ("critical_flops", ctypes.c_double), ("est_flops", ctypes.c_double),
                 ("type_seconds", ctypes.c_double * 16), ("type_count", ctypes.c_int64 * 16),
-                ("wait_seconds", ctypes.c_double), ("rand_truncations", ctypes.c_int64),
+                ("wait_seconds", ctypes.c_double), ("schedule_reused", ctypes.c_int),
+                ("rand_truncations", ctypes.c_int64),
                 ("rand_fallbacks", ctypes.c_int64), ("cp_seconds", ctypes.c_double),
                 ("cp_type_seconds", ctypes.c_double * 16), ("cp_type_count", ctypes.c_int64 * 16)]
 
@@ -202,8 +203,9 @@ class HMatrix:
     def copy_values_from(self, src: "HMatrix"):
         _check(lib().hmat_copy_values(self.ctx.h, self.h, src.h))
 
-    def lu(self, eps: float, max_rank: int = 0, precision: int = HMAT_FP64, spin_limit: int = 0):
-        o = Opts(eps, max_rank, precision, spin_limit)
+    def lu(self, eps: float, max_rank: int = 0, precision: int = HMAT_FP64, spin_limit: int = 0,
+           reuse_schedule: bool = False):
+        o = Opts(eps, max_rank, precision, spin_limit, int(reuse_schedule))
         _check(lib().hmat_lu(self.ctx.h, self.h, ctypes.byref(o)))
 
     def to_dense(self, out):
@@ -230,12 +232,20 @@ class HMatrix:
         return r
 
 
+def lu_batched(ctx: Context, Hs, eps: float, max_rank: int = 0, precision: int = HMAT_FP64, spin_limit: int = 0,
+               reuse_schedule: bool = False):
+    """hmat_lu_batched: factor the HMatrix objects Hs together in one launch."""
+    arr = (ctypes.c_void_p * len(Hs))(*[H.h.value for H in Hs])
+    o = Opts(eps, max_rank, precision, spin_limit, int(reuse_schedule))
+    _check(lib().hmat_lu_batched(ctx.h, arr, ctypes.c_int(len(Hs)), ctypes.byref(o)))
+
+
 def analyze_lu(bt: BlockTree, csr, eps: float = 0.0, max_rank: int = 0) -> dict:
     """Host-only analysis of the H-LU schedule (hmat_analyze_lu)."""
     rp = np.ascontiguousarray(csr.rowptr, np.int64)
     ci = np.ascontiguousarray(csr.colidx, np.int64)
     va = np.ascontiguousarray(csr.val, np.float64)
-    o = Opts(eps, max_rank, HMAT_FP64, 0)
+    o = Opts(eps, max_rank, HMAT_FP64, 0, 0)
     s = Stats()
     _check(lib().hmat_analyze_lu(bt.h, ctypes.c_int64(csr.n), _hp(rp, I64P), _hp(ci, I64P), _hp(va, F64P),
                                  ctypes.byref(o), ctypes.byref(s)))

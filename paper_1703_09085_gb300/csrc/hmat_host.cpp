@@ -252,7 +252,10 @@ int bt_rec(hmat_btree& B, int t, int s, int level, int parent, double eta) {
 // ===========================================================================
 // H-matrix: device storage of every leaf
 // ===========================================================================
+struct SchedCache;
+
 struct hmat {
+  std::shared_ptr<SchedCache> cache;  // schedule kept by hmat_lu(reuse_schedule)
   hmat_ctx* ctx = nullptr;
   const hmat_btree* bt = nullptr;
   int64_t n = 0;
@@ -292,9 +295,17 @@ struct Sched {
     int64_t off;
     int cls;
     int obj;
+    int pool;
   };
   std::vector<Chunk> chunks;
-  std::vector<std::deque<int>> freelist = std::vector<std::deque<int>>(64);
+  // Free lists per pool and size class.  Independent instances of a batch use
+  // separate pools, so reusing scratch never orders one instance after another.
+  std::vector<std::vector<std::deque<int>>> pools = std::vector<std::vector<std::deque<int>>>(1, std::vector<std::deque<int>>(64));
+  int pool = 0;
+  void set_pool(int p) {
+    while ((int)pools.size() <= p) pools.emplace_back(64);
+    pool = p;
+  }
   int64_t ws_top = 0;
   std::vector<int32_t> depbuf;
   std::vector<int32_t> level;   // longest chain of predecessors (ASAP level)
@@ -353,7 +364,7 @@ struct Sched {
   }
   int alloc(int64_t dbl) {
     int c = cls_of(std::max<int64_t>(dbl, 1));
-    auto& fl = freelist[(size_t)c];
+    auto& fl = pools[(size_t)pool][(size_t)c];
     if (fl.size() > keep(c)) {
       int id = fl.front();
       fl.pop_front();
@@ -363,11 +374,12 @@ struct Sched {
     ch.off = ws_top;
     ch.cls = c;
     ch.obj = new_obj();
+    ch.pool = pool;
     ws_top += (int64_t)1 << c;
     chunks.push_back(ch);
     return (int)chunks.size() - 1;
   }
-  void release(int id) { freelist[(size_t)chunks[(size_t)id].cls].push_back(id); }
+  void release(int id) { pools[(size_t)chunks[(size_t)id].pool][(size_t)chunks[(size_t)id].cls].push_back(id); }
   int64_t chunk_loc(int id) const { return tag_ws(chunks[(size_t)id].off); }
   int chunk_obj(int id) const { return chunks[(size_t)id].obj; }
 
@@ -553,19 +565,29 @@ struct Sym {
   bool mixed = false;
   std::vector<const hmat*> mats;
   std::vector<int> objbase;
+  std::vector<int64_t> hoffs;
+  std::vector<int> slotbases;
 
   Sym(Sched& s, const hmat_ctree& rt, const hmat_ctree& ct, int64_t mr) : S(s), RT(rt), CT(ct), maxrank(mr) {}
 
-  void add_matrix(const hmat* M) {
+  // A matrix whose storage sits hoff doubles from the run's storage base and
+  // whose leaf rank slots start at slot slotbase (batches of instances).
+  void add_matrix(const hmat* M, int64_t hoff = 0, int slotbase = 0) {
     mats.push_back(M);
     objbase.push_back((int)S.objs.size());
+    hoffs.push_back(hoff);
+    slotbases.push_back(slotbase);
     for (size_t b = 0; b < M->bt->nodes.size(); ++b) S.new_obj();
   }
-  int obj_of(const hmat* M, int b) const {
+  size_t mat_index(const hmat* M) const {
     for (size_t i = 0; i < mats.size(); ++i)
-      if (mats[i] == M) return objbase[i] + b;
+      if (mats[i] == M) return i;
     throw HmError(HMAT_ERR_INTERNAL, "unknown matrix");
   }
+  int obj_of(const hmat* M, int b) const { return objbase[mat_index(M)] + b; }
+  int64_t hl(const hmat* M, int b) const { return M->loc[(size_t)b] + hoffs[mat_index(M)]; }
+  int64_t hv(const hmat* M, int b) const { return M->vloc[(size_t)b] + hoffs[mat_index(M)]; }
+  int sl(const hmat* M, int b) const { return M->slot[(size_t)b] + slotbases[mat_index(M)]; }
   const CNodeH& rc(int t) const { return RT.nodes[(size_t)t]; }
   const CNodeH& cc(int r) const { return CT.nodes[(size_t)r]; }
   int capof(int64_t m, int64_t n) const { return (int)std::min<int64_t>(std::min(m, n), maxrank); }
@@ -589,9 +611,9 @@ struct Sym {
     L.coff = (int)(M->sc(b).off - c0);
     L.lda = (int)M->rows(b);
     L.ldb = (int)M->cols(b);
-    L.a = M->loc[(size_t)b];
-    L.b = nd.kind == 2 ? M->vloc[(size_t)b] : -1;
-    L.rank_slot = nd.kind == 2 ? M->slot[(size_t)b] : -1;
+    L.a = hl(M, b);
+    L.b = nd.kind == 2 ? hv(M, b) : -1;
+    L.rank_slot = nd.kind == 2 ? sl(M, b) : -1;
     out.push_back(L);
     objs.push_back(obj_of(M, b));
   }
@@ -637,7 +659,7 @@ struct Sym {
       HTask t = blank(T_TRSM);
       t.p = kind;
       t.m = (int)M->rows(d);
-      t.a = M->loc[(size_t)d];
+      t.a = hl(M, d);
       t.lda = (int)M->rows(d);
       t.b = x;
       t.ldb = ldx;
@@ -701,7 +723,7 @@ struct Sym {
         tc.flags = F_TRANS;
         tc.m = ns;
         tc.n = nt;
-        tc.a = X->loc[(size_t)xb];
+        tc.a = hl(X, xb);
         tc.lda = nt;
         tc.c = S.chunk_loc(cT);
         tc.ldc = ns;
@@ -717,7 +739,7 @@ struct Sym {
         // Ahat = N_X (t x s), Bhat = Y^T (r x s)
         int cB = scratch((int64_t)nr * ns, P);
         densify(Y, yb, true, S.chunk_loc(cB), nr, S.chunk_obj(cB));
-        P.a = X->loc[(size_t)xb];
+        P.a = hl(X, xb);
         P.lda = nt;
         P.objs.push_back(xobj);
         P.b = S.chunk_loc(cB);
@@ -733,7 +755,7 @@ struct Sym {
       if (nr <= ns) {
         // Bhat = I, Ahat = X N_Y (t x r)
         int cA = scratch((int64_t)nt * nr, P);
-        hmv(X, xb, false, 1.0, Y->loc[(size_t)yb], ns, yobj, S.chunk_loc(cA), nt, S.chunk_obj(cA), nr, true, nt);
+        hmv(X, xb, false, 1.0, hl(Y, yb), ns, yobj, S.chunk_loc(cA), nt, S.chunk_obj(cA), nr, true, nt);
         P.bid = true;
         P.a = S.chunk_loc(cA);
         P.lda = nt;
@@ -744,7 +766,7 @@ struct Sym {
         densify(X, xb, false, S.chunk_loc(cA), nt, S.chunk_obj(cA));
         P.a = S.chunk_loc(cA);
         P.lda = nt;
-        P.b = Y->loc[(size_t)yb];
+        P.b = hl(Y, yb);
         P.ldb = ns;
         P.btr = true;
         P.objs.push_back(yobj);
@@ -757,10 +779,10 @@ struct Sym {
       }
       int xobj = obj_of(X, xb);
       int cx = X->cap[(size_t)xb];
-      int wc = width_from_slot(X->slot[(size_t)xb]);
+      int wc = width_from_slot(sl(X, xb));
       int cB = scratch((int64_t)nr * cx, P);
-      hmv(Y, yb, true, 1.0, X->vloc[(size_t)xb], ns, xobj, S.chunk_loc(cB), nr, S.chunk_obj(cB), wc, true, nr);
-      P.a = X->loc[(size_t)xb];
+      hmv(Y, yb, true, 1.0, hv(X, xb), ns, xobj, S.chunk_loc(cB), nr, S.chunk_obj(cB), wc, true, nr);
+      P.a = hl(X, xb);
       P.lda = nt;
       P.objs.push_back(xobj);
       P.b = S.chunk_loc(cB);
@@ -774,10 +796,10 @@ struct Sym {
       }
       int yobj = obj_of(Y, yb);
       int cy = Y->cap[(size_t)yb];
-      int wc = width_from_slot(Y->slot[(size_t)yb]);
+      int wc = width_from_slot(sl(Y, yb));
       int cA = scratch((int64_t)nt * cy, P);
-      hmv(X, xb, false, 1.0, Y->loc[(size_t)yb], ns, yobj, S.chunk_loc(cA), nt, S.chunk_obj(cA), wc, true, nt);
-      P.b = Y->vloc[(size_t)yb];
+      hmv(X, xb, false, 1.0, hl(Y, yb), ns, yobj, S.chunk_loc(cA), nt, S.chunk_obj(cA), wc, true, nt);
+      P.b = hv(Y, yb);
       P.ldb = nr;
       P.objs.push_back(yobj);
       P.a = S.chunk_loc(cA);
@@ -1004,7 +1026,7 @@ struct Sym {
       g.b = R.v;
       g.ldb = R.ldv;
       g.wa = R.wcode;
-      g.c = M->loc[(size_t)z.b];
+      g.c = hl(M, z.b);
       g.ldc = (int)m;
       int o = obj_of(M, z.b);
       S.emit(g, {R.obj}, {o});
@@ -1044,12 +1066,12 @@ struct Sym {
   // low-rank leaf of an H-matrix as an SLow with its own storage and slot
   SLow leaf_low(hmat* M, int b) {
     SLow L;
-    L.u = M->loc[(size_t)b];
-    L.v = M->vloc[(size_t)b];
+    L.u = hl(M, b);
+    L.v = hv(M, b);
     L.ldu = (int)M->rows(b);
     L.ldv = (int)M->cols(b);
     L.cap = M->cap[(size_t)b];
-    L.slot = M->slot[(size_t)b];
+    L.slot = sl(M, b);
     L.wcode = width_from_slot(L.slot);
     L.obj = obj_of(M, b);
     L.own = true;
@@ -1072,7 +1094,7 @@ struct Sym {
         t.alpha = 1.0;
         t.a = a.dloc;
         t.lda = (int)m;
-        t.c = z.M->loc[(size_t)z.b];
+        t.c = hl(z.M, z.b);
         t.ldc = (int)m;
         int o = obj_of(z.M, z.b);
         S.emit(t, {a.dobj}, {o});
@@ -1232,10 +1254,10 @@ struct Sym {
     int kind = G->kind(b);
     if (kind == 1) {
       if (!G->zero[(size_t)b])
-        hsolve(G, d, TRSM_L, G->loc[(size_t)b], (int)G->rows(b), obj_of(G, b), (int)G->cols(b));
+        hsolve(G, d, TRSM_L, hl(G, b), (int)G->rows(b), obj_of(G, b), (int)G->cols(b));
     } else if (kind == 2) {
       if (!G->zero[(size_t)b])
-        hsolve(G, d, TRSM_L, G->loc[(size_t)b], (int)G->rows(b), obj_of(G, b), width_from_slot(G->slot[(size_t)b]));
+        hsolve(G, d, TRSM_L, hl(G, b), (int)G->rows(b), obj_of(G, b), width_from_slot(sl(G, b)));
     } else {
       const CNodeH& t = G->tc(b);
       const CNodeH& r = G->sc(b);
@@ -1270,7 +1292,7 @@ struct Sym {
       t1.flags = F_TRANS;
       t1.m = n;
       t1.n = m;
-      t1.a = G->loc[(size_t)b];
+      t1.a = hl(G, b);
       t1.lda = m;
       t1.c = S.chunk_loc(c);
       t1.ldc = n;
@@ -1282,14 +1304,14 @@ struct Sym {
       t2.n = n;
       t2.a = S.chunk_loc(c);
       t2.lda = n;
-      t2.c = G->loc[(size_t)b];
+      t2.c = hl(G, b);
       t2.ldc = m;
       S.emit(t2, {cobj}, {bobj});
       S.release(c);
     } else if (kind == 2) {
       if (!G->zero[(size_t)b])
-        hsolve(G, d, TRSM_UT, G->vloc[(size_t)b], (int)G->cols(b), obj_of(G, b),
-               width_from_slot(G->slot[(size_t)b]));
+        hsolve(G, d, TRSM_UT, hv(G, b), (int)G->cols(b), obj_of(G, b),
+               width_from_slot(sl(G, b)));
     } else {
       const CNodeH& r = G->tc(b);
       const CNodeH& t = G->sc(b);
@@ -1322,7 +1344,7 @@ struct Sym {
       flush(acc, z);
       HTask t = blank(T_LU);
       t.m = (int)G->rows(b);
-      t.a = G->loc[(size_t)b];
+      t.a = hl(G, b);
       t.lda = t.m;
       int o = obj_of(G, b);
       S.emit(t, {}, {o});
@@ -1414,46 +1436,56 @@ void critical_path(const Sched& S, const std::vector<uint32_t>& ns, hmat_stats& 
   }
 }
 
-RunResult run_tasks(hmat_ctx* ctx, const Sched& S, double* hbase, int* ranks, double eps, int64_t spin_limit,
-                    double* ext0, double* ext1, bool mixed = false) {
-  RunResult rr;
-  if (S.tasks.empty()) return rr;
+// A schedule uploaded to the device, with its scratch arena.
+struct DevSched {
+  DevBuf tasks, ptr, idx, leaves, done, ws, misc, tns;
+  size_t ntasks = 0;
+};
+
+void upload_sched(hmat_ctx* ctx, const Sched& S, DevSched& D) {
   cudaStream_t st = ctx->stream;
-  DevBuf dtasks, dptr, didx, dleaves, ddone, dws, dmisc;
-  upload(dtasks, S.tasks, st);
-  upload(dptr, S.dep_ptr, st);
-  upload(didx, S.dep_idx, st);
-  upload(dleaves, S.leaves, st);
-  ddone.alloc(S.tasks.size() * sizeof(int));
-  HM_CUDA(cudaMemsetAsync(ddone.p, 0, S.tasks.size() * sizeof(int), st));
-  dws.alloc((size_t)std::max<int64_t>(S.ws_top, 1) * sizeof(double));
-  dmisc.alloc(64 * 8);
-  HM_CUDA(cudaMemsetAsync(dmisc.p, 0, 64 * 8, st));
+  upload(D.tasks, S.tasks, st);
+  upload(D.ptr, S.dep_ptr, st);
+  upload(D.idx, S.dep_idx, st);
+  upload(D.leaves, S.leaves, st);
+  D.done.alloc(S.tasks.size() * sizeof(int));
+  D.ws.alloc((size_t)std::max<int64_t>(S.ws_top, 1) * sizeof(double));
+  D.misc.alloc(64 * 8);
+  D.ntasks = S.tasks.size();
+}
+
+RunResult launch_sched(hmat_ctx* ctx, const Sched& S, DevSched& D, double* hbase, int* ranks, double eps,
+                       int64_t spin_limit, double* ext0, double* ext1, bool mixed) {
+  RunResult rr;
+  if (D.ntasks == 0) return rr;
+  cudaStream_t st = ctx->stream;
+  HM_CUDA(cudaMemsetAsync(D.done.p, 0, D.ntasks * sizeof(int), st));
+  HM_CUDA(cudaMemsetAsync(D.misc.p, 0, 64 * 8, st));
   ExecEnv e;
   e.hbase = hbase;
-  e.wsbase = dws.as<double>();
+  e.wsbase = D.ws.as<double>();
   e.ext0 = ext0;
   e.ext1 = ext1;
   e.ranks = ranks;
-  e.tasks = dtasks.as<HTask>();
-  e.ntasks = (long long)S.tasks.size();
-  e.dep_ptr = dptr.as<int64_t>();
-  e.dep_idx = didx.as<int32_t>();
-  e.leaves = dleaves.as<LeafRef>();
-  e.done = ddone.as<int>();
-  e.head = (unsigned long long*)dmisc.p;
-  e.counters = (unsigned long long*)dmisc.p + 44;
-  e.status = (int*)((unsigned long long*)dmisc.p + 2);
-  e.flops = (double*)((unsigned long long*)dmisc.p + 3);
-  e.type_ns = (unsigned long long*)dmisc.p + 8;
-  e.type_cnt = (unsigned long long*)dmisc.p + 24;
-  e.wait_ns = (unsigned long long*)dmisc.p + 40;
-  DevBuf dtns;
+  e.tasks = D.tasks.as<HTask>();
+  e.ntasks = (long long)D.ntasks;
+  e.dep_ptr = D.ptr.as<int64_t>();
+  e.dep_idx = D.idx.as<int32_t>();
+  e.leaves = D.leaves.as<LeafRef>();
+  e.done = D.done.as<int>();
+  void* dmp = D.misc.p;
+  e.head = (unsigned long long*)dmp;
+  e.counters = (unsigned long long*)dmp + 44;
+  e.status = (int*)((unsigned long long*)dmp + 2);
+  e.flops = (double*)((unsigned long long*)dmp + 3);
+  e.type_ns = (unsigned long long*)dmp + 8;
+  e.type_cnt = (unsigned long long*)dmp + 24;
+  e.wait_ns = (unsigned long long*)dmp + 40;
   e.task_ns = nullptr;
   if (profile_tasks()) {
-    dtns.alloc(S.tasks.size() * sizeof(uint32_t));
-    HM_CUDA(cudaMemsetAsync(dtns.p, 0, S.tasks.size() * sizeof(uint32_t), st));
-    e.task_ns = dtns.as<uint32_t>();
+    D.tns.alloc(D.ntasks * sizeof(uint32_t));
+    HM_CUDA(cudaMemsetAsync(D.tns.p, 0, D.ntasks * sizeof(uint32_t), st));
+    e.task_ns = D.tns.as<uint32_t>();
   }
   e.eps = eps;
   e.mixed = mixed ? 1 : 0;
@@ -1469,13 +1501,13 @@ RunResult run_tasks(hmat_ctx* ctx, const Sched& S, double* hbase, int* ranks, do
   HM_CUDA(launch_exec(e, grid, st));
   HM_CUDA(cudaEventRecord(e1, st));
   unsigned long long misc[64];
-  HM_CUDA(cudaMemcpyAsync(misc, dmisc.p, sizeof(misc), cudaMemcpyDeviceToHost, st));
+  HM_CUDA(cudaMemcpyAsync(misc, dmp, sizeof(misc), cudaMemcpyDeviceToHost, st));
+  HM_CUDA(cudaStreamSynchronize(st));
   for (int i = 0; i < 16; ++i) {
     rr.type_ns[i] = misc[8 + i];
     rr.type_cnt[i] = misc[24 + i];
   }
   rr.wait_ns = misc[40];
-  HM_CUDA(cudaStreamSynchronize(st));
   float ms = 0.f;
   HM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
   cudaEventDestroy(e0);
@@ -1486,12 +1518,20 @@ RunResult run_tasks(hmat_ctx* ctx, const Sched& S, double* hbase, int* ranks, do
   rr.rand_fail = misc[46];
   for (int i = 0; i < 6; ++i) rr.bad[i] = misc[47 + i];
   if (e.task_ns) {
-    rr.task_ns.resize(S.tasks.size());
-    HM_CUDA(cudaMemcpy(rr.task_ns.data(), dtns.p, S.tasks.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    rr.task_ns.resize(D.ntasks);
+    HM_CUDA(cudaMemcpy(rr.task_ns.data(), D.tns.p, D.ntasks * sizeof(uint32_t), cudaMemcpyDeviceToHost));
   }
   rr.status = (int)(misc[2] & 0xffffffffu);
   std::memcpy(&rr.flops, &misc[3], sizeof(double));
   return rr;
+}
+
+RunResult run_tasks(hmat_ctx* ctx, const Sched& S, double* hbase, int* ranks, double eps, int64_t spin_limit,
+                    double* ext0, double* ext1, bool mixed = false) {
+  DevSched D;
+  if (S.tasks.empty()) return RunResult();
+  upload_sched(ctx, S, D);
+  return launch_sched(ctx, S, D, hbase, ranks, eps, spin_limit, ext0, ext1, mixed);
 }
 
 hmat_ctx* check_ctx(hmat_ctx* ctx) {
@@ -1887,51 +1927,141 @@ hmat_status hmat_addeval(hmat_ctx* ctx, const hmat* H, double alpha, int trans, 
   });
 }
 
+}  // extern "C"
+
+// A factorisation schedule kept for reuse: it depends only on the block
+// trees, the storage layout, the initial zero pattern of the leaves, max_rank
+// and the precision, never on the values.
+struct SchedCache {
+  std::vector<const hmat*> mats;
+  std::vector<const hmat_btree*> trees;
+  std::vector<uint64_t> zero_hash;
+  std::vector<std::vector<char>> zero_after;
+  int64_t mr = 0;
+  bool mixed = false;
+  double* base = nullptr;
+  Sched S;
+  DevSched D;
+};
+
+namespace {
+uint64_t hash_flags(const std::vector<char>& v) {
+  uint64_t h = 1469598103934665603ull;  // FNV-1a
+  for (char c : v) h = (h ^ (uint64_t)(unsigned char)c) * 1099511628211ull;
+  return h ^ v.size();
+}
+
+// H-LU of count independent H-matrices in one schedule and one persistent
+// launch.  Storage locations are offsets from the lowest storage pointer of
+// the batch; each instance's leaf rank slots get their own range.
+void lu_batch(hmat_ctx* ctx, hmat* const* Hs, int count, const hmat_opts* opts) {
+  check_ctx(ctx);
+  require(Hs != nullptr && count >= 1, "no H-matrices");
+  for (int i = 0; i < count; ++i) require(Hs[i] != nullptr && Hs[i]->ctx == ctx, "null H-matrix or other context");
+  double eps = opts ? opts->eps : 0.0;
+  int64_t spin = opts ? opts->spin_limit : 0;
+  require(eps >= 0.0, "eps must be >= 0");
+  bool mixed = opts && opts->precision == HMAT_MIXED;
+  auto t0 = std::chrono::steady_clock::now();
+  double* base = Hs[0]->store.as<double>();
+  for (int i = 1; i < count; ++i) base = std::min(base, Hs[i]->store.as<double>());
+  std::vector<int> slotbase((size_t)count, 0);
+  int nslots = 0;
+  for (int i = 0; i < count; ++i) {
+    slotbase[(size_t)i] = nslots;
+    nslots += Hs[i]->nslots;
+  }
+  int64_t mr0 = (opts && opts->max_rank > 0) ? opts->max_rank : DEFAULT_MAX_RANK;
+  std::vector<uint64_t> zh((size_t)count);
+  for (int i = 0; i < count; ++i) zh[(size_t)i] = hash_flags(Hs[i]->zero);
+  bool reuse = opts && opts->reuse_schedule;
+  SchedCache* C = Hs[0]->cache.get();
+  bool hit = reuse && C && C->mixed == mixed && C->mr == mr0 && C->base == base && (int)C->mats.size() == count &&
+             C->zero_hash == zh;
+  for (int i = 0; hit && i < count; ++i) hit = C->mats[(size_t)i] == Hs[i] && C->trees[(size_t)i] == Hs[i]->bt;
+  std::shared_ptr<SchedCache> fresh;
+  if (!hit) {
+    fresh = std::make_shared<SchedCache>();
+    C = fresh.get();
+  }
+  Sched& S = C->S;
+  if (!hit) {
+  S.next_slot = nslots;
+  for (int i = 0; i < count; ++i) {
+    hmat* H = Hs[i];
+    int64_t mr = std::min<int64_t>(mr0, H->max_rank);
+    S.set_pool(i);
+    Sym sym(S, *H->bt->R, *H->bt->C, mr);
+    sym.mixed = mixed;
+    sym.add_matrix(H, (int64_t)(H->store.as<double>() - base), slotbase[(size_t)i]);
+    SAcc root = sym.acc_new(0, 0);
+    sym.lu(H, 0, root);
+  }
+  S.order_by_level();
+  upload_sched(ctx, S, C->D);
+  for (int i = 0; i < count; ++i) {
+    C->mats.push_back(Hs[i]);
+    C->trees.push_back(Hs[i]->bt);
+    C->zero_after.push_back(Hs[i]->zero);
+  }
+  C->zero_hash = zh;
+  C->mr = mr0;
+  C->mixed = mixed;
+  C->base = base;
+  if (reuse) Hs[0]->cache = fresh;
+  } else {
+    for (int i = 0; i < count; ++i) Hs[i]->zero = C->zero_after[(size_t)i];
+  }
+  double sched_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  DevBuf allranks((size_t)std::max(S.next_slot, 1) * sizeof(int));
+  for (int i = 0; i < count; ++i)
+    HM_CUDA(cudaMemcpyAsync(allranks.as<int>() + slotbase[(size_t)i], Hs[i]->ranks.p, (size_t)Hs[i]->nslots * sizeof(int),
+                            cudaMemcpyDeviceToDevice, ctx->stream));
+  RunResult rr = launch_sched(ctx, S, C->D, base, allranks.as<int>(), eps, spin, nullptr, nullptr, mixed);
+  for (int i = 0; i < count; ++i)
+    HM_CUDA(cudaMemcpyAsync(Hs[i]->ranks.p, allranks.as<int>() + slotbase[(size_t)i], (size_t)Hs[i]->nslots * sizeof(int),
+                            cudaMemcpyDeviceToDevice, ctx->stream));
+  HM_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (rr.bad[0]) {
+    double sc;
+    std::memcpy(&sc, &rr.bad[5], sizeof(sc));
+    std::fprintf(stderr, "hmat_lu: non-finite randomised result redone exactly (path %llu, m %llu, n %llu, l %llu, k %llu, scale %g)\n",
+                 rr.bad[0], rr.bad[1], rr.bad[2], rr.bad[3], rr.bad[4], sc);
+  }
+  for (int i = 0; i < count; ++i) {
+    hmat_stats& st = Hs[i]->st;  // the batch's totals, on every instance
+    st.tasks = (int64_t)S.tasks.size();
+    st.truncations = (int64_t)rr.truncations;
+    st.flops = rr.flops;
+    st.rand_truncations = (int64_t)rr.rand_ok;
+    st.rand_fallbacks = (int64_t)rr.rand_fail;
+    if (!rr.task_ns.empty()) critical_path(S, rr.task_ns, st);
+    for (int k = 0; k < 16; ++k) {
+      st.type_seconds[k] = rr.type_ns[k] * 1e-9;
+      st.type_count[k] = (int64_t)rr.type_cnt[k];
+    }
+    st.wait_seconds = rr.wait_ns * 1e-9;
+    st.factor_seconds = rr.ms * 1e-3;
+    st.schedule_seconds = sched_s;
+    st.schedule_reused = hit ? 1 : 0;
+    st.status = rr.status;
+    st.levels = S.levels();
+    st.critical_flops = S.critical_flops();
+    st.est_flops = S.est_total;
+    st.device_bytes = (int64_t)(Hs[i]->store.bytes + Hs[i]->ranks.bytes) + S.ws_top * 8;
+  }
+  if (rr.status) throw HmError(rr.status, "hmat_lu: device status " + std::to_string(rr.status));
+}
+}  // namespace
+
+extern "C" {
+
 hmat_status hmat_lu(hmat_ctx* ctx, hmat* H, const hmat_opts* opts) {
-  return guarded([&] {
-    check_ctx(ctx);
-    require(H != nullptr, "null H-matrix");
-    double eps = opts ? opts->eps : 0.0;
-    int64_t mr = (opts && opts->max_rank > 0) ? std::min<int64_t>(opts->max_rank, H->max_rank) : H->max_rank;
-    int64_t spin = opts ? opts->spin_limit : 0;
-    require(eps >= 0.0, "eps must be >= 0");
-    Sched S;
-    bool mixed = opts && opts->precision == HMAT_MIXED;
-    double sched_s = schedule_lu(H, mr, mixed, S);
-    // rank slots beyond the leaves' live in a per-call array
-    DevBuf allranks((size_t)std::max(S.next_slot, 1) * sizeof(int));
-    HM_CUDA(cudaMemcpyAsync(allranks.p, H->ranks.p, (size_t)H->nslots * sizeof(int), cudaMemcpyDeviceToDevice,
-                            ctx->stream));
-    RunResult rr = run_tasks(ctx, S, H->store.as<double>(), allranks.as<int>(), eps, spin, nullptr, nullptr, mixed);
-    HM_CUDA(cudaMemcpyAsync(H->ranks.p, allranks.p, (size_t)H->nslots * sizeof(int), cudaMemcpyDeviceToDevice,
-                            ctx->stream));
-    HM_CUDA(cudaStreamSynchronize(ctx->stream));
-    H->st.tasks = (int64_t)S.tasks.size();
-    H->st.truncations = (int64_t)rr.truncations;
-    H->st.flops = rr.flops;
-    H->st.rand_truncations = (int64_t)rr.rand_ok;
-    H->st.rand_fallbacks = (int64_t)rr.rand_fail;
-    if (!rr.task_ns.empty()) critical_path(S, rr.task_ns, H->st);
-    if (rr.bad[0]) {
-      double sc;
-      std::memcpy(&sc, &rr.bad[5], sizeof(sc));
-      std::fprintf(stderr, "hmat_lu: non-finite randomised result redone exactly (path %llu, m %llu, n %llu, l %llu, k %llu, scale %g)\n",
-                   rr.bad[0], rr.bad[1], rr.bad[2], rr.bad[3], rr.bad[4], sc);
-    }
-    for (int i = 0; i < 16; ++i) {
-      H->st.type_seconds[i] = rr.type_ns[i] * 1e-9;
-      H->st.type_count[i] = (int64_t)rr.type_cnt[i];
-    }
-    H->st.wait_seconds = rr.wait_ns * 1e-9;
-    H->st.factor_seconds = rr.ms * 1e-3;
-    H->st.schedule_seconds = sched_s;
-    H->st.status = rr.status;
-    H->st.levels = S.levels();
-    H->st.critical_flops = S.critical_flops();
-    H->st.est_flops = S.est_total;
-    H->st.device_bytes = (int64_t)(H->store.bytes + H->ranks.bytes) + S.ws_top * 8;
-    if (rr.status) throw HmError(rr.status, "hmat_lu: device status " + std::to_string(rr.status));
-  });
+  return guarded([&] { lu_batch(ctx, &H, 1, opts); });
+}
+
+hmat_status hmat_lu_batched(hmat_ctx* ctx, hmat** G, int count, const hmat_opts* opts) {
+  return guarded([&] { lu_batch(ctx, G, count, opts); });
 }
 
 hmat_status hmat_solve(hmat_ctx* ctx, const hmat* LU, int trans, int64_t nrhs, double* B, int64_t ldb) {

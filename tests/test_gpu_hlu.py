@@ -98,3 +98,61 @@ def test_hlu_truncated_matches_oracle_quality(ctx, prob, precision):
         # exceed the optimal ones by what the sketch missed
         assert rg[adm].mean() <= ro[adm].mean() + 1.0
         assert st["rand_truncations"] > 0
+
+
+def _batch_problems():
+    f = hs.rff_field(2, 0.1, seed=11)
+    return [hs.small_laplace(32, 2, 16, 1e-6),
+            hs.Problem("diffusion2d_24", 24, 2, 16, 2.0, 1e-5, kind="diffusion", lc=0.1, seed=11),
+            hs.small_laplace(8, 3, 16, 1e-4)]
+
+
+def test_hlu_batched_equals_individual_fp64(ctx):
+    """One launch for several instances gives the same factors as factoring
+    each instance on its own (every task does the same arithmetic)."""
+    g = hm()
+    probs = _batch_problems()
+    single, batch = [], []
+    for p in probs:
+        gp = GpuProblem(ctx, p)
+        gp.H.lu(p.eps)
+        single.append(gp.dense())
+        batch.append(GpuProblem(ctx, p))
+    # one eps for the whole batch: use each problem at its own eps by batching
+    # those that share it, and the smallest one for a mixed-eps check
+    for eps in sorted({p.eps for p in probs}):
+        idx = [i for i, p in enumerate(probs) if p.eps == eps]
+        g.lu_batched(ctx, [batch[i].H for i in idx], eps)
+        for i in idx:
+            D = batch[i].dense()
+            assert np.abs(D - single[i]).max() <= 1e-12 * np.abs(single[i]).max()
+
+
+def test_hlu_batched_mixed_quality(ctx):
+    g = hm()
+    probs = [hs.Problem(f"diffusion2d_{N}", N, 2, 32, 2.0, 1e-5, kind="diffusion", lc=0.1, seed=2 + N)
+             for N in (48, 56, 64)]
+    gps = [GpuProblem(ctx, p) for p in probs]
+    g.lu_batched(ctx, [gp.H for gp in gps], 1e-5, precision=g.HMAT_MIXED)
+    for p, gp in zip(probs, gps):
+        v0 = hs.start_vector(p.n, 0)
+        err_gpu = gp.precond_error(v0[gp.perm])
+        ct, bt, csr, H = oracle.setup(p)
+        H.lu(p.eps, True)
+        err_orc, _ = H.precond_error(csr, v0)
+        assert err_gpu <= 2.0 * err_orc and err_orc <= 2.0 * err_gpu
+
+
+def test_reused_schedule_gives_same_factors(ctx):
+    g = hm()
+    p = hs.small_laplace(16, 3, 64, 1e-4)
+    gp = GpuProblem(ctx, p)
+    pristine = g.HMatrix(ctx, gp.bt, gp.csr)
+    gp.H.lu(p.eps, reuse_schedule=True)
+    D1 = gp.dense()
+    assert gp.H.stats()["schedule_reused"] == 0
+    gp.H.copy_values_from(pristine)
+    gp.H.lu(p.eps, reuse_schedule=True)
+    assert gp.H.stats()["schedule_reused"] == 1
+    D2 = gp.dense()
+    assert np.array_equal(D1, D2)
