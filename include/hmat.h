@@ -46,6 +46,7 @@ typedef struct hmat_ctx hmat_ctx;
 typedef struct hmat_ctree hmat_ctree;
 typedef struct hmat_btree hmat_btree;
 typedef struct hmat hmat;
+typedef struct hmat_mlp hmat_mlp;
 
 /* Options of the arithmetic.
  *  eps        truncation tolerance: every truncation keeps the smallest rank k
@@ -63,7 +64,14 @@ typedef struct hmat hmat;
  *             reuses it when called again on the same matrices with the same
  *             trees, initial zero pattern, max_rank and precision (the
  *             schedule never depends on the values).  The kept schedule is
- *             freed with the matrix. */
+ *             freed with the matrix.
+ *  predictor  rank predictor (hmat_mlp_*) sizing the randomised truncation's
+ *             first sketch in HMAT_MIXED: max(predicted rank + 3, kz + 2)
+ *             columns, kz the larger input rank; NULL: max(kz + 6, 8).  A
+ *             sketch that misses too much is
+ *             widened and, at its limit, replaced by the exact QR + SVD.
+ *  record_training  non-zero: every exact truncation records its features
+ *             and rank (see hmat_lu_training_data). */
 enum { HMAT_FP64 = 0, HMAT_MIXED = 1 };
 typedef struct {
   double eps;
@@ -71,6 +79,8 @@ typedef struct {
   int precision;
   int64_t spin_limit;
   int reuse_schedule;
+  const hmat_mlp* predictor;
+  int record_training;
 } hmat_opts;
 
 typedef struct {
@@ -96,6 +106,9 @@ typedef struct {
   int schedule_reused;    /* 1 if the last hmat_lu reused a kept schedule       */
   int64_t rand_truncations; /* truncations done by the randomised path (MIXED)  */
   int64_t rand_fallbacks;   /* randomised attempts that fell back to QR + SVD   */
+  int64_t sketch_attempts;  /* sketches tried by the randomised truncations     */
+  int64_t sketch_columns;   /* columns sketched over all those attempts         */
+  int64_t training_pairs;   /* pairs recorded by the last hmat_lu               */
   /* Filled when the environment sets HMAT_PROFILE_TASKS=1: the measured
    * critical path (longest chain of task durations) and its make-up. */
   double cp_seconds;
@@ -232,6 +245,35 @@ hmat_status trunc_lowrank_batched(hmat_ctx* ctx, int64_t count, const int64_t* m
  * The call synchronises the context stream to return *k_new. */
 hmat_status trunc_lowrank_noalloc(hmat_ctx* ctx, int64_t m, int64_t n, int64_t k, double* U, int64_t ldu, double* V,
                                   int64_t ldv, double eps, int64_t* k_new);
+
+/* Training pairs recorded by the last hmat_lu with record_training (kept with
+ * the batch's first matrix): X (host, max x 6 floats, row-major) receives the
+ * predictor's features of the block t x r (log2 #t / 10, log2 #r / 10,
+ * log(dbar / (dist + 1e-3 dbar)) / 4 with dbar the mean of the clusters'
+ * diameters, dimension / 3, l / 16 with l the rank of the sum before
+ * truncation, log10(eps) / 4),
+ * y (host, max) log(1 + rank);
+ * *count = number of pairs held (copies min(max, count)). */
+hmat_status hmat_lu_training_data(const hmat* H, int64_t max, float* X, float* y, int64_t* count);
+
+/* Rank predictor: 3-layer MLP (6 -> 64 -> 64 -> 1, ReLU), BF16 weights and FP32
+ * accumulation, predicting log(1 + truncated rank) from the features above.
+ * Parameters: 4673 FP32 masters (W1[64][6], b1[64], W2[64][64], b2[64],
+ * w3[64], b3), evaluated through their BF16 copy.  Created with He-uniform
+ * weights from a counter-based generator seeded by seed. */
+hmat_status hmat_mlp_create(hmat_ctx* ctx, uint64_t seed, hmat_mlp** out);
+hmat_status hmat_mlp_destroy(hmat_mlp* M);
+hmat_status hmat_mlp_get_params(const hmat_mlp* M, float* out);
+hmat_status hmat_mlp_set_params(hmat_mlp* M, const float* in);
+/* y[i] = network(X[i]) for count feature rows (host arrays). */
+hmat_status hmat_mlp_forward(const hmat_mlp* M, int64_t count, const float* X, float* y);
+/* Mean squared error over the rows and its gradient (4673 floats, host) by
+ * the library's backward kernel. */
+hmat_status hmat_mlp_grad(hmat_mlp* M, int64_t count, const float* X, const float* y, float* loss, float* grad);
+/* Adam (lr, beta 0.9 / 0.999) on minibatches of size batch, epochs passes over
+ * a seeded shuffle; *final_loss (may be NULL) = MSE on the whole set after. */
+hmat_status hmat_mlp_train(hmat_mlp* M, int64_t count, const float* X, const float* y, int epochs, int batch,
+                           float lr, uint64_t seed, float* final_loss);
 
 /* Statistics of H and of its last hmat_lu (synchronous). */
 hmat_status hmat_stats_get(const hmat* H, hmat_stats* out);

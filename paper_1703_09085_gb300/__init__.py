@@ -35,7 +35,10 @@ EXPORTS = ["hmat_last_error", "hmat_ctx_create", "hmat_ctx_destroy", "hmat_clust
            "hmat_blocktree_build", "hmat_blocktree_size", "hmat_blocktree_nodes", "hmat_btree_destroy",
            "hmat_create_from_csr", "hmat_destroy", "hmat_to_dense", "hmat_addeval", "hmat_lu", "hmat_solve",
            "trunc_lowrank", "trunc_lowrank_batched", "hmat_stats_get", "hmat_ranks", "hmat_copy_values",
-           "hmat_analyze_lu", "trunc_lowrank_noalloc", "hmat_lu_batched"]
+           "hmat_analyze_lu", "trunc_lowrank_noalloc", "hmat_lu_batched", "hmat_lu_training_data",
+           "hmat_mlp_create", "hmat_mlp_destroy", "hmat_mlp_get_params", "hmat_mlp_set_params", "hmat_mlp_forward",
+           "hmat_mlp_grad", "hmat_mlp_train"]
+MLP_NPARAM = 4673
 
 
 class HmatError(RuntimeError):
@@ -46,7 +49,8 @@ class HmatError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("max_rank", ctypes.c_int64), ("precision", ctypes.c_int),
-                ("spin_limit", ctypes.c_int64), ("reuse_schedule", ctypes.c_int)]
+                ("spin_limit", ctypes.c_int64), ("reuse_schedule", ctypes.c_int), ("predictor", ctypes.c_void_p),
+                ("record_training", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -59,7 +63,8 @@ class Stats(ctypes.Structure):
                 ("type_seconds", ctypes.c_double * 16), ("type_count", ctypes.c_int64 * 16),
                 ("wait_seconds", ctypes.c_double), ("schedule_reused", ctypes.c_int),
                 ("rand_truncations", ctypes.c_int64),
-                ("rand_fallbacks", ctypes.c_int64), ("cp_seconds", ctypes.c_double),
+                ("rand_fallbacks", ctypes.c_int64), ("sketch_attempts", ctypes.c_int64),
+                ("sketch_columns", ctypes.c_int64), ("training_pairs", ctypes.c_int64), ("cp_seconds", ctypes.c_double),
                 ("cp_type_seconds", ctypes.c_double * 16), ("cp_type_count", ctypes.c_int64 * 16)]
 
     def as_dict(self) -> dict:
@@ -204,8 +209,9 @@ class HMatrix:
         _check(lib().hmat_copy_values(self.ctx.h, self.h, src.h))
 
     def lu(self, eps: float, max_rank: int = 0, precision: int = HMAT_FP64, spin_limit: int = 0,
-           reuse_schedule: bool = False):
-        o = Opts(eps, max_rank, precision, spin_limit, int(reuse_schedule))
+           reuse_schedule: bool = False, predictor=None, record_training: bool = False):
+        o = Opts(eps, max_rank, precision, spin_limit, int(reuse_schedule), predictor.h if predictor else None,
+                 int(record_training))
         _check(lib().hmat_lu(self.ctx.h, self.h, ctypes.byref(o)))
 
     def to_dense(self, out):
@@ -226,6 +232,16 @@ class HMatrix:
         _check(lib().hmat_stats_get(self.h, ctypes.byref(s)))
         return s.as_dict()
 
+    def training_data(self):
+        """(X, y) pairs recorded by the last lu(record_training=True)."""
+        cnt = ctypes.c_int64(0)
+        _check(lib().hmat_lu_training_data(self.h, ctypes.c_int64(0), None, None, ctypes.byref(cnt)))
+        X = np.zeros((cnt.value, 6), np.float32)
+        y = np.zeros(cnt.value, np.float32)
+        _check(lib().hmat_lu_training_data(self.h, ctypes.c_int64(cnt.value), _hp(X, ctypes.POINTER(ctypes.c_float)),
+                                           _hp(y, ctypes.POINTER(ctypes.c_float)), ctypes.byref(cnt)))
+        return X, y
+
     def ranks(self) -> np.ndarray:
         r = np.zeros(lib().hmat_blocktree_size(self.bt.h), np.int64)
         _check(lib().hmat_ranks(self.h, _hp(r, I64P)))
@@ -233,10 +249,11 @@ class HMatrix:
 
 
 def lu_batched(ctx: Context, Hs, eps: float, max_rank: int = 0, precision: int = HMAT_FP64, spin_limit: int = 0,
-               reuse_schedule: bool = False):
+               reuse_schedule: bool = False, predictor=None, record_training: bool = False):
     """hmat_lu_batched: factor the HMatrix objects Hs together in one launch."""
     arr = (ctypes.c_void_p * len(Hs))(*[H.h.value for H in Hs])
-    o = Opts(eps, max_rank, precision, spin_limit, int(reuse_schedule))
+    o = Opts(eps, max_rank, precision, spin_limit, int(reuse_schedule), predictor.h if predictor else None,
+             int(record_training))
     _check(lib().hmat_lu_batched(ctx.h, arr, ctypes.c_int(len(Hs)), ctypes.byref(o)))
 
 
@@ -245,7 +262,7 @@ def analyze_lu(bt: BlockTree, csr, eps: float = 0.0, max_rank: int = 0) -> dict:
     rp = np.ascontiguousarray(csr.rowptr, np.int64)
     ci = np.ascontiguousarray(csr.colidx, np.int64)
     va = np.ascontiguousarray(csr.val, np.float64)
-    o = Opts(eps, max_rank, HMAT_FP64, 0, 0)
+    o = Opts(eps, max_rank, HMAT_FP64, 0, 0, None, 0)
     s = Stats()
     _check(lib().hmat_analyze_lu(bt.h, ctypes.c_int64(csr.n), _hp(rp, I64P), _hp(ci, I64P), _hp(va, F64P),
                                  ctypes.byref(o), ctypes.byref(s)))
@@ -291,3 +308,53 @@ def trunc_lowrank_batched(ctx: Context, Us, Vs, eps: float, k_new, precision: in
                                        ctypes.c_double(eps), ctypes.c_void_p(k_new.data_ptr()), ctypes.c_int(precision),
                                        ctypes.byref(rnd)))
     return rnd.value
+
+
+F32P = ctypes.POINTER(ctypes.c_float)
+
+
+class RankPredictor:
+    """The rank predictor (hmat_mlp_*): 3-layer MLP, BF16 weights, FP32
+    accumulation, trained on the GPU by the library's own kernels."""
+
+    def __init__(self, ctx: Context, seed: int = 0):
+        h = ctypes.c_void_p()
+        _check(lib().hmat_mlp_create(ctx.h, ctypes.c_uint64(seed), ctypes.byref(h)))
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().hmat_mlp_destroy(self.h)
+            self.h = None
+
+    def params(self) -> np.ndarray:
+        p = np.zeros(MLP_NPARAM, np.float32)
+        _check(lib().hmat_mlp_get_params(self.h, _hp(p, F32P)))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        _check(lib().hmat_mlp_set_params(self.h, _hp(p, F32P)))
+
+    def forward(self, X) -> np.ndarray:
+        X = np.ascontiguousarray(X, np.float32)
+        y = np.zeros(X.shape[0], np.float32)
+        _check(lib().hmat_mlp_forward(self.h, ctypes.c_int64(X.shape[0]), _hp(X, F32P), _hp(y, F32P)))
+        return y
+
+    def grad(self, X, y):
+        X = np.ascontiguousarray(X, np.float32)
+        y = np.ascontiguousarray(y, np.float32)
+        loss = ctypes.c_float(0)
+        g = np.zeros(MLP_NPARAM, np.float32)
+        _check(lib().hmat_mlp_grad(self.h, ctypes.c_int64(X.shape[0]), _hp(X, F32P), _hp(y, F32P), ctypes.byref(loss),
+                                   _hp(g, F32P)))
+        return loss.value, g
+
+    def train(self, X, y, epochs: int = 30, batch: int = 256, lr: float = 3e-3, seed: int = 3) -> float:
+        X = np.ascontiguousarray(X, np.float32)
+        y = np.ascontiguousarray(y, np.float32)
+        loss = ctypes.c_float(0)
+        _check(lib().hmat_mlp_train(self.h, ctypes.c_int64(X.shape[0]), _hp(X, F32P), _hp(y, F32P), ctypes.c_int(epochs),
+                                    ctypes.c_int(batch), ctypes.c_float(lr), ctypes.c_uint64(seed), ctypes.byref(loss)))
+        return loss.value

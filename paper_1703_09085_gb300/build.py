@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libhmat.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["hmat_kernels.cu", "hmat_host.cpp", "hmat_noalloc.cu"]
+SOURCES = ["hmat_kernels.cu", "hmat_host.cpp", "hmat_noalloc.cu", "hmat_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
           "-I" + CSRC, "-I" + INCLUDE]

@@ -525,6 +525,7 @@ static __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 static __device__ int trunc_rand(const RandIn& in, double eps, int cap, double* U, int ldu, double* V, int ldv,
                           int* status, Smem& s, double* flops, int* ok) {
   int tid = threadIdx.x;
+  if (tid == 0) s.ivals[5] = s.ivals[6] = 0;  // attempts, columns sketched over all attempts
   int m = in.m, n = in.n, l = in.l;
   bool factored = (in.Md == nullptr);
   int rmax = HM_RMAX;
@@ -585,6 +586,11 @@ static __device__ int trunc_rand(const RandIn& in, double eps, int cap, double* 
   int r = in.r0 < 2 ? 2 : in.r0;
   if (r > rmax) r = rmax;
   for (;;) {
+    __syncthreads();
+    if (tid == 0) {
+      s.ivals[5] += 1;
+      s.ivals[6] += r;
+    }
     // Rademacher signs, one 32-bit word per row of Omega
     for (int i = tid; i < n; i += HM_THREADS) Om[i] = (uint32_t)mix64(in.seed ^ ((uint64_t)i * 0xD1B54A32D192ED03ull));
     __syncthreads();
@@ -818,6 +824,7 @@ static __device__ int trunc_rand32(const float* M, int m, int n, double scale, f
                                    int cap, double* U, int ldu, double* V, int ldv, int* status, Smem& s,
                                    double* flops, int* ok, uint64_t seed, int r0) {
   int tid = threadIdx.x;
+  if (tid == 0) s.ivals[5] = s.ivals[6] = 0;  // attempts, columns sketched over all attempts
   int rmax = HM_RMAX;
   if (rmax > m) rmax = m;
   if (rmax > n) rmax = n;
@@ -845,6 +852,10 @@ static __device__ int trunc_rand32(const float* M, int m, int n, double scale, f
   if (r > rmax) r = rmax;
   for (;;) {
     __syncthreads();
+    if (tid == 0) {
+      s.ivals[5] += 1;
+      s.ivals[6] += r;
+    }
     for (int idx = tid; idx < m * r; idx += HM_THREADS) {
       int i = idx % m, j = idx / m;
       float a = 0.f;

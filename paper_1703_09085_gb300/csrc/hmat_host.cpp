@@ -254,8 +254,13 @@ int bt_rec(hmat_btree& B, int t, int s, int level, int parent, double eta) {
 // ===========================================================================
 struct SchedCache;
 
+namespace hm_internal {
+const void* mlp_weights(const hmat_mlp* M);
+}
+
 struct hmat {
   std::shared_ptr<SchedCache> cache;  // schedule kept by hmat_lu(reuse_schedule)
+  std::vector<float> train;           // training pairs recorded by the last hmat_lu
   hmat_ctx* ctx = nullptr;
   const hmat_btree* bt = nullptr;
   int64_t n = 0;
@@ -308,6 +313,7 @@ struct Sched {
   }
   int64_t ws_top = 0;
   std::vector<int32_t> depbuf;
+  std::vector<float> feat;      // 4 static features per task (truncations only)
   std::vector<int32_t> level;   // longest chain of predecessors (ASAP level)
   std::vector<double> cpath;    // estimated flops of the longest chain ending here
   double est_total = 0.0;
@@ -408,6 +414,7 @@ struct Sched {
     level.push_back(lv);
     double c = est_cost(t);
     cpath.push_back(cp + c);
+    feat.insert(feat.end(), {0.f, 0.f, 0.f, 0.f});
     est_total += c;
     for (int r : reads) {
       Obj& o = objs[(size_t)r];
@@ -447,12 +454,15 @@ struct Sched {
     dep_idx.swap(d2);
     std::vector<int32_t> l2(n);
     std::vector<double> c2(n);
+    std::vector<float> f2(4 * n);
     for (size_t i = 0; i < n; ++i) {
       l2[i] = level[(size_t)ord[i]];
       c2[i] = cpath[(size_t)ord[i]];
+      for (int k = 0; k < 4; ++k) f2[4 * i + k] = feat[4 * (size_t)ord[i] + k];
     }
     level.swap(l2);
     cpath.swap(c2);
+    feat.swap(f2);
   }
   int32_t levels() const {
     int32_t m = 0;
@@ -588,6 +598,22 @@ struct Sym {
   int64_t hl(const hmat* M, int b) const { return M->loc[(size_t)b] + hoffs[mat_index(M)]; }
   int64_t hv(const hmat* M, int b) const { return M->vloc[(size_t)b] + hoffs[mat_index(M)]; }
   int sl(const hmat* M, int b) const { return M->slot[(size_t)b] + slotbases[mat_index(M)]; }
+  // Static features of the truncation just emitted for block (t, r): level of
+  // t / 10, log diam t, log diam r, log(dist + 1e-6) (the rank predictor's
+  // first four inputs).
+  void set_features(int t, int r) {
+    const CNodeH& a = rc(t);
+    const CNodeH& b = cc(r);
+    int d = RT.d;
+    // scale-free block descriptors: cluster sizes, diameter over distance
+    // (bounded where the clusters touch), spatial dimension
+    float* f = &S.feat[S.feat.size() - 4];
+    double diam = 0.5 * (box_diam(a, d) + box_diam(b, d)) + 1e-300;
+    f[0] = (float)(std::log2((double)std::max<int64_t>(a.size, 1)) / 10.0);
+    f[1] = (float)(std::log2((double)std::max<int64_t>(b.size, 1)) / 10.0);
+    f[2] = (float)(std::log(diam / (box_dist(a, b, d) + 1e-3 * diam)) / 4.0);
+    f[3] = (float)d / 3.f;
+  }
   const CNodeH& rc(int t) const { return RT.nodes[(size_t)t]; }
   const CNodeH& cc(int r) const { return CT.nodes[(size_t)r]; }
   int capof(int64_t m, int64_t n) const { return (int)std::min<int64_t>(std::min(m, n), maxrank); }
@@ -866,7 +892,7 @@ struct Sym {
   }
 
   // low-rank target <- trunc(target + alpha P) by one T_RKADD, in place.
-  void rkadd_into(double alpha, const SProd& P, SLow& Z, int64_t m, int64_t n) {
+  void rkadd_into(double alpha, const SProd& P, SLow& Z, int64_t m, int64_t n, int ft, int fr) {
     int rin = Z.zero ? -1 : (Z.wcode < 0 ? -(Z.wcode + 1) : -2);
     if (rin == -2) throw HmError(HMAT_ERR_INTERNAL, "rkadd: fixed-width target");
     int64_t cu = Z.u, cv = Z.v;
@@ -901,6 +927,7 @@ struct Sym {
     std::vector<int> reads = P.objs;
     if (rin >= 0 && inobj >= 0 && inobj != Z.obj) reads.push_back(inobj);
     S.emit(t, reads, {Z.obj, S.chunk_obj(ws)});
+    set_features(ft, fr);
     S.release(ws);
     Z.wcode = width_from_slot(Z.slot);
     Z.zero = false;
@@ -937,7 +964,7 @@ struct Sym {
       S.emit(t, reads, {a.dobj});
       a.dzero = false;
     } else {
-      rkadd_into(alpha, P, a.R, m, n);
+      rkadd_into(alpha, P, a.R, m, n, a.t, a.r);
     }
   }
 
@@ -1011,7 +1038,7 @@ struct Sym {
       P.wcode = R.wcode;
       P.wcap = R.wmax;
       P.objs.push_back(R.obj);
-      rkadd_into(1.0, P, *z.tmp, m, n);
+      rkadd_into(1.0, P, *z.tmp, m, n, t, r);
       return;
     }
     hmat* M = z.M;
@@ -1041,7 +1068,7 @@ struct Sym {
       P.wcode = R.wcode;
       P.wcap = R.wmax;
       P.objs.push_back(R.obj);
-      rkadd_into(1.0, P, L, m, n);
+      rkadd_into(1.0, P, L, m, n, t, r);
       M->zero[(size_t)z.b] = 0;
     } else {
       const BNodeH& nd = M->bt->nodes[(size_t)z.b];
@@ -1116,10 +1143,10 @@ struct Sym {
           P.wcode = P.wcap = (int)n;
         }
         if (z.tmp) {
-          rkadd_into(1.0, P, *z.tmp, m, n);
+          rkadd_into(1.0, P, *z.tmp, m, n, a.t, a.r);
         } else {
           SLow L = leaf_low(z.M, z.b);
-          rkadd_into(1.0, P, L, m, n);
+          rkadd_into(1.0, P, L, m, n, a.t, a.r);
           z.M->zero[(size_t)z.b] = 0;
         }
       }
@@ -1203,6 +1230,7 @@ struct Sym {
         for (int i = 0; i < 2; ++i)
           if (tmp[i][j].obj >= 0) reads.push_back(tmp[i][j].obj);
         S.emit(t, reads, {C.obj, S.chunk_obj(ws)});
+        set_features(a.t, rr.son[j]);
         S.release(ws);
         C.wcode = width_from_slot(C.slot);
         C.zero = false;
@@ -1237,6 +1265,7 @@ struct Sym {
       int ws = S.alloc(rk_ws(m, n, l) + (int64_t)m * l + (mixed ? n * l + rand_ws(m, n, l) : 0));
       t.ws = S.chunk_loc(ws);
       S.emit(t, {col[0].obj, col[1].obj}, {out.obj, S.chunk_obj(ws)});
+      set_features(a.t, a.r);
       S.release(ws);
       if (z.tmp) {
         z.tmp->wcode = width_from_slot(z.tmp->slot);
@@ -1394,7 +1423,7 @@ struct RunResult {
   unsigned long long truncations = 0;
   double flops = 0.0;
   unsigned long long type_ns[16] = {0}, type_cnt[16] = {0}, wait_ns = 0;
-  unsigned long long rand_ok = 0, rand_fail = 0;
+  unsigned long long rand_ok = 0, rand_fail = 0, sketch_attempts = 0, sketch_cols = 0;
   unsigned long long bad[6] = {0, 0, 0, 0, 0, 0};
   std::vector<uint32_t> task_ns;  // filled when profiling
 };
@@ -1438,8 +1467,16 @@ void critical_path(const Sched& S, const std::vector<uint32_t>& ns, hmat_stats& 
 
 // A schedule uploaded to the device, with its scratch arena.
 struct DevSched {
-  DevBuf tasks, ptr, idx, leaves, done, ws, misc, tns;
+  DevBuf tasks, ptr, idx, leaves, done, ws, misc, tns, feat, rec;
   size_t ntasks = 0;
+};
+
+// What a launch needs beyond the schedule: the rank predictor and whether the
+// exact truncations record training pairs.
+struct LaunchOpts {
+  const void* mlp = nullptr;
+  bool record = false;
+  std::vector<float>* rec_out = nullptr;
 };
 
 void upload_sched(hmat_ctx* ctx, const Sched& S, DevSched& D) {
@@ -1448,6 +1485,7 @@ void upload_sched(hmat_ctx* ctx, const Sched& S, DevSched& D) {
   upload(D.ptr, S.dep_ptr, st);
   upload(D.idx, S.dep_idx, st);
   upload(D.leaves, S.leaves, st);
+  upload(D.feat, S.feat, st);
   D.done.alloc(S.tasks.size() * sizeof(int));
   D.ws.alloc((size_t)std::max<int64_t>(S.ws_top, 1) * sizeof(double));
   D.misc.alloc(64 * 8);
@@ -1455,7 +1493,7 @@ void upload_sched(hmat_ctx* ctx, const Sched& S, DevSched& D) {
 }
 
 RunResult launch_sched(hmat_ctx* ctx, const Sched& S, DevSched& D, double* hbase, int* ranks, double eps,
-                       int64_t spin_limit, double* ext0, double* ext1, bool mixed) {
+                       int64_t spin_limit, double* ext0, double* ext1, bool mixed, const LaunchOpts& lo = LaunchOpts()) {
   RunResult rr;
   if (D.ntasks == 0) return rr;
   cudaStream_t st = ctx->stream;
@@ -1487,6 +1525,17 @@ RunResult launch_sched(hmat_ctx* ctx, const Sched& S, DevSched& D, double* hbase
     HM_CUDA(cudaMemsetAsync(D.tns.p, 0, D.ntasks * sizeof(uint32_t), st));
     e.task_ns = D.tns.as<uint32_t>();
   }
+  e.feat = D.feat.as<float>();
+  e.mlp = lo.mlp;
+  e.oversample = 3;
+  e.rec = nullptr;
+  e.rec_count = (unsigned long long*)dmp + 60;
+  e.rec_cap = 0;
+  if (lo.record) {
+    e.rec_cap = (long long)std::max<size_t>(D.ntasks / 2, 1024);
+    D.rec.alloc((size_t)e.rec_cap * 7 * sizeof(float));
+    e.rec = D.rec.as<float>();
+  }
   e.eps = eps;
   e.mixed = mixed ? 1 : 0;
   e.rand_min_l = 8;
@@ -1517,6 +1566,13 @@ RunResult launch_sched(hmat_ctx* ctx, const Sched& S, DevSched& D, double* hbase
   rr.rand_ok = misc[45];
   rr.rand_fail = misc[46];
   for (int i = 0; i < 6; ++i) rr.bad[i] = misc[47 + i];
+  rr.sketch_attempts = misc[53];
+  rr.sketch_cols = misc[54];
+  if (lo.record && lo.rec_out) {
+    size_t cnt = (size_t)std::min<unsigned long long>(misc[60], (unsigned long long)e.rec_cap);
+    lo.rec_out->resize(cnt * 7);
+    if (cnt) HM_CUDA(cudaMemcpy(lo.rec_out->data(), D.rec.p, cnt * 7 * sizeof(float), cudaMemcpyDeviceToHost));
+  }
   if (e.task_ns) {
     rr.task_ns.resize(D.ntasks);
     HM_CUDA(cudaMemcpy(rr.task_ns.data(), D.tns.p, D.ntasks * sizeof(uint32_t), cudaMemcpyDeviceToHost));
@@ -2017,7 +2073,11 @@ void lu_batch(hmat_ctx* ctx, hmat* const* Hs, int count, const hmat_opts* opts) 
   for (int i = 0; i < count; ++i)
     HM_CUDA(cudaMemcpyAsync(allranks.as<int>() + slotbase[(size_t)i], Hs[i]->ranks.p, (size_t)Hs[i]->nslots * sizeof(int),
                             cudaMemcpyDeviceToDevice, ctx->stream));
-  RunResult rr = launch_sched(ctx, S, C->D, base, allranks.as<int>(), eps, spin, nullptr, nullptr, mixed);
+  LaunchOpts lo;
+  lo.mlp = opts ? hm_internal::mlp_weights(opts->predictor) : nullptr;
+  lo.record = opts && opts->record_training;
+  lo.rec_out = &Hs[0]->train;
+  RunResult rr = launch_sched(ctx, S, C->D, base, allranks.as<int>(), eps, spin, nullptr, nullptr, mixed, lo);
   for (int i = 0; i < count; ++i)
     HM_CUDA(cudaMemcpyAsync(Hs[i]->ranks.p, allranks.as<int>() + slotbase[(size_t)i], (size_t)Hs[i]->nslots * sizeof(int),
                             cudaMemcpyDeviceToDevice, ctx->stream));
@@ -2035,6 +2095,9 @@ void lu_batch(hmat_ctx* ctx, hmat* const* Hs, int count, const hmat_opts* opts) 
     st.flops = rr.flops;
     st.rand_truncations = (int64_t)rr.rand_ok;
     st.rand_fallbacks = (int64_t)rr.rand_fail;
+    st.sketch_attempts = (int64_t)rr.sketch_attempts;
+    st.sketch_columns = (int64_t)rr.sketch_cols;
+    st.training_pairs = (int64_t)(Hs[0]->train.size() / 7);
     if (!rr.task_ns.empty()) critical_path(S, rr.task_ns, st);
     for (int k = 0; k < 16; ++k) {
       st.type_seconds[k] = rr.type_ns[k] * 1e-9;
@@ -2160,6 +2223,18 @@ hmat_status hmat_stats_get(const hmat* H, hmat_stats* out) {
     s.max_rank = mx;
     s.mean_rank = H->nslots ? sum / H->nslots : 0.0;
     *out = s;
+  });
+}
+
+hmat_status hmat_lu_training_data(const hmat* H, int64_t max, float* X, float* y, int64_t* count) {
+  return guarded([&] {
+    require(H && count && (max <= 0 || (X && y)), "null argument");
+    int64_t n = (int64_t)(H->train.size() / 7);
+    *count = n;
+    for (int64_t i = 0; i < std::min(n, max); ++i) {
+      for (int j = 0; j < 6; ++j) X[i * 6 + j] = H->train[(size_t)(i * 7 + j)];
+      y[i] = H->train[(size_t)(i * 7 + 6)];
+    }
   });
 }
 

@@ -18,6 +18,7 @@
 
 #include "hmat_device.cuh"
 #include "hmat_kernels.h"
+#include "hmat_mlp.cuh"
 
 namespace hm {
 
@@ -85,6 +86,55 @@ __device__ void record_bad(const ExecEnv& e, int path, int m, int n, int l, int 
     e.counters[6] = (unsigned long long)l;
     e.counters[7] = (unsigned long long)k;
     e.counters[8] = __double_as_longlong(scale);
+  }
+}
+
+// First sketch width of a randomised truncation: kz + 6 (at least 8), kz the
+// larger input rank, without a predictor; else max(predicted rank + 3, kz + 2).
+// l is the total input rank (a feature of the predictor).
+__device__ int sketch_width(const ExecEnv& e, long long ti, int kz, int l, Smem& s) {
+  if (!e.mlp) {
+    int r0 = kz + 6;
+    return r0 < 8 ? 8 : r0;
+  }
+  if ((threadIdx.x >> 5) == 0) {
+    float x[HM_MLP_IN];
+    for (int i = 0; i < 4; ++i) x[i] = e.feat[4 * ti + i];
+    x[4] = (float)l / 16.f;
+    x[5] = (float)log10(e.eps) / 4.f;
+    float y = mlp_forward_warp((const __nv_bfloat16*)e.mlp, x);
+    if ((threadIdx.x & 31) == 0) s.bcast[1] = (double)y;
+  }
+  __syncthreads();
+  double y = s.bcast[1];
+  __syncthreads();
+  double kh = expm1(y < 8.0 ? y : 8.0);
+  if (kh < 0.0) kh = 0.0;
+  // never below kz + 2: a truncated sum rarely loses rank against its larger
+  // term, and a sketch that misses costs a second, doubled one
+  int r0 = (int)ceil(kh) + e.oversample;
+  if (r0 < kz + 2) r0 = kz + 2;
+  return r0 < 2 ? 2 : r0;
+}
+
+// Training pair of an exact truncation: features and log(1 + rank); l is the
+// total input rank.
+__device__ void record_rank(const ExecEnv& e, long long ti, int l, int k) {
+  if (!e.rec || threadIdx.x != 0) return;
+  unsigned long long i = atomicAdd(e.rec_count, 1ull);
+  if ((long long)i >= e.rec_cap) return;
+  float* r = e.rec + 7 * i;
+  for (int j = 0; j < 4; ++j) r[j] = e.feat[4 * ti + j];
+  r[4] = (float)l / 16.f;
+  r[5] = (float)log10(e.eps) / 4.f;
+  r[6] = (float)log1p((double)k);
+}
+
+// attempts and columns sketched (over all attempts) by a randomised truncation
+__device__ void count_sketch(const ExecEnv& e, Smem& s) {
+  if (threadIdx.x == 0) {
+    atomicAdd(e.counters + 9, (unsigned long long)s.ivals[5]);
+    atomicAdd(e.counters + 10, (unsigned long long)s.ivals[6]);
   }
 }
 
@@ -158,7 +208,7 @@ __device__ void task_densify(const ExecEnv& e, const HTask& t, Smem& s) {
   }
 }
 
-__device__ void task_rkadd(const ExecEnv& e, const HTask& t, Smem& s) {
+__device__ void task_rkadd(const ExecEnv& e, const HTask& t, Smem& s, long long ti) {
   int m = t.m, n = t.n;
   bool aid = t.flags & F_A_IDENT, bid = t.flags & F_B_IDENT, btr = t.flags & F_B_TRANS;
   int w = aid ? m : (bid ? n : width_of(e, t.wa));
@@ -247,8 +297,7 @@ __device__ void task_rkadd(const ExecEnv& e, const HTask& t, Smem& s) {
     }
     if (__syncthreads_or(nonfinite)) record_bad(e, 9, m, n, l, kin, mx);
     f += 2.0 * m * n * (double)(kin + ((aid || bid) ? 0 : w));
-    int r0 = kin + 6;
-    if (r0 < 8) r0 = 8;
+    int r0 = sketch_width(e, ti, kin, l, s);
     uint64_t seed = e.seed ^ ((uint64_t)blockIdx.x << 40) ^ (uint64_t)(t.rout + 1) * 0x9E3779B97F4A7C15ull;
     int ok = 0;
     int k = trunc_rand32(Mf, m, n, mx, Mf + mn, Om, e.eps, t.cap, Uout, t.lde, Vout, t.ldf, e.status, s, &f, &ok,
@@ -264,9 +313,11 @@ __device__ void task_rkadd(const ExecEnv& e, const HTask& t, Smem& s) {
         atomicAdd(e.counters + 1, 1ull);
         atomicAdd(e.flops, f);
       }
+      count_sketch(e, s);
       return;
     }
     if (threadIdx.x == 0) atomicAdd(e.counters + 2, 1ull);
+    count_sketch(e, s);
   } else if (e.mixed && e.eps > 0.0 && l >= e.rand_min_l) {
     // Randomised truncation; M explicit when that is the smaller form.
     double* R = Jg + 2 * (int64_t)l * l;
@@ -301,9 +352,7 @@ __device__ void task_rkadd(const ExecEnv& e, const HTask& t, Smem& s) {
     ri.SB = SB;
     ri.ws = R;
     ri.seed = e.seed ^ ((uint64_t)blockIdx.x << 40) ^ (uint64_t)(t.rout + 1) * 0x9E3779B97F4A7C15ull;
-    int r0 = kin + 6;
-    if (r0 < 8) r0 = 8;
-    ri.r0 = r0;
+    ri.r0 = sketch_width(e, ti, kin, l, s);
     int ok = 0;
     int k = trunc_rand(ri, e.eps, t.cap, Uout, t.lde, Vout, t.ldf, e.status, s, &f, &ok);
     if (ok) {
@@ -313,9 +362,11 @@ __device__ void task_rkadd(const ExecEnv& e, const HTask& t, Smem& s) {
         atomicAdd(e.counters + 1, 1ull);
         atomicAdd(e.flops, f);
       }
+      count_sketch(e, s);
       return;
     }
     if (threadIdx.x == 0) atomicAdd(e.counters + 2, 1ull);
+    count_sketch(e, s);
   }
   TruncIn in;
   in.nb = 1;
@@ -332,9 +383,10 @@ __device__ void task_rkadd(const ExecEnv& e, const HTask& t, Smem& s) {
     atomicAdd(e.counters, 1ull);
     atomicAdd(e.flops, f);
   }
+  record_rank(e, ti, l, k);
 }
 
-__device__ void task_rowmerge(const ExecEnv& e, const HTask& t, Smem& s) {
+__device__ void task_rowmerge(const ExecEnv& e, const HTask& t, Smem& s, long long ti) {
   int m = t.m;
   int n0 = t.p, n1 = t.q;
   int k0 = width_of(e, t.wa), k1 = width_of(e, t.wb);
@@ -389,8 +441,7 @@ __device__ void task_rowmerge(const ExecEnv& e, const HTask& t, Smem& s) {
     for (int idx = threadIdx.x; idx < mn; idx += HM_THREADS) Mf[idx] = (float)(entry(idx) * inv);
     __syncthreads();
     f += 2.0 * m * (double)(n0 * k0 + n1 * k1);
-    int r0 = (k0 > k1 ? k0 : k1) + 6;
-    if (r0 < 8) r0 = 8;
+    int r0 = sketch_width(e, ti, k0 > k1 ? k0 : k1, l, s);
     uint64_t seed = e.seed ^ ((uint64_t)blockIdx.x << 40) ^ (uint64_t)(t.rout + 7) * 0x9E3779B97F4A7C15ull;
     int ok = 0;
     int k = trunc_rand32(Mf, m, n, mx, Mf + mn, Om, e.eps, t.cap, Uout, t.lde, Vout, t.ldf, e.status, s, &f, &ok,
@@ -406,9 +457,11 @@ __device__ void task_rowmerge(const ExecEnv& e, const HTask& t, Smem& s) {
         atomicAdd(e.counters + 1, 1ull);
         atomicAdd(e.flops, f);
       }
+      count_sketch(e, s);
       return;
     }
     if (threadIdx.x == 0) atomicAdd(e.counters + 2, 1ull);
+    count_sketch(e, s);
   } else if (e.mixed && e.eps > 0.0 && l >= e.rand_min_l) {
     // [A_0 A_1] blockdiag(B_0, B_1)^T with SA = [SA0 SA1] (contiguous)
     double* SBd = Jg + 2 * (int64_t)l * l;
@@ -448,9 +501,7 @@ __device__ void task_rowmerge(const ExecEnv& e, const HTask& t, Smem& s) {
     ri.SB = SBd;
     ri.ws = R;
     ri.seed = e.seed ^ ((uint64_t)blockIdx.x << 40) ^ (uint64_t)(t.rout + 7) * 0x9E3779B97F4A7C15ull;
-    int r0 = (k0 > k1 ? k0 : k1) + 6;
-    if (r0 < 8) r0 = 8;
-    ri.r0 = r0;
+    ri.r0 = sketch_width(e, ti, k0 > k1 ? k0 : k1, l, s);
     int ok = 0;
     int k = trunc_rand(ri, e.eps, t.cap, Uout, t.lde, Vout, t.ldf, e.status, s, &f, &ok);
     if (ok) {
@@ -460,9 +511,11 @@ __device__ void task_rowmerge(const ExecEnv& e, const HTask& t, Smem& s) {
         atomicAdd(e.counters + 1, 1ull);
         atomicAdd(e.flops, f);
       }
+      count_sketch(e, s);
       return;
     }
     if (threadIdx.x == 0) atomicAdd(e.counters + 2, 1ull);
+    count_sketch(e, s);
   }
   TruncIn in;
   in.nb = 2;
@@ -483,6 +536,7 @@ __device__ void task_rowmerge(const ExecEnv& e, const HTask& t, Smem& s) {
     atomicAdd(e.counters, 1ull);
     atomicAdd(e.flops, f);
   }
+  record_rank(e, ti, l, k);
 }
 
 // FP64 operations of the non-truncation tasks (counted by thread 0).
@@ -518,7 +572,7 @@ __device__ double task_flops(const ExecEnv& e, const HTask& t) {
   }
 }
 
-__device__ void run_task(const ExecEnv& e, const HTask& t, Smem& s) {
+__device__ void run_task(const ExecEnv& e, const HTask& t, Smem& s, long long ti) {
   switch (t.type) {
     case T_NOP:
       break;
@@ -564,10 +618,10 @@ __device__ void run_task(const ExecEnv& e, const HTask& t, Smem& s) {
       if (threadIdx.x == 0) e.ranks[t.rout] = width_of(e, t.wa);
       break;
     case T_RKADD:
-      task_rkadd(e, t, s);
+      task_rkadd(e, t, s, ti);
       break;
     case T_ROWMERGE:
-      task_rowmerge(e, t, s);
+      task_rowmerge(e, t, s, ti);
       break;
     default:
       if (threadIdx.x == 0) set_status(e.status, DS_INTERNAL);
@@ -616,7 +670,7 @@ __global__ void __launch_bounds__(HM_THREADS) exec_tasks(ExecEnv e) {
         double f = task_flops(e, task);
         if (f > 0.0) atomicAdd(e.flops, f);
       }
-      run_task(e, task, s);
+      run_task(e, task, s, t);
       __syncthreads();
       if (threadIdx.x == 0 && task.type >= 0 && task.type < 16) {
         uint64_t dt = global_ns() - cur_t0;

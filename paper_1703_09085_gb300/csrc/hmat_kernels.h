@@ -28,6 +28,12 @@ struct ExecEnv {
   unsigned long long* type_cnt;  // per task type: tasks run
   unsigned long long* wait_ns;   // summed time CTAs spent waiting on predecessors
   uint32_t* task_ns;             // optional: execution time of every task (profiling)
+  const float* feat;             // 4 static features per task (truncations)
+  const void* mlp;               // rank predictor weights (BF16), or null
+  int oversample;                // sketch columns beyond the predicted rank
+  float* rec;                    // optional: training pairs (7 floats each) of exact truncations
+  unsigned long long* rec_count;
+  long long rec_cap;
   double eps;
   int mixed;                  // randomised truncation path on
   int rand_min_l;             // smallest stacked width that takes it

@@ -1,0 +1,122 @@
+"""Rank predictor on the GPU: forward and backward kernels against the FP64
+CPU reference, training on pairs recorded from exact truncations, and the
+sketch sizes it gives the randomised truncation."""
+import numpy as np
+import pytest
+
+import hmat_synth as hs
+import oracle
+from gpu_util import GpuProblem, hm
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return hm().Context(0)
+
+
+def _params(seed, scale=0.25):
+    return (hs.normal(seed, omlp.NPARAM) * scale).astype(np.float32)
+
+
+def _features(seed, count):
+    return hs.normal(seed, count * 6).reshape(count, 6).astype(np.float32)
+
+
+@pytest.mark.parametrize("count", [1, 63, 64, 1000])
+def test_forward_matches_reference(ctx, count):
+    g = hm()
+    P = g.RankPredictor(ctx, seed=1)
+    p = _params(10 + count)
+    P.set_params(p)
+    assert np.array_equal(P.params(), p)
+    X = _features(20 + count, count)
+    y_gpu = P.forward(X)
+    y_ref = omlp.forward(p, X.astype(np.float64))
+    # FP32 sums of at most 64 products of BF16 weights: relative error a few
+    # units of 2^-24 times the sum of magnitudes
+    scale = np.abs(omlp.forward(np.abs(p), np.abs(X).astype(np.float64), round_bf16=True)) + 1.0
+    assert np.all(np.abs(y_gpu - y_ref) <= 1e-5 * scale)
+
+
+@pytest.mark.parametrize("count", [5, 64, 200])
+def test_gradient_matches_reference(ctx, count):
+    g = hm()
+    P = g.RankPredictor(ctx, seed=1)
+    p = _params(30 + count)
+    P.set_params(p)
+    X = _features(40 + count, count)
+    y = hs.normal(50 + count, count).astype(np.float32)
+    loss_gpu, g_gpu = P.grad(X, y)
+    loss_ref, g_ref = omlp.loss_grad(p, X.astype(np.float64), y.astype(np.float64))
+    assert abs(loss_gpu - loss_ref) <= 1e-4 * max(1.0, loss_ref)
+    assert np.abs(g_gpu - g_ref).max() <= 1e-4 * np.abs(g_ref).max()
+
+
+def _recorded_pairs(ctx):
+    """Training pairs of exact (FP64) truncations from small problems."""
+    Xs, ys, truncs = [], [], 0
+    for p in (hs.small_laplace(32, 2, 16, 1e-4), hs.small_laplace(32, 2, 16, 1e-6),
+              hs.small_laplace(12, 3, 32, 1e-4), hs.small_laplace(16, 3, 64, 1e-4),
+              hs.small_laplace(16, 3, 64, 1e-6),
+              hs.Problem("diffusion2d_40", 40, 2, 16, 2.0, 1e-5, kind="diffusion", lc=0.1, seed=5)):
+        gp = GpuProblem(ctx, p)
+        gp.H.lu(p.eps, record_training=True)
+        st = gp.H.stats()
+        X, y = gp.H.training_data()
+        assert st["training_pairs"] == len(y) == st["truncations"]
+        truncs += st["truncations"]
+        Xs.append(X)
+        ys.append(y)
+    return np.concatenate(Xs), np.concatenate(ys), truncs
+
+
+def test_recorded_pairs_are_ranks(ctx):
+    X, y, truncs = _recorded_pairs(ctx)
+    assert len(y) == truncs > 100
+    assert np.all(np.isfinite(X)) and np.all(np.isfinite(y))
+    k = np.expm1(y.astype(np.float64))
+    assert np.all(np.abs(k - np.round(k)) <= 1e-4 * (1 + k)) and k.min() >= 0
+    # the accumulated rank is an upper bound of the truncated rank
+    assert np.all(np.round(k) <= np.round(X[:, 4] * 16) + 1e-9)
+    assert set(np.round(X[:, 5] * 4, 3)) <= {-4.0, -5.0, -6.0}
+
+
+def test_training_lowers_loss_and_sizes_sketches(ctx):
+    g = hm()
+    X, y, _ = _recorded_pairs(ctx)
+    P = g.RankPredictor(ctx, seed=7)
+    loss0, _ = P.grad(X, y)
+    loss = P.train(X, y, epochs=60, batch=256, lr=3e-3, seed=3)
+    var = float(np.var(y.astype(np.float64)))
+    # better than the best constant predictor by a clear margin
+    assert loss < 0.1 * loss0 and loss < 0.5 * var
+    # the trained network against the FP64 reference with the same weights
+    y_ref = omlp.forward(P.params(), X[:256].astype(np.float64))
+    assert np.abs(P.forward(X[:256]) - y_ref).max() <= 1e-3 * (1 + np.abs(y_ref).max())
+
+    # held-out problem, mixed precision with and without the predictor
+    p = hs.small_laplace(20, 3, 64, 1e-4)
+    v0 = hs.start_vector(p.n, 0)
+    ct, bt, csr, H = oracle.setup(p)
+    H.lu(p.eps, True)
+    err_orc, _ = H.precond_error(csr, v0)
+    res = {}
+    for name, pred in (("heuristic", None), ("predictor", P)):
+        gp = GpuProblem(ctx, p)
+        gp.H.lu(p.eps, precision=g.HMAT_MIXED, predictor=pred)
+        st = gp.H.stats()
+        assert st["status"] == 0
+        err = gp.precond_error(v0[gp.perm])
+        assert err <= 2.0 * err_orc and err_orc <= 2.0 * err
+        res[name] = st
+    # the gain: fewer columns sketched (FP64 projection work) over all
+    # attempts, with no more fallbacks to the exact truncation
+    h, q = res["heuristic"], res["predictor"]
+    print({k: (h[k], q[k]) for k in ("sketch_columns", "sketch_attempts", "rand_truncations", "rand_fallbacks",
+                                     "factor_seconds")})
+    assert q["rand_truncations"] > 1000 and h["rand_truncations"] > 1000
+    assert q["sketch_columns"] < 0.98 * h["sketch_columns"]
+    assert q["rand_fallbacks"] <= h["rand_fallbacks"] + 2
