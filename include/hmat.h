@@ -196,6 +196,20 @@ hmat_status hmat_lu(hmat_ctx* ctx, hmat* H, const hmat_opts* opts);
  * as by hmat_lu; the statistics of every instance report the batch's totals. */
 hmat_status hmat_lu_batched(hmat_ctx* ctx, hmat** G, int count, const hmat_opts* opts);
 
+/* H-matrix multiplication Z <- blocktrunc(Z + alpha X Y) (Section 4) in the
+ * accumulated form of Section 5: the product of the root blocks is entered
+ * into an accumulator by addproduct (the four leaf cases produce low-rank
+ * factors or dense blocks), split down the block tree of Z and flushed into
+ * Z's leaves, so that every leaf of Z is truncated once per pending product
+ * sum rather than once per product.  X, Y and Z must be distinct matrices of
+ * this context built on block trees of ONE cluster tree (same index set and
+ * ordering); X and Y are read only.  opts: eps (relative Frobenius rule per
+ * truncation), precision, max_rank (capped by Z's leaf capacity), predictor,
+ * spin_limit, record_training.  Runs as one persistent kernel launch and
+ * synchronises the stream; Z's statistics describe the call.  Errors:
+ * HMAT_ERR_ARG for aliasing or mismatched trees, device statuses as hmat_lu. */
+hmat_status hmat_addmul(hmat_ctx* ctx, double alpha, const hmat* X, const hmat* Y, hmat* Z, const hmat_opts* opts);
+
 /* Host-only analysis of the schedule hmat_lu would run for this matrix (no
  * device is touched): fills tasks, levels (longest dependency chain),
  * critical_flops / est_flops (static estimates with rank 8 for unknown

@@ -29,6 +29,9 @@ STATUS = {0: "HMAT_OK", 1: "HMAT_ERR_ARG", 2: "HMAT_ERR_NOMEM", 3: "HMAT_ERR_SIN
           9: "HMAT_ERR_INTERNAL"}
 HMAT_FP64, HMAT_MIXED = 0, 1
 
+for _code, _name in STATUS.items():  # HMAT_OK, HMAT_ERR_ARG, ... as module constants
+    globals()[_name] = _code
+
 # Every symbol include/hmat.h declares.
 EXPORTS = ["hmat_last_error", "hmat_ctx_create", "hmat_ctx_destroy", "hmat_clustertree_build",
            "hmat_clustertree_perm", "hmat_clustertree_size", "hmat_clustertree_nodes", "hmat_ctree_destroy",
@@ -37,7 +40,7 @@ EXPORTS = ["hmat_last_error", "hmat_ctx_create", "hmat_ctx_destroy", "hmat_clust
            "trunc_lowrank", "trunc_lowrank_batched", "hmat_stats_get", "hmat_ranks", "hmat_copy_values",
            "hmat_analyze_lu", "trunc_lowrank_noalloc", "hmat_lu_batched", "hmat_lu_training_data",
            "hmat_mlp_create", "hmat_mlp_destroy", "hmat_mlp_get_params", "hmat_mlp_set_params", "hmat_mlp_forward",
-           "hmat_mlp_grad", "hmat_mlp_train"]
+           "hmat_mlp_grad", "hmat_mlp_train", "hmat_addmul"]
 MLP_NPARAM = 4673
 
 
@@ -246,6 +249,13 @@ class HMatrix:
         r = np.zeros(lib().hmat_blocktree_size(self.bt.h), np.int64)
         _check(lib().hmat_ranks(self.h, _hp(r, I64P)))
         return r
+
+
+def addmul(ctx: Context, alpha: float, X: "HMatrix", Y: "HMatrix", Z: "HMatrix", eps: float, max_rank: int = 0,
+           precision: int = HMAT_FP64, spin_limit: int = 0, predictor=None, record_training: bool = False):
+    """hmat_addmul: Z <- blocktrunc(Z + alpha X Y), accumulated form, one launch."""
+    o = Opts(eps, max_rank, precision, spin_limit, 0, predictor.h if predictor else None, int(record_training))
+    _check(lib().hmat_addmul(ctx.h, ctypes.c_double(alpha), X.h, Y.h, Z.h, ctypes.byref(o)))
 
 
 def lu_batched(ctx: Context, Hs, eps: float, max_rank: int = 0, precision: int = HMAT_FP64, spin_limit: int = 0,

@@ -598,9 +598,8 @@ struct Sym {
   int64_t hl(const hmat* M, int b) const { return M->loc[(size_t)b] + hoffs[mat_index(M)]; }
   int64_t hv(const hmat* M, int b) const { return M->vloc[(size_t)b] + hoffs[mat_index(M)]; }
   int sl(const hmat* M, int b) const { return M->slot[(size_t)b] + slotbases[mat_index(M)]; }
-  // Static features of the truncation just emitted for block (t, r): level of
-  // t / 10, log diam t, log diam r, log(dist + 1e-6) (the rank predictor's
-  // first four inputs).
+  // Static features of the truncation just emitted for block (t, r) (the rank
+  // predictor's first four inputs).
   void set_features(int t, int r) {
     const CNodeH& a = rc(t);
     const CNodeH& b = cc(r);
@@ -2115,6 +2114,88 @@ void lu_batch(hmat_ctx* ctx, hmat* const* Hs, int count, const hmat_opts* opts) 
   }
   if (rr.status) throw HmError(rr.status, "hmat_lu: device status " + std::to_string(rr.status));
 }
+
+// Z <- blocktrunc(Z + alpha X Y) in the accumulated form: one addproduct at
+// the root pair, one flush into Z, one launch.
+void addmul_run(hmat_ctx* ctx, double alpha, const hmat* X, const hmat* Y, hmat* Z, const hmat_opts* opts) {
+  check_ctx(ctx);
+  require(X && Y && Z, "null H-matrix");
+  require(X->ctx == ctx && Y->ctx == ctx && Z->ctx == ctx, "H-matrix of another context");
+  require(Z != X && Z != Y, "addmul: Z must not be X or Y");
+  const hmat_ctree* T = Z->bt->R;
+  require(Z->bt->C == T && X->bt->R == T && X->bt->C == T && Y->bt->R == T && Y->bt->C == T,
+          "addmul: X, Y and Z must be built on one cluster tree");
+  double eps = opts ? opts->eps : 0.0;
+  require(eps >= 0.0, "eps must be >= 0");
+  int64_t spin = opts ? opts->spin_limit : 0;
+  bool mixed = opts && opts->precision == HMAT_MIXED;
+  auto t0 = std::chrono::steady_clock::now();
+  const hmat* M[3] = {X, Y, Z};
+  double* base = X->store.as<double>();
+  for (int i = 1; i < 3; ++i) base = std::min(base, M[i]->store.as<double>());
+  int slotbase[3];
+  int nslots = 0;
+  for (int i = 0; i < 3; ++i) {
+    slotbase[i] = nslots;
+    nslots += M[i]->nslots;
+  }
+  int64_t mr = (opts && opts->max_rank > 0) ? opts->max_rank : DEFAULT_MAX_RANK;
+  mr = std::min<int64_t>(mr, Z->max_rank);
+  Sched S;
+  DevSched D;
+  S.next_slot = nslots;
+  S.set_pool(0);
+  Sym sym(S, *T, *T, mr);
+  sym.mixed = mixed;
+  for (int i = 0; i < 3; ++i) sym.add_matrix(M[i], (int64_t)(M[i]->store.as<double>() - base), slotbase[i]);
+  SAcc root = sym.acc_new(0, 0);
+  sym.addproduct(alpha, X, 0, Y, 0, root);
+  STarget z;
+  z.M = Z;
+  z.b = 0;
+  z.t = 0;
+  z.r = 0;
+  sym.flush(root, z);
+  S.order_by_level();
+  upload_sched(ctx, S, D);
+  double sched_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  DevBuf allranks((size_t)std::max(S.next_slot, 1) * sizeof(int));
+  for (int i = 0; i < 3; ++i)
+    HM_CUDA(cudaMemcpyAsync(allranks.as<int>() + slotbase[i], M[i]->ranks.p, (size_t)M[i]->nslots * sizeof(int),
+                            cudaMemcpyDeviceToDevice, ctx->stream));
+  LaunchOpts lo;
+  lo.mlp = opts ? hm_internal::mlp_weights(opts->predictor) : nullptr;
+  lo.record = opts && opts->record_training;
+  lo.rec_out = &Z->train;
+  RunResult rr = launch_sched(ctx, S, D, base, allranks.as<int>(), eps, spin, nullptr, nullptr, mixed, lo);
+  HM_CUDA(cudaMemcpyAsync(Z->ranks.p, allranks.as<int>() + slotbase[2], (size_t)Z->nslots * sizeof(int),
+                          cudaMemcpyDeviceToDevice, ctx->stream));
+  HM_CUDA(cudaStreamSynchronize(ctx->stream));
+  hmat_stats& st = Z->st;
+  st.tasks = (int64_t)S.tasks.size();
+  st.truncations = (int64_t)rr.truncations;
+  st.flops = rr.flops;
+  st.rand_truncations = (int64_t)rr.rand_ok;
+  st.rand_fallbacks = (int64_t)rr.rand_fail;
+  st.sketch_attempts = (int64_t)rr.sketch_attempts;
+  st.sketch_columns = (int64_t)rr.sketch_cols;
+  st.training_pairs = (int64_t)(Z->train.size() / 7);
+  if (!rr.task_ns.empty()) critical_path(S, rr.task_ns, st);
+  for (int k = 0; k < 16; ++k) {
+    st.type_seconds[k] = rr.type_ns[k] * 1e-9;
+    st.type_count[k] = (int64_t)rr.type_cnt[k];
+  }
+  st.wait_seconds = rr.wait_ns * 1e-9;
+  st.factor_seconds = rr.ms * 1e-3;
+  st.schedule_seconds = sched_s;
+  st.schedule_reused = 0;
+  st.status = rr.status;
+  st.levels = S.levels();
+  st.critical_flops = S.critical_flops();
+  st.est_flops = S.est_total;
+  st.device_bytes = (int64_t)(Z->store.bytes + Z->ranks.bytes) + S.ws_top * 8;
+  if (rr.status) throw HmError(rr.status, "hmat_addmul: device status " + std::to_string(rr.status));
+}
 }  // namespace
 
 extern "C" {
@@ -2125,6 +2206,10 @@ hmat_status hmat_lu(hmat_ctx* ctx, hmat* H, const hmat_opts* opts) {
 
 hmat_status hmat_lu_batched(hmat_ctx* ctx, hmat** G, int count, const hmat_opts* opts) {
   return guarded([&] { lu_batch(ctx, G, count, opts); });
+}
+
+hmat_status hmat_addmul(hmat_ctx* ctx, double alpha, const hmat* X, const hmat* Y, hmat* Z, const hmat_opts* opts) {
+  return guarded([&] { addmul_run(ctx, alpha, X, Y, Z, opts); });
 }
 
 hmat_status hmat_solve(hmat_ctx* ctx, const hmat* LU, int trans, int64_t nrhs, double* B, int64_t ldb) {

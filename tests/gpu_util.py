@@ -26,12 +26,15 @@ def from_dev(t, ncol=None) -> np.ndarray:
 class GpuProblem:
     """Trees, H-matrix and CSR of a synthetic problem on the GPU path."""
 
-    def __init__(self, ctx, problem, csr=None):
+    def __init__(self, ctx, problem, csr=None, trees_of=None):
         g = hm()
         self.p = problem
         self.csr = csr if csr is not None else problem.matrix()
-        self.ct = g.ClusterTree(ctx, problem.coords(), problem.leaf)
-        self.bt = g.BlockTree(ctx, self.ct, self.ct, problem.eta)
+        if trees_of is not None:  # share the cluster and block trees of another problem
+            self.ct, self.bt = trees_of.ct, trees_of.bt
+        else:
+            self.ct = g.ClusterTree(ctx, problem.coords(), problem.leaf)
+            self.bt = g.BlockTree(ctx, self.ct, self.ct, problem.eta)
         self.H = g.HMatrix(ctx, self.bt, self.csr)
         self.perm = self.ct.perm()
 
