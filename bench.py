@@ -114,9 +114,42 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def rank_problems(workload: str, rank: int):
+    """This rank's problems.  A single H-LU does not shard, so every rank
+    factors a replica of it; the batch workload gives each rank its own
+    64 instances (seeds offset by 64 per rank), with no exchange."""
+    if workload == "diffusion2d_batch64":
+        return hs.diffusion2d_batch(64, seed=2 + 64 * rank)
+    w = WORKLOADS[workload]()
+    return w if isinstance(w, list) else [w]
+
+
+def job_throughput(units: float, seconds: float, world: int, device=None):
+    """(units of all ranks / the slowest rank's time, that time)."""
+    if world > 1:
+        import torch
+        u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+        t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(u, op=torch.distributed.ReduceOp.SUM)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        units, seconds = float(u.item()), float(t.item())
+    return units / seconds, seconds
+
+
+def workload_config(args, probs, world: int) -> dict:
+    """The config object of both arms' JSON lines."""
+    par = (f"instances sharded: {world} rank(s) x 64 own instances" if args.workload == "diffusion2d_batch64"
+           else f"replicas{world}")
+    return {"workload": args.workload, "instances": len(probs), "n": sum(p.n for p in probs), "leaf": probs[0].leaf,
+            "eta": probs[0].eta, "eps": probs[0].eps, "precision": args.precision,
+            "max_rank": args.max_rank or 64, "l2": "flushed between steps (256 MiB write)",
+            "parallelism": par}
+
+
 def run_reference(args, rank: int, world: int) -> None:
     if rank != 0:
         return
+    cfg = workload_config(args, rank_problems(args.workload, 0), world)
     p = SAMPLE[args.workload]()
     import oracle
     oracle.build()
@@ -134,10 +167,11 @@ def run_reference(args, rank: int, world: int) -> None:
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": p.name, "n": p.n, "leaf": p.leaf, "eta": p.eta,
-                                            "eps": p.eps, "note": "bounded CPU sample of " + args.workload},
+            "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} timed serial oracle H-LUs of {p.name}"},
+                             "sample": f"each step one serial FP64 oracle H-LU (accumulated) of {p.name} "
+                                       f"(n={p.n}, leaf {p.leaf}, eps {p.eps:g}), the same recipe at a size "
+                                       f"the oracle finishes in seconds"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -154,8 +188,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
-    w = WORKLOADS[args.workload]()
-    probs = w if isinstance(w, list) else [w]
+    probs = rank_problems(args.workload, rank)
     eps = probs[0].eps
     assert all(p.eps == eps for p in probs)
     csrs = [p.matrix() for p in probs]
@@ -204,12 +237,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop() if clocks else None
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * sum(truncs) / total_s
+    value, total_s = job_throughput(sum(truncs), sum(step_ms) / 1e3, world, dev)
     st = work[0].stats()
 
     # end to end through the public API with host buffers: CSR -> device,
@@ -228,12 +256,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         if i >= 1:
             e2e_times.append(time.perf_counter() - t0)
         del Hs
-    e2e_s = sum(e2e_times)
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * sum(truncs) / e2e_s
+    e2e_value, e2e_s = job_throughput(sum(truncs), sum(e2e_times), world, dev)
 
     if rank != 0:
         return
@@ -259,15 +282,11 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     peaks = measured_peaks()
     avg_kern_s = statistics.mean(kern_ms) / 1e3
     achieved = statistics.mean(flops) / avg_kern_s / 1e12
-    name = args.workload if len(probs) > 1 else probs[0].name
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
-        "config": {"workload": name, "instances": len(probs), "n": sum(p.n for p in probs), "leaf": probs[0].leaf,
-                   "eta": probs[0].eta, "eps": eps, "precision": args.precision,
-                   "max_rank": args.max_rank or 64, "l2": "flushed between steps (256 MiB write)",
-                   "parallelism": f"replicas{world}"},
+        "config": workload_config(args, probs, world),
         "setup_s": statistics.mean(step_ms) / 1e3,
         "truncations_per_step": int(statistics.mean(truncs)),
         "tasks_per_step": int(statistics.mean(tasks)),

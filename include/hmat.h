@@ -196,8 +196,9 @@ hmat_status hmat_lu(hmat_ctx* ctx, hmat* H, const hmat_opts* opts);
  * as by hmat_lu; the statistics of every instance report the batch's totals. */
 hmat_status hmat_lu_batched(hmat_ctx* ctx, hmat** G, int count, const hmat_opts* opts);
 
-/* H-matrix multiplication Z <- blocktrunc(Z + alpha X Y) (Section 4) in the
- * accumulated form of Section 5: the product of the root blocks is entered
+/* H-matrix multiplication Z <- blocktrunc(Z + alpha X Y) (Section 4) with
+ * accumulated updates (Section 4, Figs. addproduct, split, flush): the
+ * product of the root blocks is entered
  * into an accumulator by addproduct (the four leaf cases produce low-rank
  * factors or dense blocks), split down the block tree of Z and flushed into
  * Z's leaves, so that every leaf of Z is truncated once per pending product

@@ -12,8 +12,7 @@
 // one-sided Jacobi SVD (Hestenes 1958; Demmel & Veselic 1992), no-pivot
 // Gaussian elimination.  No blocking, fusion or reordering beyond that.
 //
-// Readings where the paper is silent or inconsistent (each also listed in
-// the design doc):
+// Readings where the paper is silent or inconsistent:
 //  * cluster tree: geometric bisection at the midpoint of the tight bounding
 //    box along its longest side (first side on ties), stable partition
 //    "coordinate < midpoint" -> first son; the paper only requires a cluster

@@ -1,0 +1,62 @@
+"""The multi-rank host logic of bench.py on CPU: two gloo ranks aggregate
+units (sum) and time (max over ranks); the batch workload gives every rank
+its own instances."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _worker(rank, world, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import bench
+        v, t = bench.job_throughput(10.0 * (rank + 1), 1.0 + rank, world)
+        dist.barrier()
+        out.put((rank, v, t))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_sum_units_and_take_max_time():
+    import torch.multiprocessing as mp
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, v, t in res:
+        assert t == 2.0  # the slowest rank's time
+        assert v == pytest.approx(30.0 / 2.0)  # all ranks' units over that time
+
+
+def test_single_rank_is_plain_ratio():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.job_throughput(12.0, 4.0, 1) == (3.0, 4.0)
+
+
+def test_batch_ranks_get_their_own_instances():
+    sys.path.insert(0, ROOT)
+    import bench
+    import hmat_synth as hs
+    r0, r1 = bench.rank_problems("diffusion2d_batch64", 0), bench.rank_problems("diffusion2d_batch64", 1)
+    assert [p.seed for p in r0] == [p.seed for p in hs.diffusion2d_batch()]
+    assert len(r0) == len(r1) == 64
+    assert not set(p.seed for p in r0) & set(p.seed for p in r1)
+    # a single H-LU is replicated
+    assert bench.rank_problems("laplace3d_32", 1)[0].n == bench.rank_problems("laplace3d_32", 0)[0].n
