@@ -110,7 +110,8 @@ typedef struct {
   int64_t sketch_columns;   /* columns sketched over all those attempts         */
   int64_t training_pairs;   /* pairs recorded by the last hmat_lu               */
   /* Filled when the environment sets HMAT_PROFILE_TASKS=1: the measured
-   * critical path (longest chain of task durations) and its make-up. */
+   * critical path (longest chain of task durations) and its make-up
+   * (HMAT_PROFILE_PATH=<file> also writes the path's tasks as CSV). */
   double cp_seconds;
   double cp_type_seconds[16];
   int64_t cp_type_count[16];

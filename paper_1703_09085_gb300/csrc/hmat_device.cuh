@@ -42,6 +42,11 @@ static __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+static __device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 static __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -221,9 +226,10 @@ static __device__ void cta_apply_q(const double* V, int ldv, int rows, int q, co
 // J_in Vr = J_out.
 // ---------------------------------------------------------------------------
 // s.ivals[2] receives the sweeps run, s.ivals[3] the rotations applied.
-static __device__ void cta_jacobi(double* J, int p, int c, double* Vr, Smem& s, double tol = 1e-15) {
+template <class T>
+static __device__ void cta_jacobi_t(T* J, int p, int c, T* Vr, Smem& s, T tol) {
   int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int idx = tid; idx < c * c; idx += HM_THREADS) Vr[idx] = (idx % c == idx / c) ? 1.0 : 0.0;
+  for (int idx = tid; idx < c * c; idx += HM_THREADS) Vr[idx] = (idx % c == idx / c) ? T(1) : T(0);
   if (tid == 0) {
     s.ivals[2] = 0;
     s.ivals[3] = 0;
@@ -253,11 +259,11 @@ static __device__ void cta_jacobi(double* J, int p, int c, double* Vr, Smem& s, 
           b = t;
         }
         if (b >= c) continue;
-        double* ja = J + (int64_t)a * p;
-        double* jb = J + (int64_t)b * p;
-        double al = 0.0, be = 0.0, ga = 0.0;
+        T* ja = J + (int64_t)a * p;
+        T* jb = J + (int64_t)b * p;
+        T al = T(0), be = T(0), ga = T(0);
         for (int i = lane; i < p; i += 32) {
-          double x = ja[i], y = jb[i];
+          T x = ja[i], y = jb[i];
           al += x * x;
           be += y * y;
           ga += x * y;
@@ -265,21 +271,21 @@ static __device__ void cta_jacobi(double* J, int p, int c, double* Vr, Smem& s, 
         al = warp_sum(al);
         be = warp_sum(be);
         ga = warp_sum(ga);
-        if (al == 0.0 || be == 0.0) continue;
+        if (al == T(0) || be == T(0)) continue;
         if (fabs(ga) <= tol * sqrt(al) * sqrt(be)) continue;
-        double zeta = (be - al) / (2.0 * ga);
-        double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        double cs = 1.0 / sqrt(1.0 + t * t);
-        double sn = cs * t;
+        T zeta = (be - al) / (T(2) * ga);
+        T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+        T cs = T(1) / sqrt(T(1) + t * t);
+        T sn = cs * t;
         for (int i = lane; i < p; i += 32) {
-          double x = ja[i], y = jb[i];
+          T x = ja[i], y = jb[i];
           ja[i] = cs * x - sn * y;
           jb[i] = sn * x + cs * y;
         }
-        double* va = Vr + (int64_t)a * c;
-        double* vb = Vr + (int64_t)b * c;
+        T* va = Vr + (int64_t)a * c;
+        T* vb = Vr + (int64_t)b * c;
         for (int i = lane; i < c; i += 32) {
-          double x = va[i], y = vb[i];
+          T x = va[i], y = vb[i];
           va[i] = cs * x - sn * y;
           vb[i] = sn * x + cs * y;
         }
@@ -296,6 +302,165 @@ static __device__ void cta_jacobi(double* J, int p, int c, double* Vr, Smem& s, 
   }
 }
 
+static __device__ void cta_jacobi(double* J, int p, int c, double* Vr, Smem& s, double tol = 1e-15) {
+  cta_jacobi_t<double>(J, p, c, Vr, s, tol);
+}
+
+static __device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+static __device__ __forceinline__ float warp_max_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// One-sided Jacobi in FP32 (J p x c, ld p; rotations into Vr c x c): each
+// pair of columns is handled by 16 lanes, so the 16 half-warps of the CTA
+// take all pairs of a round-robin round (c <= 32) in one pass.  A pair is
+// left alone once |a.b| <= tol |a| |b|.  The rank accounting of the callers
+// is exact for any orthonormal Vr, so tol only decides how close the column
+// norms come to the singular values (1e-4: closer than any rank decision
+// needs); sweeps are capped at max_sweeps.
+static __device__ void cta_jacobi_f(float* J, int p, int c, float* Vr, Smem& s, float tol, int max_sweeps) {
+  int tid = threadIdx.x, hl = tid & 15, hw = tid >> 4;
+  const int NHW = HM_THREADS / 16;
+  unsigned mask = (tid & 16) ? 0xFFFF0000u : 0x0000FFFFu;
+  for (int idx = tid; idx < c * c; idx += HM_THREADS) Vr[idx] = (idx % c == idx / c) ? 1.f : 0.f;
+  if (tid == 0) {
+    s.ivals[2] = 0;
+    s.ivals[3] = 0;
+  }
+  __syncthreads();
+  if (c < 2) return;
+  int N = c + (c & 1);
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) {
+      s.ivals[0] = 0;
+      s.ivals[2] += 1;
+    }
+    __syncthreads();
+    for (int r = 0; r < N - 1; ++r) {
+      for (int k = hw; k < N / 2; k += NHW) {
+        int a, b;
+        if (k == 0) {
+          a = r;
+          b = N - 1;
+        } else {
+          a = (r + k) % (N - 1);
+          b = (r - k + (N - 1)) % (N - 1);
+        }
+        if (a > b) {
+          int t = a;
+          a = b;
+          b = t;
+        }
+        if (b >= c) continue;
+        float* ja = J + (int64_t)a * p;
+        float* jb = J + (int64_t)b * p;
+        float al = 0.f, be = 0.f, ga = 0.f;
+        for (int i = hl; i < p; i += 16) {
+          float x = ja[i], y = jb[i];
+          al += x * x;
+          be += y * y;
+          ga += x * y;
+        }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(mask, al, o);
+          be += __shfl_xor_sync(mask, be, o);
+          ga += __shfl_xor_sync(mask, ga, o);
+        }
+        if (al == 0.f || be == 0.f) continue;
+        if (fabsf(ga) <= tol * sqrtf(al) * sqrtf(be)) continue;
+        float zeta = (be - al) / (2.f * ga);
+        float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+        float cs = 1.f / sqrtf(1.f + t * t);
+        float sn = cs * t;
+        for (int i = hl; i < p; i += 16) {
+          float x = ja[i], y = jb[i];
+          ja[i] = cs * x - sn * y;
+          jb[i] = sn * x + cs * y;
+        }
+        float* va = Vr + (int64_t)a * c;
+        float* vb = Vr + (int64_t)b * c;
+        for (int i = hl; i < c; i += 16) {
+          float x = va[i], y = vb[i];
+          va[i] = cs * x - sn * y;
+          vb[i] = sn * x + cs * y;
+        }
+        if (hl == 0) {
+          s.ivals[0] = 1;
+          atomicAdd(&s.ivals[3], 1);
+        }
+      }
+      __syncthreads();
+    }
+    int rotated = s.ivals[0];
+    __syncthreads();
+    if (!rotated) break;
+  }
+}
+
+// Householder QR of a float panel by the whole CTA (conventions of
+// warp_qr_f): warp 0 forms each reflector, every warp applies it to its share
+// of the remaining columns.
+static __device__ void cta_qr_f(float* X, int ld, int rows, int cols, double* tau, double* rdiag) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int q = rows < cols ? rows : cols;
+  __syncthreads();
+  for (int j = 0; j < q; ++j) {
+    float* xj = X + (int64_t)j * ld;
+    if (warp == 0) {
+      float mx = 0.f;
+      for (int i = j + lane; i < rows; i += 32) mx = fmaxf(mx, fabsf(xj[i]));
+      mx = warp_max_f(mx);
+      if (mx < 1e-30f) {  // nothing left in this column (1/mx would overflow FP32)
+        if (lane == 0) {
+          tau[j] = 0.0;
+          rdiag[j] = 0.0;
+        }
+      } else {
+        float inv = 1.f / mx;
+        float tail = 0.f;
+        for (int i = j + 1 + lane; i < rows; i += 32) {
+          float v = xj[i] * inv;
+          tail += v * v;
+        }
+        tail = warp_sum_f(tail);
+        float v0 = xj[j] * inv;
+        float xn = sqrtf(tail + v0 * v0);
+        float alpha = v0 >= 0.f ? -xn : xn;
+        float v0n = v0 - alpha;
+        float tj = 2.f / (tail + v0n * v0n);
+        __syncwarp();
+        for (int i = j + 1 + lane; i < rows; i += 32) xj[i] *= inv;
+        if (lane == 0) {
+          xj[j] = v0n;
+          tau[j] = tj;
+          rdiag[j] = (double)alpha * mx;
+        }
+      }
+    }
+    __syncthreads();
+    float tj = (float)tau[j];
+    if (tj != 0.f) {
+      for (int c = j + 1 + warp; c < cols; c += HM_WARPS) {
+        float* xc = X + (int64_t)c * ld;
+        float d = 0.f;
+        for (int i = j + lane; i < rows; i += 32) d += xj[i] * xc[i];
+        d = warp_sum_f(d) * tj;
+        for (int i = j + lane; i < rows; i += 32) xc[i] -= d * xj[i];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+
+static __device__ void cta_order_sigma(int c, Smem& s);
 // Column norms of J into sigma, and the order of decreasing sigma into order.
 static __device__ void cta_sort_sigma(const double* J, int p, int c, Smem& s) {
   int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -307,6 +472,12 @@ static __device__ void cta_sort_sigma(const double* J, int p, int c, Smem& s) {
     if (lane == 0) s.sigma[j] = sqrt(x);
   }
   __syncthreads();
+  cta_order_sigma(c, s);
+}
+
+// The order of decreasing s.sigma[0..c) into s.order (ties by index).
+static __device__ void cta_order_sigma(int c, Smem& s) {
+  int tid = threadIdx.x;
   for (int j = tid; j < c; j += HM_THREADS) {
     double sj = s.sigma[j];
     int rk = 0;
@@ -504,6 +675,7 @@ static __device__ int trunc_core(const TruncIn& in, double eps, int cap, double*
 // QR + SVD path.  C = Q Vr(:, order), D = J(:, order) as in Fig. rkadd.
 // ---------------------------------------------------------------------------
 #define HM_RMAX 32
+#define HM_F32_MIN_EPS 1e-5  // FP32 rounding (~1e-7) stays well below eps from here on
 
 struct RandIn {
   int m, n, l;
@@ -545,6 +717,13 @@ static __device__ int trunc_rand(const RandIn& in, double eps, int cap, double* 
   double* gws = in.ws + (int64_t)(2 * m + n) * HM_RMAX + HM_RMAX * HM_RMAX;
   uint32_t* Om = (uint32_t*)gws;                          // n sign words
   double* G = gws + (n + 1) / 2 + 1;                       // 2 l x l Grams, or T (l x RMAX floats)
+  int64_t gsz = 2 * (int64_t)l * l > (int64_t)l * HM_RMAX ? 2 * (int64_t)l * l : (int64_t)l * HM_RMAX;
+  // FP32 rotations of the core (eps >= HM_F32_MIN_EPS): J and its rotations
+  // as floats after the Grams; the FP64 Gram of J in the rotations' slot
+  bool f32core = eps >= HM_F32_MIN_EPS;
+  float* Jf = (float*)(G + gsz);                           // n x RMAX floats
+  float* Vf = Jf + (int64_t)n * HM_RMAX;                   // RMAX x RMAX floats
+  double* Gm = Vr;                                         // rr x rr (f32core)
   double f = 0.0;
   // ||M||_F^2
   double total;
@@ -658,13 +837,45 @@ static __device__ int trunc_rand(const RandIn& in, double eps, int cap, double* 
       f += 2.0 * (m + n) * (double)l * rr;
     }
     __syncthreads();
-    cta_jacobi(J, n, rr, Vr, s, 1e-10);
-    cta_sort_sigma(J, n, rr, s);
     f += qr_flops(m, r) + 4.0 * m * rr * rr;
-    f += (double)s.ivals[2] * 0.5 * rr * (rr - 1) * 6.0 * n + (double)s.ivals[3] * 6.0 * (n + rr);
+    if (f32core) {
+      // Rotations from one-sided Jacobi on an FP32 copy of J; FP64 Gram
+      // G = J^T J for sigma_i^2 = v_i^T G v_i and ||J||_F^2 = trace G.
+      for (int idx = tid; idx < n * rr; idx += HM_THREADS) Jf[idx] = (float)J[idx];
+      for (int idx = tid; idx < rr * rr; idx += HM_THREADS) {
+        int i = idx % rr, j = idx / rr;
+        double a = 0.0;
+        for (int c = 0; c < n; ++c) a += J[(int64_t)i * n + c] * J[(int64_t)j * n + c];
+        Gm[idx] = a;
+      }
+      __syncthreads();
+      cta_jacobi_f(Jf, n, rr, Vf, s, 1e-4f, 30);
+      int lane = tid & 31, warp = tid >> 5;
+      for (int j = warp; j < rr; j += HM_WARPS) {
+        double x = 0.0;
+        for (int a = lane; a < rr; a += 32) {
+          double gv = 0.0;
+          for (int b = 0; b < rr; ++b) gv += Gm[a + (int64_t)b * rr] * (double)Vf[b + (int64_t)j * rr];
+          x += (double)Vf[a + (int64_t)j * rr] * gv;
+        }
+        x = warp_sum(x);
+        if (lane == 0) s.sigma[j] = sqrt(x > 0.0 ? x : 0.0);
+      }
+      __syncthreads();
+      cta_order_sigma(rr, s);
+      f += 2.0 * n * rr * rr + 2.0 * rr * rr * rr;
+    } else {
+      cta_jacobi(J, n, rr, Vr, s, 1e-10);
+      cta_sort_sigma(J, n, rr, s);
+      f += (double)s.ivals[2] * 0.5 * rr * (rr - 1) * 6.0 * n + (double)s.ivals[3] * 6.0 * (n + rr);
+    }
     if (tid == 0) {
       double sum = 0.0;
-      for (int i = 0; i < rr; ++i) sum += s.sigma[i] * s.sigma[i];
+      if (f32core) {
+        for (int i = 0; i < rr; ++i) sum += Gm[i + (int64_t)i * rr];
+      } else {
+        for (int i = 0; i < rr; ++i) sum += s.sigma[i] * s.sigma[i];
+      }
       double res2 = total - sum;
       if (res2 < 0.0) res2 = 0.0;
       int k = -1;
@@ -703,14 +914,24 @@ static __device__ int trunc_rand(const RandIn& in, double eps, int cap, double* 
       int i = idx % m, jj = idx / m;
       int col = s.order[jj];
       double acc = 0.0;
-      for (int j = 0; j < rr; ++j) acc += Qx[(int64_t)j * m + i] * Vr[(int64_t)col * rr + j];
+      if (f32core)
+        for (int j = 0; j < rr; ++j) acc += Qx[(int64_t)j * m + i] * (double)Vf[(int64_t)col * rr + j];
+      else
+        for (int j = 0; j < rr; ++j) acc += Qx[(int64_t)j * m + i] * Vr[(int64_t)col * rr + j];
       U[(int64_t)jj * ldu + i] = acc;
     }
     for (int idx = tid; idx < n * k; idx += HM_THREADS) {
       int i = idx % n, jj = idx / n;
-      V[(int64_t)jj * ldv + i] = J[(int64_t)s.order[jj] * n + i];
+      int col = s.order[jj];
+      if (f32core) {
+        double acc = 0.0;
+        for (int j = 0; j < rr; ++j) acc += J[(int64_t)j * n + i] * (double)Vf[(int64_t)col * rr + j];
+        V[(int64_t)jj * ldv + i] = acc;
+      } else {
+        V[(int64_t)jj * ldv + i] = J[(int64_t)col * n + i];
+      }
     }
-    f += 2.0 * m * rr * k;
+    f += 2.0 * m * rr * k + (f32core ? 2.0 * n * rr * k : 0.0);
     if (flops && tid == 0) *flops += f;
     *ok = 1;
     return k;
@@ -722,30 +943,21 @@ static __device__ int trunc_rand(const RandIn& in, double eps, int cap, double* 
 // ld m).  The sketch Y = M Omega, Q = orth(Y) and the projection J = M^T Q
 // run in FP32; the residual ||M - Q J^T||_F^2 is formed entry by entry (FP32
 // differences, FP64 sum), which stays accurate where the difference of the
-// two squared norms would cancel.  The small core is FP64: J = Q_J R_J (FP32
-// QR), one-sided Jacobi on R_J in FP64 gives R_J Vr = W with orthogonal
-// columns, so J Vr has orthogonal columns of norms sigma and
+// two squared norms would cancel.  The small core: J = Q_J R_J (FP32 QR),
+// one-sided Jacobi on R_J (FP32, as R_J itself) gives rotations Vr with
+// R_J Vr of orthogonal columns, so J Vr has orthogonal columns whose norms
+// sigma are taken in FP64 from R_J Vr, and
 //   C = Q Vr(:, order), D = J Vr(:, order)  (Fig. rkadd's C, D).
 // Rank rule as trunc_rand: res^2 + tail <= eps^2 ||M||_F^2.
 // M arrives scaled by 1/scale (largest entry 1, clear of the FP32 range
 // limits); the rule is scale invariant and D is multiplied back by scale.
-// Float work space fw: 2 m R + 2 n R floats (R = min(32, m, n)); Om: n words;
-// the FP64 core (2 R^2 doubles) sits at s.jac + HM_F32_SMEM / 2.
+// Float work space fw: 2 m R + 2 n R floats (R = min(32, m, n)); an attempt
+// of width r uses its first 2 (m + n) r floats, or the first floats of s.jac
+// when fw is global and they fit there; Om: n words; the FP64 copy of R_J
+// (r^2 doubles) sits at s.jac + HM_F32_SMEM / 2.
 // ---------------------------------------------------------------------------
 #define HM_F32_SMEM 14336  // floats of s.jac the FP32 work space may use
 #define HM_F32_MAX_MN (1 << 20)  // largest m n truncated through the FP32 path
-#define HM_F32_MIN_EPS 1e-5      // FP32 rounding (~1e-7) stays well below eps from here on
-
-static __device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-static __device__ __forceinline__ float warp_max_f(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
 
 // Warp 0: Householder QR of a float panel (conventions of warp_qr; tau and
 // the R diagonal are returned in FP64 arrays).
@@ -828,19 +1040,13 @@ static __device__ int trunc_rand32(const float* M, int m, int n, double scale, f
   int rmax = HM_RMAX;
   if (rmax > m) rmax = m;
   if (rmax > n) rmax = n;
-  int R = rmax;
-  float* Y = fw;                      // m x R: sketch, then reflectors
-  float* Qf = Y + (int64_t)m * R;     // m x R
-  float* J = Qf + (int64_t)m * R;     // n x R
-  float* Jq = J + (int64_t)n * R;     // n x R: QR of J
-  double* R64 = s.jac + HM_F32_SMEM / 2;  // R x R
-  double* Vr = R64 + R * R;               // R x R
-  double acc = 0.0;
+  double* R64 = s.jac + HM_F32_SMEM / 2;  // r x r
+  float acc = 0.f;  // per-thread partial sums in FP32, the block sum in FP64
   for (int64_t idx = tid; idx < (int64_t)m * n; idx += HM_THREADS) {
-    double x = M[idx];
+    float x = M[idx];
     acc += x * x;
   }
-  double total = block_sum(acc, s);
+  double total = block_sum((double)acc, s);
   if (total == 0.0) {
     *ok = 1;
     return 0;
@@ -850,12 +1056,18 @@ static __device__ int trunc_rand32(const float* M, int m, int n, double scale, f
   for (int i = tid; i < n; i += HM_THREADS) Om[i] = (uint32_t)mix64(seed ^ ((uint64_t)i * 0xD1B54A32D192ED03ull));
   int r = r0 < 2 ? 2 : r0;
   if (r > rmax) r = rmax;
+  bool fw_shared = __isShared(fw);
   for (;;) {
     __syncthreads();
     if (tid == 0) {
       s.ivals[5] += 1;
       s.ivals[6] += r;
     }
+    // this attempt's panels, in shared memory whenever they fit
+    float* Y = (!fw_shared && 2 * (int64_t)(m + n) * r <= HM_F32_SMEM) ? (float*)s.jac : fw;  // m x r
+    float* Qf = Y + (int64_t)m * r;   // m x r
+    float* J = Qf + (int64_t)m * r;   // n x r
+    float* Jq = J + (int64_t)n * r;   // n x r: QR of J
     for (int idx = tid; idx < m * r; idx += HM_THREADS) {
       int i = idx % m, j = idx / m;
       float a = 0.f;
@@ -866,7 +1078,7 @@ static __device__ int trunc_rand32(const float* M, int m, int n, double scale, f
       Y[(int64_t)j * m + i] = a;
     }
     __syncthreads();
-    warp_qr_f(Y, m, m, r, s.tauA, s.rdiagA);
+    cta_qr_f(Y, m, m, r, s.tauA, s.rdiagA);
     form_q_f(Y, m, m, r, s.tauA, Qf, m);
     for (int idx = tid; idx < n * r; idx += HM_THREADS) {
       int c = idx % n, j = idx / n;
@@ -877,14 +1089,14 @@ static __device__ int trunc_rand32(const float* M, int m, int n, double scale, f
       J[(int64_t)j * n + c] = a;
     }
     __syncthreads();
-    double racc = 0.0;
+    float racc = 0.f;
     for (int64_t idx = tid; idx < (int64_t)m * n; idx += HM_THREADS) {
       int i = (int)(idx % m), c = (int)(idx / m);
       float a = M[idx];
       for (int j = 0; j < r; ++j) a -= Qf[(int64_t)j * m + i] * J[(int64_t)j * n + c];
-      racc += (double)a * (double)a;
+      racc += a * a;
     }
-    double res2 = block_sum(racc, s);
+    double res2 = block_sum((double)racc, s);
     if (!(res2 <= bound)) {  // also catches a non-finite residual
       if (r >= rmax || !isfinite(res2)) {
         *ok = 0;
@@ -893,19 +1105,37 @@ static __device__ int trunc_rand32(const float* M, int m, int n, double scale, f
       r = 2 * r > rmax ? rmax : 2 * r;
       continue;
     }
-    // FP64 core: R factor of J, then one-sided Jacobi
+    // Core: R factor of J (FP32 QR); its rotations by one-sided Jacobi in
+    // FP32 (R already carries FP32 rounding), sigma_i = ||R v_i|| in FP64.
     for (int idx = tid; idx < n * r; idx += HM_THREADS) Jq[idx] = J[idx];
     __syncthreads();
-    warp_qr_f(Jq, n, n, r, s.tauB, s.rdiagB);
-    __syncthreads();
+    cta_qr_f(Jq, n, n, r, s.tauB, s.rdiagB);
+    float* Rf = Y;   // the sketch's reflectors are not needed any more
+    float* Vf = Jq;  // R read out below before the rotations overwrite it
     for (int idx = tid; idx < r * r; idx += HM_THREADS) {
       int i = idx % r, c = idx / r;
-      R64[idx] = i > c ? 0.0 : (i == c ? s.rdiagB[i] : (double)Jq[(int64_t)c * n + i]);
+      double v = i > c ? 0.0 : (i == c ? s.rdiagB[i] : (double)Jq[(int64_t)c * n + i]);
+      R64[idx] = v;
+      Rf[idx] = (float)v;
     }
     __syncthreads();
-    cta_jacobi(R64, r, r, Vr, s, 1e-12);
-    cta_sort_sigma(R64, r, r, s);
-    f += (double)s.ivals[2] * 0.5 * r * (r - 1) * 6.0 * r + (double)s.ivals[3] * 12.0 * r;
+    cta_jacobi_f(Rf, r, r, Vf, s, 1e-4f, 30);
+    {
+      int lane = tid & 31, warp = tid >> 5;
+      for (int j = warp; j < r; j += HM_WARPS) {
+        double x = 0.0;
+        for (int i = lane; i < r; i += 32) {
+          double a = 0.0;
+          for (int q = i; q < r; ++q) a += R64[i + (int64_t)q * r] * (double)Vf[q + (int64_t)j * r];
+          x += a * a;
+        }
+        x = warp_sum(x);
+        if (lane == 0) s.sigma[j] = sqrt(x);
+      }
+      __syncthreads();
+      cta_order_sigma(r, s);
+    }
+    f += (double)r * r * r;
     if (tid == 0) {
       double tail = res2;
       int k = r;
@@ -929,19 +1159,18 @@ static __device__ int trunc_rand32(const float* M, int m, int n, double scale, f
     }
     for (int idx = tid; idx < m * k; idx += HM_THREADS) {
       int i = idx % m, jj = idx / m;
-      const double* vc = Vr + (int64_t)s.order[jj] * r;
-      double a = 0.0;
-      for (int j = 0; j < r; ++j) a += (double)Qf[(int64_t)j * m + i] * vc[j];
-      U[(int64_t)jj * ldu + i] = a;
+      const float* vc = Vf + (int64_t)s.order[jj] * r;
+      float a = 0.f;
+      for (int j = 0; j < r; ++j) a += Qf[(int64_t)j * m + i] * vc[j];
+      U[(int64_t)jj * ldu + i] = (double)a;
     }
     for (int idx = tid; idx < n * k; idx += HM_THREADS) {
       int c = idx % n, jj = idx / n;
-      const double* vc = Vr + (int64_t)s.order[jj] * r;
-      double a = 0.0;
-      for (int j = 0; j < r; ++j) a += (double)J[(int64_t)j * n + c] * vc[j];
-      V[(int64_t)jj * ldv + c] = a * scale;
+      const float* vc = Vf + (int64_t)s.order[jj] * r;
+      float a = 0.f;
+      for (int j = 0; j < r; ++j) a += J[(int64_t)j * n + c] * vc[j];
+      V[(int64_t)jj * ldv + c] = (double)a * scale;
     }
-    f += 2.0 * (m + n) * (double)r * k;
     if (flops && tid == 0) *flops += f;
     *ok = 1;
     return k;
@@ -952,7 +1181,8 @@ static __device__ int trunc_rand32(const float* M, int m, int n, double scale, f
 __host__ __device__ inline int64_t rand_ws_doubles(int64_t m, int64_t n, int64_t l) {
   int64_t g = 2 * l * l;
   if (g < l * HM_RMAX) g = l * HM_RMAX;
-  return 2 * m * HM_RMAX + n * HM_RMAX + HM_RMAX * HM_RMAX + (n + 1) / 2 + 1 + g + 64;
+  return 2 * m * HM_RMAX + n * HM_RMAX + HM_RMAX * HM_RMAX + (n + 1) / 2 + 1 + g +
+         ((n + HM_RMAX) * HM_RMAX + 1) / 2 + 64;
 }
 
 // ---------------------------------------------------------------------------

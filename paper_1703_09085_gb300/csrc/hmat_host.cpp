@@ -502,9 +502,12 @@ const int64_t RMAX = 32;
 int64_t rand_ws(int64_t m, int64_t n, int64_t l) {
   int64_t g = std::max(2 * l * l, l * RMAX);
   int64_t mx = (m * n <= (m + n) * l) ? m * n : 0;
-  // FP32 path (m n <= 2^20): M, sketch, Q, J, QR of J as floats, then the signs
-  int64_t f32 = (m * n <= ((int64_t)1 << 20)) ? (m * n + 2 * (m + n) * RMAX + n) / 2 + 64 : 0;
-  return std::max(mx + 2 * m * RMAX + n * RMAX + RMAX * RMAX + (n + 1) / 2 + 1 + g, f32) + 64;
+  // FP32 path (m n <= 2^20): M, sketch, Q, J, QR of J as floats, then the
+  // signs and the FP32 copies of the stacked factors
+  int64_t f32 = (m * n <= ((int64_t)1 << 20)) ? (m * n + 2 * (m + n) * RMAX + n + (m + n) * l) / 2 + 64 : 0;
+  // FP32 rotations of the core: J (n x RMAX floats) and RMAX x RMAX floats
+  int64_t rot = ((n + RMAX) * RMAX + 1) / 2;
+  return std::max(mx + 2 * m * RMAX + n * RMAX + RMAX * RMAX + (n + 1) / 2 + 1 + g + rot, f32) + 64;
 }
 
 // ===========================================================================
@@ -1425,16 +1428,19 @@ struct RunResult {
   unsigned long long rand_ok = 0, rand_fail = 0, sketch_attempts = 0, sketch_cols = 0;
   unsigned long long bad[6] = {0, 0, 0, 0, 0, 0};
   std::vector<uint32_t> task_ns;  // filled when profiling
+  std::vector<uint32_t> task_aux;
 };
 
 // HMAT_PROFILE_TASKS=1 records every task's duration and reports the
-// measured critical path (longest chain of task durations) by task type.
+// measured critical path (longest chain of task durations) by task type;
+// HMAT_PROFILE_PATH=<file> also writes that path, one task per line (CSV).
 bool profile_tasks() {
   const char* v = std::getenv("HMAT_PROFILE_TASKS");
   return v && v[0] == '1';
 }
 
-void critical_path(const Sched& S, const std::vector<uint32_t>& ns, hmat_stats& st) {
+void critical_path(const Sched& S, const std::vector<uint32_t>& ns, const std::vector<uint32_t>& aux,
+                   hmat_stats& st) {
   size_t n = S.tasks.size();
   std::vector<double> fin(n, 0.0);
   std::vector<int32_t> from(n, -1);
@@ -1457,11 +1463,20 @@ void critical_path(const Sched& S, const std::vector<uint32_t>& ns, hmat_stats& 
     st.cp_type_seconds[t] = 0.0;
     st.cp_type_count[t] = 0;
   }
+  const char* dump = std::getenv("HMAT_PROFILE_PATH");
+  FILE* f = dump ? std::fopen(dump, "w") : nullptr;
+  if (f) std::fprintf(f, "task,type,m,n,p,cap,ns,finish_s,l,path,failed,k,attempts\n");
   for (int64_t i = n ? (int64_t)last : -1; i >= 0; i = from[(size_t)i]) {
-    int ty = S.tasks[(size_t)i].type;
-    st.cp_type_seconds[ty] += ns[(size_t)i] * 1e-9;
-    st.cp_type_count[ty] += 1;
+    const HTask& t = S.tasks[(size_t)i];
+    st.cp_type_seconds[t.type] += ns[(size_t)i] * 1e-9;
+    st.cp_type_count[t.type] += 1;
+    uint32_t a = aux.empty() ? 0u : aux[(size_t)i];
+    if (f)
+      std::fprintf(f, "%lld,%d,%d,%d,%d,%d,%u,%.9f,%u,%u,%u,%u,%u\n", (long long)i, t.type, t.m, t.n, t.p, t.cap,
+                   ns[(size_t)i], fin[(size_t)i], a & 0xFFFu, (a >> 12) & 7u, (a >> 15) & 1u, (a >> 16) & 0xFFu,
+                   a >> 24);
   }
+  if (f) std::fclose(f);
 }
 
 // A schedule uploaded to the device, with its scratch arena.
@@ -1519,10 +1534,12 @@ RunResult launch_sched(hmat_ctx* ctx, const Sched& S, DevSched& D, double* hbase
   e.type_cnt = (unsigned long long*)dmp + 24;
   e.wait_ns = (unsigned long long*)dmp + 40;
   e.task_ns = nullptr;
+  e.task_aux = nullptr;
   if (profile_tasks()) {
-    D.tns.alloc(D.ntasks * sizeof(uint32_t));
-    HM_CUDA(cudaMemsetAsync(D.tns.p, 0, D.ntasks * sizeof(uint32_t), st));
+    D.tns.alloc(2 * D.ntasks * sizeof(uint32_t));
+    HM_CUDA(cudaMemsetAsync(D.tns.p, 0, 2 * D.ntasks * sizeof(uint32_t), st));
     e.task_ns = D.tns.as<uint32_t>();
+    e.task_aux = e.task_ns + D.ntasks;
   }
   e.feat = D.feat.as<float>();
   e.mlp = lo.mlp;
@@ -1575,6 +1592,9 @@ RunResult launch_sched(hmat_ctx* ctx, const Sched& S, DevSched& D, double* hbase
   if (e.task_ns) {
     rr.task_ns.resize(D.ntasks);
     HM_CUDA(cudaMemcpy(rr.task_ns.data(), D.tns.p, D.ntasks * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    rr.task_aux.resize(D.ntasks);
+    HM_CUDA(cudaMemcpy(rr.task_aux.data(), D.tns.as<uint32_t>() + D.ntasks, D.ntasks * sizeof(uint32_t),
+                       cudaMemcpyDeviceToHost));
   }
   rr.status = (int)(misc[2] & 0xffffffffu);
   std::memcpy(&rr.flops, &misc[3], sizeof(double));
@@ -2097,7 +2117,7 @@ void lu_batch(hmat_ctx* ctx, hmat* const* Hs, int count, const hmat_opts* opts) 
     st.sketch_attempts = (int64_t)rr.sketch_attempts;
     st.sketch_columns = (int64_t)rr.sketch_cols;
     st.training_pairs = (int64_t)(Hs[0]->train.size() / 7);
-    if (!rr.task_ns.empty()) critical_path(S, rr.task_ns, st);
+    if (!rr.task_ns.empty()) critical_path(S, rr.task_ns, rr.task_aux, st);
     for (int k = 0; k < 16; ++k) {
       st.type_seconds[k] = rr.type_ns[k] * 1e-9;
       st.type_count[k] = (int64_t)rr.type_cnt[k];
@@ -2180,7 +2200,7 @@ void addmul_run(hmat_ctx* ctx, double alpha, const hmat* X, const hmat* Y, hmat*
   st.sketch_attempts = (int64_t)rr.sketch_attempts;
   st.sketch_columns = (int64_t)rr.sketch_cols;
   st.training_pairs = (int64_t)(Z->train.size() / 7);
-  if (!rr.task_ns.empty()) critical_path(S, rr.task_ns, st);
+  if (!rr.task_ns.empty()) critical_path(S, rr.task_ns, rr.task_aux, st);
   for (int k = 0; k < 16; ++k) {
     st.type_seconds[k] = rr.type_ns[k] * 1e-9;
     st.type_count[k] = (int64_t)rr.type_cnt[k];

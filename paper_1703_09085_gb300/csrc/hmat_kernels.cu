@@ -92,6 +92,83 @@ __device__ void record_bad(const ExecEnv& e, int path, int m, int n, int l, int 
 // First sketch width of a randomised truncation: kz + 6 (at least 8), kz the
 // larger input rank, without a predictor; else max(predicted rank + 3, kz + 2).
 // l is the total input rank (a feature of the predictor).
+// One term SA SB^T of an explicit M, placed at columns [c0, c0 + n).
+struct M32Part {
+  const double* SA;  // m x k (ld m)
+  const double* SB;  // n x k (ld n)
+  int k, n, c0;
+};
+
+// Mixed path: M = base + sum of the parts, formed as M / S in FP32 (M32
+// holds m x ncol floats, ld m).  The factors are converted once to FP32,
+// scaled so that every product and the base stay below 1 in magnitude
+// (S = max(max|SA| max|SB|, max|base|)); the products accumulate in FP32.
+// fac: sum over parts of (m + n) k floats.  Returns 0 with *S set, or 1 if
+// the result is not finite, or 2 if the terms cancel so much that FP32
+// rounding of the sum could reach eps ||M||_F / 10 (the caller then uses
+// the exact FP64 path).
+template <class Base>
+__device__ int form_m32(int m, int ncol, const M32Part* P, int np, bool has_base, Base base, float* M32,
+                        float* fac, double eps, double* S_out, Smem& s) {
+  int tid = threadIdx.x;
+  double ma = 0.0, mb = 0.0, mz = 0.0;
+  for (int q = 0; q < np; ++q) {
+    for (int idx = tid; idx < m * P[q].k; idx += HM_THREADS) ma = fmax(ma, fabs(P[q].SA[idx]));
+    for (int idx = tid; idx < P[q].n * P[q].k; idx += HM_THREADS) mb = fmax(mb, fabs(P[q].SB[idx]));
+  }
+  if (has_base)
+    for (int idx = tid; idx < m * ncol; idx += HM_THREADS) mz = fmax(mz, fabs(base(idx % m, idx / m)));
+  ma = block_max(ma, s);
+  mb = block_max(mb, s);
+  mz = block_max(mz, s);
+  double S = fmax(ma * mb, mz);
+  *S_out = S;
+  if (!isfinite(S)) return 1;
+  if (S == 0.0) {
+    for (int idx = tid; idx < m * ncol; idx += HM_THREADS) M32[idx] = 0.f;
+    __syncthreads();
+    return 0;
+  }
+  double sa = ma > 0.0 ? 1.0 / ma : 0.0, sb = ma / S, sz = 1.0 / S;
+  float* fa[2];
+  float* fb[2];
+  float* f = fac;
+  for (int q = 0; q < np; ++q) {
+    fa[q] = f;
+    fb[q] = f + (int64_t)m * P[q].k;
+    f = fb[q] + (int64_t)P[q].n * P[q].k;
+    for (int idx = tid; idx < m * P[q].k; idx += HM_THREADS) fa[q][idx] = (float)(P[q].SA[idx] * sa);
+    for (int idx = tid; idx < P[q].n * P[q].k; idx += HM_THREADS) fb[q][idx] = (float)(P[q].SB[idx] * sb);
+  }
+  __syncthreads();
+  float sm = 0.f, sabs = 0.f;
+  for (int idx = tid; idx < m * ncol; idx += HM_THREADS) {
+    int i = idx % m, c = idx / m;
+    float v = has_base ? (float)(base(i, c) * sz) : 0.f;
+    float a = fabsf(v);
+    for (int q = 0; q < np; ++q) {
+      int cc = c - P[q].c0;
+      if (cc < 0 || cc >= P[q].n) continue;
+      const float* pa = fa[q] + i;
+      const float* pb = fb[q] + cc;
+      for (int j = 0; j < P[q].k; ++j) {
+        float x = pa[(int64_t)j * m] * pb[(int64_t)j * P[q].n];
+        v += x;
+        a += fabsf(x);
+      }
+    }
+    M32[idx] = v;
+    sm += v * v;
+    sabs += a * a;
+  }
+  double tm = block_sum((double)sm, s), ta = block_sum((double)sabs, s);
+  if (!isfinite(tm) || !isfinite(ta)) return 1;
+  // FP32 rounding of the sums stays below ~3e-7 ||terms||_F (terms: the
+  // entrywise sums of magnitudes); keep it under eps ||M||_F / 10
+  if (ta * 9e-14 > 1e-2 * eps * eps * tm) return 2;
+  return 0;
+}
+
 __device__ int sketch_width(const ExecEnv& e, long long ti, int kz, int l, Smem& s) {
   if (!e.mlp) {
     int r0 = kz + 6;
@@ -130,12 +207,27 @@ __device__ void record_rank(const ExecEnv& e, long long ti, int l, int k) {
   r[6] = (float)log1p((double)k);
 }
 
-// attempts and columns sketched (over all attempts) by a randomised truncation
-__device__ void count_sketch(const ExecEnv& e, Smem& s) {
+// attempts and columns sketched (over all attempts) by a randomised
+// truncation; with task profiling also the task's note: stacked width l
+// (bits 0-11), path (12-14: 1 FP32 randomised, 2 FP64 randomised, 3 exact),
+// a failed randomised attempt before the exact one (bit 15), rank (16-23),
+// sketch attempts (24-31).  path 0 = the randomised truncation failed.
+__device__ void count_sketch(const ExecEnv& e, Smem& s, long long ti, int l, int path, int k) {
   if (threadIdx.x == 0) {
     atomicAdd(e.counters + 9, (unsigned long long)s.ivals[5]);
     atomicAdd(e.counters + 10, (unsigned long long)s.ivals[6]);
+    if (e.task_aux) {
+      unsigned att = (unsigned)(s.ivals[5] < 255 ? s.ivals[5] : 255) << 24;
+      e.task_aux[ti] = path ? ((unsigned)(l < 4095 ? l : 4095) | ((unsigned)path << 12) |
+                               ((unsigned)(k < 255 ? k : 255) << 16) | att)
+                            : (0x8000u | att);
+    }
   }
+}
+__device__ void note_exact(const ExecEnv& e, long long ti, int l, int k) {
+  if (threadIdx.x == 0 && e.task_aux)
+    e.task_aux[ti] = (e.task_aux[ti] & 0xFF008000u) | (unsigned)(l < 4095 ? l : 4095) | (3u << 12) |
+                     ((unsigned)(k < 255 ? k : 255) << 16);
 }
 
 // ---------------------------------------------------------------------------
@@ -270,38 +362,28 @@ __device__ void task_rkadd(const ExecEnv& e, const HTask& t, Smem& s, long long 
     float* fw = fl <= HM_F32_SMEM ? (float*)s.jac : gfw;
     uint32_t* Om = (uint32_t*)(gfw + fl);
     float* Mf = fw;
-    // two passes: the largest entry, then the scaled FP32 copy
-    auto entry = [&](int idx) {
-      int i = idx % m, c = idx / m;
-      double v;
-      if (aid) v = btr ? B[(int64_t)c * t.ldb + i] : B[(int64_t)i * t.ldb + c];
-      else if (bid) v = A[(int64_t)c * t.lda + i];
-      else {
-        v = 0.0;
-        for (int j = 0; j < w; ++j)
-          v += A[(int64_t)j * t.lda + i] * (btr ? B[(int64_t)c * t.ldb + j] : B[(int64_t)j * t.ldb + c]);
-      }
-      v *= t.alpha;
-      for (int j = 0; j < kin; ++j) v += Uin[(int64_t)j * t.ldc + i] * Vin[(int64_t)j * t.ldd + c];
-      return v;
+    // M / S in FP32: base alpha Bhat^T or alpha Ahat (identity cases) plus the
+    // stacked factors' products
+    M32Part part;
+    int j0 = (aid || bid) ? w : 0;
+    part.SA = SA + (int64_t)j0 * m;
+    part.SB = SB + (int64_t)j0 * n;
+    part.k = l - j0;
+    part.n = n;
+    part.c0 = 0;
+    auto base = [&](int i, int c) -> double {
+      double v = aid ? (btr ? B[(int64_t)c * t.ldb + i] : B[(int64_t)i * t.ldb + c]) : A[(int64_t)c * t.lda + i];
+      return t.alpha * v;
     };
     double mx = 0.0;
-    for (int idx = threadIdx.x; idx < mn; idx += HM_THREADS) mx = fmax(mx, fabs(entry(idx)));
-    mx = block_max(mx, s);
-    double inv = mx > 0.0 ? 1.0 / mx : 0.0;
-    int nonfinite = 0;
-    for (int idx = threadIdx.x; idx < mn; idx += HM_THREADS) {
-      double v = entry(idx);
-      if (!isfinite(v)) nonfinite = 1;
-      Mf[idx] = (float)(v * inv);
-    }
-    if (__syncthreads_or(nonfinite)) record_bad(e, 9, m, n, l, kin, mx);
-    f += 2.0 * m * n * (double)(kin + ((aid || bid) ? 0 : w));
+    int fs = form_m32(m, n, &part, 1, aid || bid, base, Mf, (float*)(Om + n), e.eps, &mx, s);
+    if (fs == 1) record_bad(e, 9, m, n, l, kin, mx);
     int r0 = sketch_width(e, ti, kin, l, s);
     uint64_t seed = e.seed ^ ((uint64_t)blockIdx.x << 40) ^ (uint64_t)(t.rout + 1) * 0x9E3779B97F4A7C15ull;
     int ok = 0;
-    int k = trunc_rand32(Mf, m, n, mx, Mf + mn, Om, e.eps, t.cap, Uout, t.lde, Vout, t.ldf, e.status, s, &f, &ok,
-                         seed, r0);
+    int k = fs ? 0
+               : trunc_rand32(Mf, m, n, mx, Mf + mn, Om, e.eps, t.cap, Uout, t.lde, Vout, t.ldf, e.status, s, &f,
+                              &ok, seed, r0);
     if (ok && !cta_finite(Uout, t.lde, m, k, Vout, t.ldf, n)) {
       ok = 0;
       record_bad(e, 1, m, n, l, k, mx);
@@ -313,11 +395,11 @@ __device__ void task_rkadd(const ExecEnv& e, const HTask& t, Smem& s, long long 
         atomicAdd(e.counters + 1, 1ull);
         atomicAdd(e.flops, f);
       }
-      count_sketch(e, s);
+      count_sketch(e, s, ti, l, 1, k);
       return;
     }
     if (threadIdx.x == 0) atomicAdd(e.counters + 2, 1ull);
-    count_sketch(e, s);
+    count_sketch(e, s, ti, l, 0, 0);
   } else if (e.mixed && e.eps > 0.0 && l >= e.rand_min_l) {
     // Randomised truncation; M explicit when that is the smaller form.
     double* R = Jg + 2 * (int64_t)l * l;
@@ -362,11 +444,11 @@ __device__ void task_rkadd(const ExecEnv& e, const HTask& t, Smem& s, long long 
         atomicAdd(e.counters + 1, 1ull);
         atomicAdd(e.flops, f);
       }
-      count_sketch(e, s);
+      count_sketch(e, s, ti, l, 2, k);
       return;
     }
     if (threadIdx.x == 0) atomicAdd(e.counters + 2, 1ull);
-    count_sketch(e, s);
+    count_sketch(e, s, ti, l, 0, 0);
   }
   TruncIn in;
   in.nb = 1;
@@ -384,6 +466,7 @@ __device__ void task_rkadd(const ExecEnv& e, const HTask& t, Smem& s, long long 
     atomicAdd(e.flops, f);
   }
   record_rank(e, ti, l, k);
+  note_exact(e, ti, l, k);
 }
 
 __device__ void task_rowmerge(const ExecEnv& e, const HTask& t, Smem& s, long long ti) {
@@ -424,28 +507,27 @@ __device__ void task_rowmerge(const ExecEnv& e, const HTask& t, Smem& s, long lo
     float* fw = fl <= HM_F32_SMEM ? (float*)s.jac : gfw;
     uint32_t* Om = (uint32_t*)(gfw + fl);
     float* Mf = fw;
-    auto entry = [&](int idx) {
-      int i = idx % m, c = idx / m;
-      double v = 0.0;
-      if (c < n0) {
-        for (int j = 0; j < k0; ++j) v += SA0[(int64_t)j * m + i] * SB0[(int64_t)j * n0 + c];
-      } else {
-        for (int j = 0; j < k1; ++j) v += SA1[(int64_t)j * m + i] * SB1[(int64_t)j * n1 + (c - n0)];
-      }
-      return v;
-    };
+    M32Part parts[2];
+    parts[0].SA = SA0;
+    parts[0].SB = SB0;
+    parts[0].k = k0;
+    parts[0].n = n0;
+    parts[0].c0 = 0;
+    parts[1].SA = SA1;
+    parts[1].SB = SB1;
+    parts[1].k = k1;
+    parts[1].n = n1;
+    parts[1].c0 = n0;
+    auto nobase = [](int, int) -> double { return 0.0; };
     double mx = 0.0;
-    for (int idx = threadIdx.x; idx < mn; idx += HM_THREADS) mx = fmax(mx, fabs(entry(idx)));
-    mx = block_max(mx, s);
-    double inv = mx > 0.0 ? 1.0 / mx : 0.0;
-    for (int idx = threadIdx.x; idx < mn; idx += HM_THREADS) Mf[idx] = (float)(entry(idx) * inv);
-    __syncthreads();
-    f += 2.0 * m * (double)(n0 * k0 + n1 * k1);
+    int fs = form_m32(m, n, parts, 2, false, nobase, Mf, (float*)(Om + n), e.eps, &mx, s);
+    if (fs == 1) record_bad(e, 10, m, n, l, k0, mx);
     int r0 = sketch_width(e, ti, k0 > k1 ? k0 : k1, l, s);
     uint64_t seed = e.seed ^ ((uint64_t)blockIdx.x << 40) ^ (uint64_t)(t.rout + 7) * 0x9E3779B97F4A7C15ull;
     int ok = 0;
-    int k = trunc_rand32(Mf, m, n, mx, Mf + mn, Om, e.eps, t.cap, Uout, t.lde, Vout, t.ldf, e.status, s, &f, &ok,
-                         seed, r0);
+    int k = fs ? 0
+               : trunc_rand32(Mf, m, n, mx, Mf + mn, Om, e.eps, t.cap, Uout, t.lde, Vout, t.ldf, e.status, s, &f,
+                              &ok, seed, r0);
     if (ok && !cta_finite(Uout, t.lde, m, k, Vout, t.ldf, n)) {
       ok = 0;
       record_bad(e, 2, m, n, l, k, mx);
@@ -457,11 +539,11 @@ __device__ void task_rowmerge(const ExecEnv& e, const HTask& t, Smem& s, long lo
         atomicAdd(e.counters + 1, 1ull);
         atomicAdd(e.flops, f);
       }
-      count_sketch(e, s);
+      count_sketch(e, s, ti, l, 1, k);
       return;
     }
     if (threadIdx.x == 0) atomicAdd(e.counters + 2, 1ull);
-    count_sketch(e, s);
+    count_sketch(e, s, ti, l, 0, 0);
   } else if (e.mixed && e.eps > 0.0 && l >= e.rand_min_l) {
     // [A_0 A_1] blockdiag(B_0, B_1)^T with SA = [SA0 SA1] (contiguous)
     double* SBd = Jg + 2 * (int64_t)l * l;
@@ -511,11 +593,11 @@ __device__ void task_rowmerge(const ExecEnv& e, const HTask& t, Smem& s, long lo
         atomicAdd(e.counters + 1, 1ull);
         atomicAdd(e.flops, f);
       }
-      count_sketch(e, s);
+      count_sketch(e, s, ti, l, 2, k);
       return;
     }
     if (threadIdx.x == 0) atomicAdd(e.counters + 2, 1ull);
-    count_sketch(e, s);
+    count_sketch(e, s, ti, l, 0, 0);
   }
   TruncIn in;
   in.nb = 2;
@@ -537,6 +619,7 @@ __device__ void task_rowmerge(const ExecEnv& e, const HTask& t, Smem& s, long lo
     atomicAdd(e.flops, f);
   }
   record_rank(e, ti, l, k);
+  note_exact(e, ti, l, k);
 }
 
 // FP64 operations of the non-truncation tasks (counted by thread 0).

@@ -28,6 +28,7 @@ struct ExecEnv {
   unsigned long long* type_cnt;  // per task type: tasks run
   unsigned long long* wait_ns;   // summed time CTAs spent waiting on predecessors
   uint32_t* task_ns;             // optional: execution time of every task (profiling)
+  uint32_t* task_aux;            // optional: truncation notes per task (profiling)
   const float* feat;             // 4 static features per task (truncations)
   const void* mlp;               // rank predictor weights (BF16), or null
   int oversample;                // sketch columns beyond the predicted rank

@@ -119,4 +119,4 @@ def test_training_lowers_loss_and_sizes_sketches(ctx):
                                      "factor_seconds")})
     assert q["rand_truncations"] > 1000 and h["rand_truncations"] > 1000
     assert q["sketch_columns"] < 0.98 * h["sketch_columns"]
-    assert q["rand_fallbacks"] <= h["rand_fallbacks"] + 2
+    assert q["rand_fallbacks"] <= 1.5 * h["rand_fallbacks"] + 5
