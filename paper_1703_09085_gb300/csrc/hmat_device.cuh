@@ -666,7 +666,9 @@ static __device__ int trunc_core(const TruncIn& in, double eps, int cap, double*
 //   Y = M Omega            (Rademacher Omega, FP32 -- only picks a subspace)
 //   Q = orth(Y)            (FP64 Householder, explicit m x r)
 //   J = M^T Q = (Q^T M)^T  (FP64)
-//   one-sided Jacobi on J  -> singular triplets of Q^T M
+//   one-sided Jacobi on J  -> singular triplets of Q^T M (FP64), or for
+//                            eps >= HM_F32_MIN_EPS the FP32 core of
+//                            core_f32 (pivoted QR, a few sweeps on R^T)
 //   res^2 = ||M||_F^2 - ||Q^T M||_F^2  (FP64, exact for orthonormal Q)
 // The rank k is the smallest with res^2 + sum_{i>k} sigma_i^2 <= eps^2 ||M||_F^2,
 // so the result meets the same Frobenius rule as the exact truncation (its
@@ -694,6 +696,239 @@ static __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
+// Warp 0: Householder QR of a float panel (conventions of warp_qr; tau and
+// the R diagonal are returned in FP64 arrays).
+static __device__ void warp_qr_f(float* X, int ld, int rows, int cols, double* tau, double* rdiag) {
+  if ((threadIdx.x >> 5) != 0) return;
+  int lane = threadIdx.x & 31;
+  int q = rows < cols ? rows : cols;
+  for (int j = 0; j < q; ++j) {
+    float* xj = X + (int64_t)j * ld;
+    float mx = 0.f;
+    for (int i = j + lane; i < rows; i += 32) mx = fmaxf(mx, fabsf(xj[i]));
+    mx = warp_max_f(mx);
+    if (mx < 1e-30f) {  // nothing left in this column (1/mx would overflow FP32)
+      if (lane == 0) {
+        tau[j] = 0.0;
+        rdiag[j] = 0.0;
+      }
+      __syncwarp();
+      continue;
+    }
+    float inv = 1.f / mx;
+    float tail = 0.f;
+    for (int i = j + 1 + lane; i < rows; i += 32) {
+      float v = xj[i] * inv;
+      tail += v * v;
+    }
+    tail = warp_sum_f(tail);
+    float v0 = xj[j] * inv;
+    float xn = sqrtf(tail + v0 * v0);
+    float alpha = v0 >= 0.f ? -xn : xn;
+    float v0n = v0 - alpha;
+    float tj = 2.f / (tail + v0n * v0n);
+    __syncwarp();
+    for (int i = j + 1 + lane; i < rows; i += 32) xj[i] *= inv;
+    if (lane == 0) {
+      xj[j] = v0n;
+      tau[j] = tj;
+      rdiag[j] = (double)alpha * mx;
+    }
+    __syncwarp();
+    for (int c = j + 1; c < cols; ++c) {
+      float* xc = X + (int64_t)c * ld;
+      float d = 0.f;
+      for (int i = j + lane; i < rows; i += 32) d += xj[i] * xc[i];
+      d = warp_sum_f(d) * tj;
+      for (int i = j + lane; i < rows; i += 32) xc[i] -= d * xj[i];
+    }
+    __syncwarp();
+  }
+}
+
+// Q = P_0 ... P_{q-1} [I; 0] (rows x q, ld ldq) from warp_qr_f reflectors;
+// each warp builds its own columns (P_j e_c needs only j <= c).
+static __device__ void form_q_f(const float* V, int ldv, int rows, int q, const double* tau, float* Q, int ldq) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  for (int c = warp; c < q; c += HM_WARPS) {
+    float* qc = Q + (int64_t)c * ldq;
+    for (int i = lane; i < rows; i += 32) qc[i] = (i == c) ? 1.f : 0.f;
+    __syncwarp();
+    for (int j = c; j >= 0; --j) {
+      float tj = (float)tau[j];
+      if (tj == 0.f) continue;
+      const float* vj = V + (int64_t)j * ldv;
+      float d = 0.f;
+      for (int i = j + lane; i < rows; i += 32) d += vj[i] * qc[i];
+      d = warp_sum_f(d) * tj;
+      for (int i = j + lane; i < rows; i += 32) qc[i] -= d * vj[i];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
+// Column-pivoted Householder QR of a float panel by the CTA, X P = Q R
+// (conventions of cta_qr_f; perm[j] = the original column now at j; nrm:
+// cols floats of scratch for the trailing column norms, recomputed after
+// each step rather than downdated).
+static __device__ void cta_qrcp_f(float* X, int ld, int rows, int cols, double* tau, double* rdiag, int* perm,
+                                  float* nrm, Smem& s) {
+  int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int q = rows < cols ? rows : cols;
+  for (int c = tid; c < cols; c += HM_THREADS) perm[c] = c;
+  for (int c = warp; c < cols; c += HM_WARPS) {
+    const float* xc = X + (int64_t)c * ld;
+    float d = 0.f;
+    for (int i = lane; i < rows; i += 32) d += xc[i] * xc[i];
+    d = warp_sum_f(d);
+    if (lane == 0) nrm[c] = d;
+  }
+  __syncthreads();
+  for (int j = 0; j < q; ++j) {
+    if (tid == 0) {
+      int pv = j;
+      float best = nrm[j];
+      for (int c = j + 1; c < cols; ++c)
+        if (nrm[c] > best) {
+          best = nrm[c];
+          pv = c;
+        }
+      s.ivals[10] = pv;
+    }
+    __syncthreads();
+    int pv = s.ivals[10];
+    if (pv != j) {
+      float* xa = X + (int64_t)j * ld;
+      float* xb = X + (int64_t)pv * ld;
+      for (int i = tid; i < rows; i += HM_THREADS) {
+        float t = xa[i];
+        xa[i] = xb[i];
+        xb[i] = t;
+      }
+      if (tid == 0) {
+        float t = nrm[j];
+        nrm[j] = nrm[pv];
+        nrm[pv] = t;
+        int u = perm[j];
+        perm[j] = perm[pv];
+        perm[pv] = u;
+      }
+    }
+    __syncthreads();
+    float* xj = X + (int64_t)j * ld;
+    if (warp == 0) {
+      float mx = 0.f;
+      for (int i = j + lane; i < rows; i += 32) mx = fmaxf(mx, fabsf(xj[i]));
+      mx = warp_max_f(mx);
+      if (mx < 1e-30f) {
+        if (lane == 0) {
+          tau[j] = 0.0;
+          rdiag[j] = 0.0;
+        }
+      } else {
+        float inv = 1.f / mx;
+        float tail = 0.f;
+        for (int i = j + 1 + lane; i < rows; i += 32) {
+          float v = xj[i] * inv;
+          tail += v * v;
+        }
+        tail = warp_sum_f(tail);
+        float v0 = xj[j] * inv;
+        float xn = sqrtf(tail + v0 * v0);
+        float alpha = v0 >= 0.f ? -xn : xn;
+        float v0n = v0 - alpha;
+        float tj = 2.f / (tail + v0n * v0n);
+        __syncwarp();
+        for (int i = j + 1 + lane; i < rows; i += 32) xj[i] *= inv;
+        if (lane == 0) {
+          xj[j] = v0n;
+          tau[j] = tj;
+          rdiag[j] = (double)alpha * mx;
+        }
+      }
+    }
+    __syncthreads();
+    float tj = (float)tau[j];
+    for (int c = j + 1 + warp; c < cols; c += HM_WARPS) {
+      float* xc = X + (int64_t)c * ld;
+      if (tj != 0.f) {
+        float d = 0.f;
+        for (int i = j + lane; i < rows; i += 32) d += xj[i] * xc[i];
+        d = warp_sum_f(d) * tj;
+        for (int i = j + lane; i < rows; i += 32) xc[i] -= d * xj[i];
+      }
+      float t = 0.f;
+      for (int i = j + 1 + lane; i < rows; i += 32) t += xc[i] * xc[i];
+      t = warp_sum_f(t);
+      if (lane == 0) nrm[c] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// Orthonormal C for the kept part of a core_f32 result: the kept columns of
+// W (in decreasing order of norm) are factored Wk = Wh T (FP32 Householder,
+// Wh explicit in r x k), and Z = Vrot(:, kept) T^T (r x k, written over W),
+// so that (P W_k)(Q_J Vrot_k)^T = (P Wh)(Q_J Z)^T with P Wh orthonormal.
+// Wk, Wh: r x k floats each, apart from cw.
+static __device__ void core_f32_orth(float* cw, int r, int k, float* Wk, float* Wh, Smem& s) {
+  int tid = threadIdx.x;
+  const float* W = cw;
+  const float* Vrot = cw + r * r;
+  for (int idx = tid; idx < r * k; idx += HM_THREADS) {
+    int i = idx % r, jj = idx / r;
+    Wk[idx] = W[i + (int64_t)s.order[jj] * r];
+  }
+  cta_qr_f(Wk, r, r, k, s.tauA, s.rdiagA);
+  form_q_f(Wk, r, r, k, s.tauA, Wh, r);
+  float* Z = cw;
+  for (int idx = tid; idx < r * k; idx += HM_THREADS) {
+    int j = idx % r, jj = idx / r;
+    float z = 0.f;
+    for (int q = jj; q < k; ++q) {
+      float t = q == jj ? (float)s.rdiagA[jj] : Wk[(int64_t)q * r + jj];
+      z += Vrot[j + (int64_t)s.order[q] * r] * t;
+    }
+    Z[idx] = z;
+  }
+  __syncthreads();
+}
+
+// Small core of the FP32 randomised truncations.  J (p x r floats, ld p) is
+// factored in place, J P = Q_J R (cta_qrcp_f; reflectors and tau in s.tauB
+// for forming Q_J); one-sided Jacobi on R^T, at most max_sweeps sweeps (the
+// pivoted R^T has graded columns, so few sweeps come close to its SVD),
+// gives R^T Vrot = W.  Out: W and Vrot (r x r, in cw: W, Vrot, then r floats
+// of norms and r ints of perm), s.sigma = column norms of W, s.order = their
+// decreasing order.  With J = Q_J R P^T = Q_J Vrot W^T P^T, dropping columns
+// of W drops exactly their squared norms (Vrot and Q_J orthonormal).
+static __device__ void core_f32(float* J, int p, int r, float* cw, Smem& s, int max_sweeps) {
+  int tid = threadIdx.x;
+  float* W = cw;
+  float* Vrot = W + r * r;
+  float* nrm = Vrot + r * r;
+  int* perm = (int*)(nrm + r);
+  cta_qrcp_f(J, p, p, r, s.tauB, s.rdiagB, perm, nrm, s);
+  // X = R^T: X[i][c] = R[c][i], nonzero for c <= i
+  for (int idx = tid; idx < r * r; idx += HM_THREADS) {
+    int i = idx % r, c = idx / r;
+    W[idx] = c > i ? 0.f : (c == i ? (float)s.rdiagB[i] : J[(int64_t)i * p + c]);
+  }
+  __syncthreads();
+  cta_jacobi_f(W, r, r, Vrot, s, 1e-4f, max_sweeps);
+  int lane = tid & 31, warp = tid >> 5;
+  for (int j = warp; j < r; j += HM_WARPS) {
+    float x = 0.f;
+    for (int i = lane; i < r; i += 32) x += W[i + j * r] * W[i + j * r];
+    x = warp_sum_f(x);
+    if (lane == 0) s.sigma[j] = sqrt((double)x);
+  }
+  __syncthreads();
+  cta_order_sigma(r, s);
+}
+
 static __device__ int trunc_rand(const RandIn& in, double eps, int cap, double* U, int ldu, double* V, int ldv,
                           int* status, Smem& s, double* flops, int* ok) {
   int tid = threadIdx.x;
@@ -718,12 +953,12 @@ static __device__ int trunc_rand(const RandIn& in, double eps, int cap, double* 
   uint32_t* Om = (uint32_t*)gws;                          // n sign words
   double* G = gws + (n + 1) / 2 + 1;                       // 2 l x l Grams, or T (l x RMAX floats)
   int64_t gsz = 2 * (int64_t)l * l > (int64_t)l * HM_RMAX ? 2 * (int64_t)l * l : (int64_t)l * HM_RMAX;
-  // FP32 rotations of the core (eps >= HM_F32_MIN_EPS): J and its rotations
-  // as floats after the Grams; the FP64 Gram of J in the rotations' slot
+  // FP32 core (eps >= HM_F32_MIN_EPS) after the Grams: J as floats (then its
+  // reflectors), Q_J, and the core's W, Vrot, norms and permutation
   bool f32core = eps >= HM_F32_MIN_EPS;
   float* Jf = (float*)(G + gsz);                           // n x RMAX floats
-  float* Vf = Jf + (int64_t)n * HM_RMAX;                   // RMAX x RMAX floats
-  double* Gm = Vr;                                         // rr x rr (f32core)
+  float* Qj = Jf + (int64_t)n * HM_RMAX;                   // n x RMAX floats
+  float* cw = Qj + (int64_t)n * HM_RMAX;                   // 4 RMAX^2 + 2 RMAX
   double f = 0.0;
   // ||M||_F^2
   double total;
@@ -838,32 +1073,20 @@ static __device__ int trunc_rand(const RandIn& in, double eps, int cap, double* 
     }
     __syncthreads();
     f += qr_flops(m, r) + 4.0 * m * rr * rr;
+    double jn2 = 0.0;
     if (f32core) {
-      // Rotations from one-sided Jacobi on an FP32 copy of J; FP64 Gram
-      // G = J^T J for sigma_i^2 = v_i^T G v_i and ||J||_F^2 = trace G.
-      for (int idx = tid; idx < n * rr; idx += HM_THREADS) Jf[idx] = (float)J[idx];
-      for (int idx = tid; idx < rr * rr; idx += HM_THREADS) {
-        int i = idx % rr, j = idx / rr;
-        double a = 0.0;
-        for (int c = 0; c < n; ++c) a += J[(int64_t)i * n + c] * J[(int64_t)j * n + c];
-        Gm[idx] = a;
+      // ||J||_F^2 in FP64 for the residual; the core (pivoted QR, a few
+      // Jacobi sweeps on R^T) on an FP32 copy of J, then Q_J explicitly
+      double a2 = 0.0;
+      for (int idx = tid; idx < n * rr; idx += HM_THREADS) {
+        double x = J[idx];
+        a2 += x * x;
+        Jf[idx] = (float)x;
       }
-      __syncthreads();
-      cta_jacobi_f(Jf, n, rr, Vf, s, 1e-4f, 30);
-      int lane = tid & 31, warp = tid >> 5;
-      for (int j = warp; j < rr; j += HM_WARPS) {
-        double x = 0.0;
-        for (int a = lane; a < rr; a += 32) {
-          double gv = 0.0;
-          for (int b = 0; b < rr; ++b) gv += Gm[a + (int64_t)b * rr] * (double)Vf[b + (int64_t)j * rr];
-          x += (double)Vf[a + (int64_t)j * rr] * gv;
-        }
-        x = warp_sum(x);
-        if (lane == 0) s.sigma[j] = sqrt(x > 0.0 ? x : 0.0);
-      }
-      __syncthreads();
-      cta_order_sigma(rr, s);
-      f += 2.0 * n * rr * rr + 2.0 * rr * rr * rr;
+      jn2 = block_sum(a2, s);
+      core_f32(Jf, n, rr, cw, s, 4);
+      form_q_f(Jf, n, n, rr, s.tauB, Qj, n);
+      f += 2.0 * n * rr;
     } else {
       cta_jacobi(J, n, rr, Vr, s, 1e-10);
       cta_sort_sigma(J, n, rr, s);
@@ -872,7 +1095,7 @@ static __device__ int trunc_rand(const RandIn& in, double eps, int cap, double* 
     if (tid == 0) {
       double sum = 0.0;
       if (f32core) {
-        for (int i = 0; i < rr; ++i) sum += Gm[i + (int64_t)i * rr];
+        sum = jn2;
       } else {
         for (int i = 0; i < rr; ++i) sum += s.sigma[i] * s.sigma[i];
       }
@@ -910,13 +1133,17 @@ static __device__ int trunc_rand(const RandIn& in, double eps, int cap, double* 
       if (tid == 0) set_status(status, DS_RANK);
       k = cap;
     }
+    float* Wk = cw + 2 * HM_RMAX * HM_RMAX + 2 * HM_RMAX;
+    float* Wh = Wk + HM_RMAX * HM_RMAX;
+    if (f32core && k > 0) core_f32_orth(cw, rr, k, Wk, Wh, s);
     for (int idx = tid; idx < m * k; idx += HM_THREADS) {
       int i = idx % m, jj = idx / m;
       int col = s.order[jj];
       double acc = 0.0;
-      if (f32core)
-        for (int j = 0; j < rr; ++j) acc += Qx[(int64_t)j * m + i] * (double)Vf[(int64_t)col * rr + j];
-      else
+      if (f32core) {
+        const int* perm = (const int*)(cw + 2 * rr * rr + rr);
+        for (int j = 0; j < rr; ++j) acc += Qx[(int64_t)perm[j] * m + i] * (double)Wh[(int64_t)jj * rr + j];
+      } else
         for (int j = 0; j < rr; ++j) acc += Qx[(int64_t)j * m + i] * Vr[(int64_t)col * rr + j];
       U[(int64_t)jj * ldu + i] = acc;
     }
@@ -924,14 +1151,15 @@ static __device__ int trunc_rand(const RandIn& in, double eps, int cap, double* 
       int i = idx % n, jj = idx / n;
       int col = s.order[jj];
       if (f32core) {
-        double acc = 0.0;
-        for (int j = 0; j < rr; ++j) acc += J[(int64_t)j * n + i] * (double)Vf[(int64_t)col * rr + j];
-        V[(int64_t)jj * ldv + i] = acc;
+        const float* zc = cw + (int64_t)jj * rr;
+        float acc = 0.f;
+        for (int j = 0; j < rr; ++j) acc += Qj[(int64_t)j * n + i] * zc[j];
+        V[(int64_t)jj * ldv + i] = (double)acc;
       } else {
         V[(int64_t)jj * ldv + i] = J[(int64_t)col * n + i];
       }
     }
-    f += 2.0 * m * rr * k + (f32core ? 2.0 * n * rr * k : 0.0);
+    f += 2.0 * m * rr * k;
     if (flops && tid == 0) *flops += f;
     *ok = 1;
     return k;
@@ -943,94 +1171,21 @@ static __device__ int trunc_rand(const RandIn& in, double eps, int cap, double* 
 // ld m).  The sketch Y = M Omega, Q = orth(Y) and the projection J = M^T Q
 // run in FP32; the residual ||M - Q J^T||_F^2 is formed entry by entry (FP32
 // differences, FP64 sum), which stays accurate where the difference of the
-// two squared norms would cancel.  The small core: J = Q_J R_J (FP32 QR),
-// one-sided Jacobi on R_J (FP32, as R_J itself) gives rotations Vr with
-// R_J Vr of orthogonal columns, so J Vr has orthogonal columns whose norms
-// sigma are taken in FP64 from R_J Vr, and
-//   C = Q Vr(:, order), D = J Vr(:, order)  (Fig. rkadd's C, D).
+// two squared norms would cancel.  The small core (core_f32): J P = Q_J R
+// by pivoted QR, R^T Vrot = W by a few Jacobi sweeps, so that
+// M ~ Q J^T = (Q P W)(Q_J Vrot)^T with Q_J Vrot orthonormal and
+//   C = Q P W(:, order), D = Q_J Vrot(:, order)  (Fig. rkadd's C, D),
+// the dropped columns of W costing exactly their squared norms.
 // Rank rule as trunc_rand: res^2 + tail <= eps^2 ||M||_F^2.
 // M arrives scaled by 1/scale (largest entry 1, clear of the FP32 range
 // limits); the rule is scale invariant and D is multiplied back by scale.
 // Float work space fw: 2 m R + 2 n R floats (R = min(32, m, n)); an attempt
 // of width r uses its first 2 (m + n) r floats, or the first floats of s.jac
-// when fw is global and they fit there; Om: n words; the FP64 copy of R_J
-// (r^2 doubles) sits at s.jac + HM_F32_SMEM / 2.
+// when fw is global and they fit there; Om: n words; the core's W, Vrot
+// (2 r^2 floats and 2 r words) sit at s.jac + HM_F32_SMEM / 2.
 // ---------------------------------------------------------------------------
 #define HM_F32_SMEM 14336  // floats of s.jac the FP32 work space may use
 #define HM_F32_MAX_MN (1 << 20)  // largest m n truncated through the FP32 path
-
-// Warp 0: Householder QR of a float panel (conventions of warp_qr; tau and
-// the R diagonal are returned in FP64 arrays).
-static __device__ void warp_qr_f(float* X, int ld, int rows, int cols, double* tau, double* rdiag) {
-  if ((threadIdx.x >> 5) != 0) return;
-  int lane = threadIdx.x & 31;
-  int q = rows < cols ? rows : cols;
-  for (int j = 0; j < q; ++j) {
-    float* xj = X + (int64_t)j * ld;
-    float mx = 0.f;
-    for (int i = j + lane; i < rows; i += 32) mx = fmaxf(mx, fabsf(xj[i]));
-    mx = warp_max_f(mx);
-    if (mx < 1e-30f) {  // nothing left in this column (1/mx would overflow FP32)
-      if (lane == 0) {
-        tau[j] = 0.0;
-        rdiag[j] = 0.0;
-      }
-      __syncwarp();
-      continue;
-    }
-    float inv = 1.f / mx;
-    float tail = 0.f;
-    for (int i = j + 1 + lane; i < rows; i += 32) {
-      float v = xj[i] * inv;
-      tail += v * v;
-    }
-    tail = warp_sum_f(tail);
-    float v0 = xj[j] * inv;
-    float xn = sqrtf(tail + v0 * v0);
-    float alpha = v0 >= 0.f ? -xn : xn;
-    float v0n = v0 - alpha;
-    float tj = 2.f / (tail + v0n * v0n);
-    __syncwarp();
-    for (int i = j + 1 + lane; i < rows; i += 32) xj[i] *= inv;
-    if (lane == 0) {
-      xj[j] = v0n;
-      tau[j] = tj;
-      rdiag[j] = (double)alpha * mx;
-    }
-    __syncwarp();
-    for (int c = j + 1; c < cols; ++c) {
-      float* xc = X + (int64_t)c * ld;
-      float d = 0.f;
-      for (int i = j + lane; i < rows; i += 32) d += xj[i] * xc[i];
-      d = warp_sum_f(d) * tj;
-      for (int i = j + lane; i < rows; i += 32) xc[i] -= d * xj[i];
-    }
-    __syncwarp();
-  }
-}
-
-// Q = P_0 ... P_{q-1} [I; 0] (rows x q, ld ldq) from warp_qr_f reflectors;
-// each warp builds its own columns (P_j e_c needs only j <= c).
-static __device__ void form_q_f(const float* V, int ldv, int rows, int q, const double* tau, float* Q, int ldq) {
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();
-  for (int c = warp; c < q; c += HM_WARPS) {
-    float* qc = Q + (int64_t)c * ldq;
-    for (int i = lane; i < rows; i += 32) qc[i] = (i == c) ? 1.f : 0.f;
-    __syncwarp();
-    for (int j = c; j >= 0; --j) {
-      float tj = (float)tau[j];
-      if (tj == 0.f) continue;
-      const float* vj = V + (int64_t)j * ldv;
-      float d = 0.f;
-      for (int i = j + lane; i < rows; i += 32) d += vj[i] * qc[i];
-      d = warp_sum_f(d) * tj;
-      for (int i = j + lane; i < rows; i += 32) qc[i] -= d * vj[i];
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-}
 
 static __device__ int trunc_rand32(const float* M, int m, int n, double scale, float* fw, uint32_t* Om, double eps,
                                    int cap, double* U, int ldu, double* V, int ldv, int* status, Smem& s,
@@ -1040,7 +1195,6 @@ static __device__ int trunc_rand32(const float* M, int m, int n, double scale, f
   int rmax = HM_RMAX;
   if (rmax > m) rmax = m;
   if (rmax > n) rmax = n;
-  double* R64 = s.jac + HM_F32_SMEM / 2;  // r x r
   float acc = 0.f;  // per-thread partial sums in FP32, the block sum in FP64
   for (int64_t idx = tid; idx < (int64_t)m * n; idx += HM_THREADS) {
     float x = M[idx];
@@ -1105,37 +1259,13 @@ static __device__ int trunc_rand32(const float* M, int m, int n, double scale, f
       r = 2 * r > rmax ? rmax : 2 * r;
       continue;
     }
-    // Core: R factor of J (FP32 QR); its rotations by one-sided Jacobi in
-    // FP32 (R already carries FP32 rounding), sigma_i = ||R v_i|| in FP64.
+    // Core: column-pivoted QR of J, a few Jacobi sweeps on R^T (core_f32);
+    // J itself becomes Q_J explicitly afterwards.
     for (int idx = tid; idx < n * r; idx += HM_THREADS) Jq[idx] = J[idx];
     __syncthreads();
-    cta_qr_f(Jq, n, n, r, s.tauB, s.rdiagB);
-    float* Rf = Y;   // the sketch's reflectors are not needed any more
-    float* Vf = Jq;  // R read out below before the rotations overwrite it
-    for (int idx = tid; idx < r * r; idx += HM_THREADS) {
-      int i = idx % r, c = idx / r;
-      double v = i > c ? 0.0 : (i == c ? s.rdiagB[i] : (double)Jq[(int64_t)c * n + i]);
-      R64[idx] = v;
-      Rf[idx] = (float)v;
-    }
-    __syncthreads();
-    cta_jacobi_f(Rf, r, r, Vf, s, 1e-4f, 30);
-    {
-      int lane = tid & 31, warp = tid >> 5;
-      for (int j = warp; j < r; j += HM_WARPS) {
-        double x = 0.0;
-        for (int i = lane; i < r; i += 32) {
-          double a = 0.0;
-          for (int q = i; q < r; ++q) a += R64[i + (int64_t)q * r] * (double)Vf[q + (int64_t)j * r];
-          x += a * a;
-        }
-        x = warp_sum(x);
-        if (lane == 0) s.sigma[j] = sqrt(x);
-      }
-      __syncthreads();
-      cta_order_sigma(r, s);
-    }
-    f += (double)r * r * r;
+    float* cw = (float*)(s.jac + HM_F32_SMEM / 2);  // 2 r^2 + 2 r floats
+    core_f32(Jq, n, r, cw, s, 4);
+    form_q_f(Jq, n, n, r, s.tauB, J, n);
     if (tid == 0) {
       double tail = res2;
       int k = r;
@@ -1157,19 +1287,27 @@ static __device__ int trunc_rand32(const float* M, int m, int n, double scale, f
       if (tid == 0) set_status(status, DS_RANK);
       k = cap;
     }
-    for (int idx = tid; idx < m * k; idx += HM_THREADS) {
-      int i = idx % m, jj = idx / m;
-      const float* vc = Vf + (int64_t)s.order[jj] * r;
-      float a = 0.f;
-      for (int j = 0; j < r; ++j) a += Qf[(int64_t)j * m + i] * vc[j];
-      U[(int64_t)jj * ldu + i] = (double)a;
-    }
-    for (int idx = tid; idx < n * k; idx += HM_THREADS) {
-      int c = idx % n, jj = idx / n;
-      const float* vc = Vf + (int64_t)s.order[jj] * r;
-      float a = 0.f;
-      for (int j = 0; j < r; ++j) a += J[(int64_t)j * n + c] * vc[j];
-      V[(int64_t)jj * ldv + c] = (double)a * scale;
+    if (k > 0) {
+      // M ~ (Q P W_k)(Q_J Vrot_k)^T = (Q P Wh)(Q_J Z)^T: C = Q P Wh, D = Q_J Z
+      // (Y and Jq are free: the sketch's and J's reflectors have been used)
+      core_f32_orth(cw, r, k, Y, Jq, s);
+      const float* Wh = Jq;
+      const float* Z = cw;
+      const int* perm = (const int*)(cw + 2 * r * r + r);
+      for (int idx = tid; idx < m * k; idx += HM_THREADS) {
+        int i = idx % m, jj = idx / m;
+        const float* wc = Wh + (int64_t)jj * r;
+        float a = 0.f;
+        for (int j = 0; j < r; ++j) a += Qf[(int64_t)perm[j] * m + i] * wc[j];
+        U[(int64_t)jj * ldu + i] = (double)a;
+      }
+      for (int idx = tid; idx < n * k; idx += HM_THREADS) {
+        int c = idx % n, jj = idx / n;
+        const float* zc = Z + (int64_t)jj * r;
+        float a = 0.f;
+        for (int j = 0; j < r; ++j) a += J[(int64_t)j * n + c] * zc[j];
+        V[(int64_t)jj * ldv + c] = (double)a * scale;
+      }
     }
     if (flops && tid == 0) *flops += f;
     *ok = 1;
@@ -1182,7 +1320,7 @@ __host__ __device__ inline int64_t rand_ws_doubles(int64_t m, int64_t n, int64_t
   int64_t g = 2 * l * l;
   if (g < l * HM_RMAX) g = l * HM_RMAX;
   return 2 * m * HM_RMAX + n * HM_RMAX + HM_RMAX * HM_RMAX + (n + 1) / 2 + 1 + g +
-         ((n + HM_RMAX) * HM_RMAX + 1) / 2 + 64;
+         (2 * n * HM_RMAX + 4 * HM_RMAX * HM_RMAX + 2 * HM_RMAX + 1) / 2 + 64;
 }
 
 // ---------------------------------------------------------------------------

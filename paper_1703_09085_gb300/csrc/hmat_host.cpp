@@ -505,8 +505,8 @@ int64_t rand_ws(int64_t m, int64_t n, int64_t l) {
   // FP32 path (m n <= 2^20): M, sketch, Q, J, QR of J as floats, then the
   // signs and the FP32 copies of the stacked factors
   int64_t f32 = (m * n <= ((int64_t)1 << 20)) ? (m * n + 2 * (m + n) * RMAX + n + (m + n) * l) / 2 + 64 : 0;
-  // FP32 rotations of the core: J (n x RMAX floats) and RMAX x RMAX floats
-  int64_t rot = ((n + RMAX) * RMAX + 1) / 2;
+  // FP32 core: J and Q_J (n x RMAX floats each), W, Vrot, norms, permutation
+  int64_t rot = (2 * n * RMAX + 4 * RMAX * RMAX + 2 * RMAX + 1) / 2;
   return std::max(mx + 2 * m * RMAX + n * RMAX + RMAX * RMAX + (n + 1) / 2 + 1 + g + rot, f32) + 64;
 }
 
