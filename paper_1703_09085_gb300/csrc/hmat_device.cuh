@@ -1315,6 +1315,68 @@ static __device__ int trunc_rand32(const float* M, int m, int n, double scale, f
   }
 }
 
+// ---------------------------------------------------------------------------
+// Mixed-precision truncation of a factored M = SA SB^T (m x n, stacked width
+// l), the steps of Fig. rkadd in FP32: SB = Q_B R_B (Householder), then
+// Mhat = SA R_B^T (m x l) carries all of M (M = Mhat Q_B^T, Q_B orthonormal),
+// so truncating Mhat by trunc_rand32 truncates M with the same error, and
+// D = Q_B Dhat.  SAf, SBf: FP32 copies scaled so that |SAf SBf^T| <= 1
+// entrywise (scale S restores M).  Mhat is formed with the cancellation guard
+// of the explicit path (a failure returns with *ok = 0, *guard = 1).
+// Float scratch fs: Mhat (m l), Q_B (n l), panels 2 (m + l) RMAX, l sign
+// words; double scratch ds: 2 l + l RMAX.
+// ---------------------------------------------------------------------------
+static __device__ int trunc_fact32(int m, int n, int l, const float* SAf, float* SBf, double S, float* fs,
+                                   double* ds, double eps, int cap, double* U, int ldu, double* V, int ldv,
+                                   int* status, Smem& s, double* flops, int* ok, int* guard, uint64_t seed, int r0) {
+  int tid = threadIdx.x;
+  *ok = 0;
+  *guard = 0;
+  float* Mh = fs;
+  float* QB = Mh + (int64_t)m * l;
+  float* pan = QB + (int64_t)n * l;
+  uint32_t* Om = (uint32_t*)(pan + 2 * (int64_t)(m + l) * HM_RMAX);
+  double* tq = ds;
+  double* rq = ds + l;
+  double* Vh = ds + 2 * l;  // l x k (ld l)
+  cta_qr_f(SBf, n, n, l, tq, rq);
+  float sm = 0.f, sabs = 0.f;
+  for (int idx = tid; idx < m * l; idx += HM_THREADS) {
+    int i = idx % m, c = idx / m;
+    float v = 0.f, a = 0.f;
+    for (int j = c; j < l; ++j) {
+      float rcj = j == c ? (float)rq[c] : SBf[(int64_t)j * n + c];
+      float x = SAf[(int64_t)j * m + i] * rcj;
+      v += x;
+      a += fabsf(x);
+    }
+    Mh[idx] = v;
+    sm += v * v;
+    sabs += a * a;
+  }
+  double tm = block_sum((double)sm, s), ta = block_sum((double)sabs, s);
+  if (!isfinite(tm) || !isfinite(ta) || ta * 9e-14 > 1e-2 * eps * eps * tm) {
+    *guard = 1;
+    return 0;
+  }
+  int k = trunc_rand32(Mh, m, l, S, pan, Om, eps, cap, U, ldu, Vh, l, status, s, flops, ok, seed, r0);
+  if (!*ok) return 0;
+  form_q_f(SBf, n, n, l, tq, QB, n);
+  for (int idx = tid; idx < n * k; idx += HM_THREADS) {
+    int c = idx % n, jj = idx / n;
+    float a = 0.f;
+    for (int j = 0; j < l; ++j) a += QB[(int64_t)j * n + c] * (float)Vh[(int64_t)jj * l + j];
+    V[(int64_t)jj * ldv + c] = (double)a;
+  }
+  __syncthreads();
+  return k;
+}
+
+// Scratch of trunc_fact32 past the FP32 factor copies: floats, then doubles.
+__host__ __device__ inline int64_t fact32_floats(int64_t m, int64_t n, int64_t l) {
+  return m * l + n * l + 2 * (m + l) * HM_RMAX + l + 2;
+}
+
 // Doubles of scratch trunc_rand needs.
 __host__ __device__ inline int64_t rand_ws_doubles(int64_t m, int64_t n, int64_t l) {
   int64_t g = 2 * l * l;

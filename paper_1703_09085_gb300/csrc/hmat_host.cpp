@@ -507,7 +507,9 @@ int64_t rand_ws(int64_t m, int64_t n, int64_t l) {
   int64_t f32 = (m * n <= ((int64_t)1 << 20)) ? (m * n + 2 * (m + n) * RMAX + n + (m + n) * l) / 2 + 64 : 0;
   // FP32 core: J and Q_J (n x RMAX floats each), W, Vrot, norms, permutation
   int64_t rot = (2 * n * RMAX + 4 * RMAX * RMAX + 2 * RMAX + 1) / 2;
-  return std::max(mx + 2 * m * RMAX + n * RMAX + RMAX * RMAX + (n + 1) / 2 + 1 + g + rot, f32) + 64;
+  // FP32 factored path: SA, SB copies, Mhat, Q_B, panels, signs; then doubles
+  int64_t fact = (2 * m * l + 2 * n * l + 2 * (m + l) * RMAX + l + 3) / 2 + 2 * l + l * RMAX + 16;
+  return std::max(std::max(mx + 2 * m * RMAX + n * RMAX + RMAX * RMAX + (n + 1) / 2 + 1 + g + rot, f32), fact) + 64;
 }
 
 // ===========================================================================

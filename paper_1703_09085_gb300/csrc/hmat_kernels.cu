@@ -300,6 +300,51 @@ __device__ void task_densify(const ExecEnv& e, const HTask& t, Smem& s) {
   }
 }
 
+// FP32 factored truncation inside a task (trunc_fact32): SA (m x l) and SB
+// (n x l, or two diagonal blocks n0 x k0 and n1 x k1 when sb1 is given) are
+// copied to FP32, scaled by their largest entries.  Returns the rank; *ok = 0
+// when the caller must fall back to the exact truncation.
+__device__ int task_fact32(const ExecEnv& e, const HTask& t, Smem& s, int m, int n, int l, const double* SA,
+                           const double* SB0, int n0, int k0, const double* SB1, int n1, int k1, double* ws,
+                           uint64_t seed, int r0, double* f, int* ok) {
+  int tid = threadIdx.x;
+  *ok = 0;
+  double ma = 0.0, mb = 0.0;
+  for (int idx = tid; idx < m * l; idx += HM_THREADS) ma = fmax(ma, fabs(SA[idx]));
+  for (int idx = tid; idx < n0 * k0; idx += HM_THREADS) mb = fmax(mb, fabs(SB0[idx]));
+  for (int idx = tid; idx < n1 * k1; idx += HM_THREADS) mb = fmax(mb, fabs(SB1[idx]));
+  ma = block_max(ma, s);
+  mb = block_max(mb, s);
+  double S = ma * mb;
+  if (!(S > 0.0) || !isfinite(S)) return 0;
+  float* SAf = (float*)ws;
+  float* SBf = SAf + (int64_t)m * l;
+  float* fs = SBf + (int64_t)n * l;
+  int64_t nf = (int64_t)m * l + (int64_t)n * l + fact32_floats(m, n, l);
+  double* ds = ws + (nf + 1) / 2;
+  double ia = 1.0 / ma, ib = 1.0 / mb;
+  for (int idx = tid; idx < m * l; idx += HM_THREADS) SAf[idx] = (float)(SA[idx] * ia);
+  for (int idx = tid; idx < n * l; idx += HM_THREADS) {
+    int c = idx % n, j = idx / n;
+    double v = 0.0;
+    if (j < k0) {
+      if (c < n0) v = SB0[(int64_t)j * n0 + c];
+    } else if (c >= n0) {
+      v = SB1[(int64_t)(j - k0) * n1 + (c - n0)];
+    }
+    SBf[idx] = (float)(v * ib);
+  }
+  __syncthreads();
+  int guard = 0;
+  int k = trunc_fact32(m, n, l, SAf, SBf, S, fs, ds, e.eps, t.cap, loc(e, t.e), t.lde, loc(e, t.f), t.ldf, e.status,
+                       s, f, ok, &guard, seed, r0);
+  if (*ok && !cta_finite(loc(e, t.e), t.lde, m, k, loc(e, t.f), t.ldf, n)) {
+    *ok = 0;
+    record_bad(e, 11, m, n, l, k, S);
+  }
+  return k;
+}
+
 __device__ void task_rkadd(const ExecEnv& e, const HTask& t, Smem& s, long long ti) {
   int m = t.m, n = t.n;
   bool aid = t.flags & F_A_IDENT, bid = t.flags & F_B_IDENT, btr = t.flags & F_B_TRANS;
@@ -388,6 +433,24 @@ __device__ void task_rkadd(const ExecEnv& e, const HTask& t, Smem& s, long long 
       ok = 0;
       record_bad(e, 1, m, n, l, k, mx);
     }
+    if (ok) {
+      if (threadIdx.x == 0) {
+        if (t.rout >= 0) e.ranks[t.rout] = k;
+        atomicAdd(e.counters, 1ull);
+        atomicAdd(e.counters + 1, 1ull);
+        atomicAdd(e.flops, f);
+      }
+      count_sketch(e, s, ti, l, 1, k);
+      return;
+    }
+    if (threadIdx.x == 0) atomicAdd(e.counters + 2, 1ull);
+    count_sketch(e, s, ti, l, 0, 0);
+  } else if (e.mixed && e.eps >= HM_F32_MIN_EPS && l >= e.rand_min_l && !aid && !bid) {
+    // factored M: FP32 steps of Fig. rkadd with a randomised core
+    int r0 = sketch_width(e, ti, kin, l, s);
+    uint64_t seed = e.seed ^ ((uint64_t)blockIdx.x << 40) ^ (uint64_t)(t.rout + 3) * 0x9E3779B97F4A7C15ull;
+    int ok = 0;
+    int k = task_fact32(e, t, s, m, n, l, SA, SB, n, l, nullptr, 0, 0, Jg + 2 * (int64_t)l * l, seed, r0, &f, &ok);
     if (ok) {
       if (threadIdx.x == 0) {
         if (t.rout >= 0) e.ranks[t.rout] = k;
@@ -532,6 +595,24 @@ __device__ void task_rowmerge(const ExecEnv& e, const HTask& t, Smem& s, long lo
       ok = 0;
       record_bad(e, 2, m, n, l, k, mx);
     }
+    if (ok) {
+      if (threadIdx.x == 0) {
+        if (t.rout >= 0) e.ranks[t.rout] = k;
+        atomicAdd(e.counters, 1ull);
+        atomicAdd(e.counters + 1, 1ull);
+        atomicAdd(e.flops, f);
+      }
+      count_sketch(e, s, ti, l, 1, k);
+      return;
+    }
+    if (threadIdx.x == 0) atomicAdd(e.counters + 2, 1ull);
+    count_sketch(e, s, ti, l, 0, 0);
+  } else if (e.mixed && e.eps >= HM_F32_MIN_EPS && l >= e.rand_min_l) {
+    // [A_0 A_1] blockdiag(B_0, B_1)^T: FP32 steps of Fig. rkadd, randomised core
+    int r0 = sketch_width(e, ti, k0 > k1 ? k0 : k1, l, s);
+    uint64_t seed = e.seed ^ ((uint64_t)blockIdx.x << 40) ^ (uint64_t)(t.rout + 5) * 0x9E3779B97F4A7C15ull;
+    int ok = 0;
+    int k = task_fact32(e, t, s, m, n, l, SA0, SB0, n0, k0, SB1, n1, k1, Jg + 2 * (int64_t)l * l, seed, r0, &f, &ok);
     if (ok) {
       if (threadIdx.x == 0) {
         if (t.rout >= 0) e.ranks[t.rout] = k;
