@@ -1184,7 +1184,90 @@ static __device__ int trunc_rand(const RandIn& in, double eps, int cap, double* 
 // when fw is global and they fit there; Om: n words; the core's W, Vrot
 // (2 r^2 floats and 2 r words) sit at s.jac + HM_F32_SMEM / 2.
 // ---------------------------------------------------------------------------
-#define HM_F32_SMEM 14336  // floats of s.jac the FP32 work space may use
+#define HM_G32_MB 64
+#define HM_G32_NB 64
+#define HM_G32_KB 32
+#define HM_G32_LD 65  // padded row of a staged tile (odd: no bank conflicts either way)
+#define HM_G32_SMEM (2 * HM_G32_KB * HM_G32_LD)  // floats of staging
+
+// C (m x n, ldc) (+)= alpha op(A) op(B) as cta_gemm, with 64 x 64 output
+// tiles, 32-deep FP32 operand tiles in sm (HM_G32_SMEM floats) and a 4 x 4
+// register block per thread; C may be FP64 (global) or FP32 (shared).  The
+// staging loops run along whichever index is contiguous in memory.
+template <class TC, class TA, class TB>
+static __device__ void cta_gemm32(TC* C, int ldc, int m, int n, int kk, double alpha, const TA* A, int lda, bool ta,
+                                  const TB* B, int ldb, bool tb, bool zero, float* sm) {
+  int tid = threadIdx.x, ti = tid & 15, tj = tid >> 4;
+  float* As = sm;                          // KB rows of MB (ld HM_G32_LD)
+  float* Bs = sm + HM_G32_KB * HM_G32_LD;  // KB rows of NB (ld HM_G32_LD)
+  for (int i0 = 0; i0 < m; i0 += HM_G32_MB) {
+    for (int j0 = 0; j0 < n; j0 += HM_G32_NB) {
+      float acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+      for (int k0 = 0; k0 < kk; k0 += HM_G32_KB) {
+        __syncthreads();
+        for (int idx = tid; idx < HM_G32_KB * HM_G32_MB; idx += HM_THREADS) {
+          // op(A)(i, l): A[l lda + i] (contiguous in i) or A[i lda + l] (in l)
+          int r = ta ? idx / HM_G32_KB : idx % HM_G32_MB, q = ta ? idx % HM_G32_KB : idx / HM_G32_MB;
+          int i = i0 + r, l = k0 + q;
+          float v = 0.f;
+          if (i < m && l < kk) v = (float)(ta ? A[(int64_t)i * lda + l] : A[(int64_t)l * lda + i]);
+          As[q * HM_G32_LD + r] = v;
+        }
+        for (int idx = tid; idx < HM_G32_KB * HM_G32_NB; idx += HM_THREADS) {
+          // op(B)(l, j): B[l ldb + j] (contiguous in j) or B[j ldb + l] (in l)
+          int c = tb ? idx % HM_G32_NB : idx / HM_G32_KB, q = tb ? idx / HM_G32_NB : idx % HM_G32_KB;
+          int j = j0 + c, l = k0 + q;
+          float v = 0.f;
+          if (j < n && l < kk) v = (float)(tb ? B[(int64_t)l * ldb + j] : B[(int64_t)j * ldb + l]);
+          Bs[q * HM_G32_LD + c] = v;
+        }
+        __syncthreads();
+        int kmax = kk - k0 < HM_G32_KB ? kk - k0 : HM_G32_KB;
+        for (int q = 0; q < kmax; ++q) {
+          float av[4], bv[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) av[a] = As[q * HM_G32_LD + ti * 4 + a];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) bv[b] = Bs[q * HM_G32_LD + tj * 4 + b];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        int i = i0 + ti * 4 + a;
+        if (i >= m) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          int j = j0 + tj * 4 + b;
+          if (j >= n) continue;
+          TC* c = C + (int64_t)j * ldc + i;
+          if constexpr (sizeof(TC) == sizeof(float)) {
+            float v = (float)alpha * acc[a][b];
+            *c = zero ? v : *c + v;
+          } else {
+            double v = alpha * (double)acc[a][b];
+            *c = zero ? v : *c + v;
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+#define HM_F32_SMEM 12160  // floats of s.jac the FP32 work space may use
+// after it: the core's W, Vrot, norms, permutation (2 RMAX^2 + 2 RMAX floats),
+// then the staging of cta_gemm32 (HM_G32_SMEM floats), up to the end of s.jac
+#define HM_F32_STAGE (HM_F32_SMEM + 2 * HM_RMAX * HM_RMAX + 2 * HM_RMAX)
+static_assert(HM_F32_STAGE + HM_G32_SMEM <= 2 * HM_JAC_SMEM, "FP32 scratch exceeds s.jac");
+
 #define HM_F32_MAX_MN (1 << 20)  // largest m n truncated through the FP32 path
 
 static __device__ int trunc_rand32(const float* M, int m, int n, double scale, float* fw, uint32_t* Om, double eps,
@@ -1234,15 +1317,8 @@ static __device__ int trunc_rand32(const float* M, int m, int n, double scale, f
     __syncthreads();
     cta_qr_f(Y, m, m, r, s.tauA, s.rdiagA);
     form_q_f(Y, m, m, r, s.tauA, Qf, m);
-    for (int idx = tid; idx < n * r; idx += HM_THREADS) {
-      int c = idx % n, j = idx / n;
-      float a = 0.f;
-      const float* mc = M + (int64_t)c * m;
-      const float* qj = Qf + (int64_t)j * m;
-      for (int i = 0; i < m; ++i) a += mc[i] * qj[i];
-      J[(int64_t)j * n + c] = a;
-    }
-    __syncthreads();
+    // J = M^T Q (tiled FP32 product)
+    cta_gemm32(J, n, n, r, m, 1.0, M, m, true, Qf, m, false, true, (float*)s.jac + HM_F32_STAGE);
     float racc = 0.f;
     for (int64_t idx = tid; idx < (int64_t)m * n; idx += HM_THREADS) {
       int i = (int)(idx % m), c = (int)(idx / m);
@@ -1412,19 +1488,20 @@ static __device__ void cta_lu(double* A, int ld, int n, int* status) {
 // Thin solves with a dense diagonal leaf N (n x n, ld): X (n x w, ldx).
 // One warp per right-hand-side column: columns are independent, so the
 // substitution needs only warp-level synchronisation.
-static __device__ void cta_trsm_cols(int kind, const double* N, int ld, int n, double* X, int ldx, int w) {
+template <class T>
+static __device__ void cta_trsm_cols_t(int kind, const T* N, int ld, int n, T* X, int ldx, int w) {
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int c = warp; c < w; c += HM_WARPS) {
-    double* x = X + (int64_t)c * ldx;
+    T* x = X + (int64_t)c * ldx;
     if (kind == TRSM_L) {
       for (int k = 0; k < n - 1; ++k) {
-        double xk = x[k];
+        T xk = x[k];
         for (int i = k + 1 + lane; i < n; i += 32) x[i] -= N[(int64_t)k * ld + i] * xk;
         __syncwarp();
       }
     } else if (kind == TRSM_U) {
       for (int k = n - 1; k >= 0; --k) {
-        double xk = x[k] / N[(int64_t)k * ld + k];
+        T xk = x[k] / N[(int64_t)k * ld + k];
         __syncwarp();
         if (lane == 0) x[k] = xk;
         for (int i = lane; i < k; i += 32) x[i] -= N[(int64_t)k * ld + i] * xk;
@@ -1432,7 +1509,7 @@ static __device__ void cta_trsm_cols(int kind, const double* N, int ld, int n, d
       }
     } else if (kind == TRSM_UT) {
       for (int k = 0; k < n; ++k) {
-        double xk = x[k] / N[(int64_t)k * ld + k];
+        T xk = x[k] / N[(int64_t)k * ld + k];
         __syncwarp();
         if (lane == 0) x[k] = xk;
         for (int i = k + 1 + lane; i < n; i += 32) x[i] -= N[(int64_t)i * ld + k] * xk;
@@ -1440,13 +1517,16 @@ static __device__ void cta_trsm_cols(int kind, const double* N, int ld, int n, d
       }
     } else {
       for (int k = n - 1; k > 0; --k) {
-        double xk = x[k];
+        T xk = x[k];
         for (int i = lane; i < k; i += 32) x[i] -= N[(int64_t)i * ld + k] * xk;
         __syncwarp();
       }
     }
   }
   __syncthreads();
+}
+static __device__ void cta_trsm_cols(int kind, const double* N, int ld, int n, double* X, int ldx, int w) {
+  cta_trsm_cols_t<double>(kind, N, ld, n, X, ldx, w);
 }
 
 // Thin triangular solve: the triangle and the right-hand sides are staged in
@@ -1483,6 +1563,26 @@ static __device__ void cta_gemm(double* C, int ldc, int m, int n, int kk, double
     double* c = C + (int64_t)j * ldc + i;
     *c = zero ? alpha * acc : *c + alpha * acc;
   }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 leaf operations of the mixed path (eps >= HM_F32_MIN_EPS): operands
+// are staged once as FP32 in shared memory, products and sums run in FP32,
+// results are stored back in FP64.
+// ---------------------------------------------------------------------------
+// cta_trsm in FP32; returns false (nothing done) if N and X do not fit.
+static __device__ bool cta_trsm_f32(int kind, const double* N, int ld, int n, double* X, int ldx, int w, Smem& s) {
+  if (w <= 0) return true;
+  if ((int64_t)n * n + (int64_t)n * w > 2 * HM_JAC_SMEM) return false;
+  float* Ns = (float*)s.jac;
+  float* Xs = Ns + (int64_t)n * n;
+  for (int idx = threadIdx.x; idx < n * n; idx += HM_THREADS) Ns[idx] = (float)N[(int64_t)(idx / n) * ld + idx % n];
+  for (int idx = threadIdx.x; idx < n * w; idx += HM_THREADS) Xs[idx] = (float)X[(int64_t)(idx / n) * ldx + idx % n];
+  __syncthreads();
+  cta_trsm_cols_t<float>(kind, Ns, n, n, Xs, n, w);
+  for (int idx = threadIdx.x; idx < n * w; idx += HM_THREADS) X[(int64_t)(idx / n) * ldx + idx % n] = (double)Xs[idx];
+  __syncthreads();
+  return true;
 }
 
 }  // namespace hm

@@ -233,7 +233,7 @@ __device__ void note_exact(const ExecEnv& e, long long ti, int l, int k) {
 // ---------------------------------------------------------------------------
 // Task bodies
 // ---------------------------------------------------------------------------
-__device__ void task_hmv(const ExecEnv& e, const HTask& t, Smem& s) {
+__device__ void task_hmv(const ExecEnv& e, const HTask& t, Smem& s, bool f32) {
   bool trans = t.flags & F_TRANS;
   int w = width_of(e, t.wa);
   double* out = loc(e, t.c);
@@ -252,8 +252,30 @@ __device__ void task_hmv(const ExecEnv& e, const HTask& t, Smem& s) {
     int irows = trans ? L.rows : L.cols;
     if (L.kind == 1) {
       const double* N = loc(e, L.a);
-      cta_gemm(out + orow, t.ldc, orows, w, irows, t.alpha, N, L.lda, trans, in + irow, t.ldb, false, false);
-      __syncthreads();
+      if (f32) {
+        cta_gemm32(out + orow, t.ldc, orows, w, irows, t.alpha, N, L.lda, trans, in + irow, t.ldb, false, false,
+                   (float*)s.jac);
+      } else {
+        cta_gemm(out + orow, t.ldc, orows, w, irows, t.alpha, N, L.lda, trans, in + irow, t.ldb, false, false);
+        __syncthreads();
+      }
+    } else if (f32) {
+      int k = e.ranks[L.rank_slot];
+      if (k <= 0) continue;
+      const double* Fin = loc(e, trans ? L.a : L.b);
+      const double* Fout = loc(e, trans ? L.b : L.a);
+      int ldin = trans ? L.lda : L.ldb;
+      int ldout = trans ? L.ldb : L.lda;
+      float* zf = (float*)s.jac + HM_G32_SMEM;  // Zhat (k x wc) in FP32
+      int wc = (2 * HM_JAC_SMEM - HM_G32_SMEM) / k;
+      if (wc > w) wc = w;
+      for (int c0 = 0; c0 < w; c0 += wc) {
+        int cw = w - c0 < wc ? w - c0 : wc;
+        cta_gemm32(zf, k, k, cw, irows, t.alpha, Fin, ldin, true, in + irow + (int64_t)c0 * t.ldb, t.ldb, false,
+                   true, (float*)s.jac);
+        cta_gemm32(out + orow + (int64_t)c0 * t.ldc, t.ldc, orows, cw, k, 1.0, Fout, ldout, false, zf, k, false,
+                   false, (float*)s.jac);
+      }
     } else {
       int k = e.ranks[L.rank_slot];
       if (k <= 0) continue;
@@ -737,6 +759,8 @@ __device__ double task_flops(const ExecEnv& e, const HTask& t) {
 }
 
 __device__ void run_task(const ExecEnv& e, const HTask& t, Smem& s, long long ti) {
+  // FP32 leaf products and solves in the mixed path (eps >= HM_F32_MIN_EPS)
+  bool f32 = e.mixed && e.eps >= HM_F32_MIN_EPS;
   switch (t.type) {
     case T_NOP:
       break;
@@ -744,10 +768,11 @@ __device__ void run_task(const ExecEnv& e, const HTask& t, Smem& s, long long ti
       cta_lu(loc(e, t.a), t.lda, t.m, e.status);
       break;
     case T_TRSM:
-      cta_trsm(t.p, loc(e, t.a), t.lda, t.m, loc(e, t.b), t.ldb, width_of(e, t.wa), s);
+      if (!(f32 && cta_trsm_f32(t.p, loc(e, t.a), t.lda, t.m, loc(e, t.b), t.ldb, width_of(e, t.wa), s)))
+        cta_trsm(t.p, loc(e, t.a), t.lda, t.m, loc(e, t.b), t.ldb, width_of(e, t.wa), s);
       break;
     case T_HMV:
-      task_hmv(e, t, s);
+      task_hmv(e, t, s, f32);
       break;
     case T_DENSIFY:
       task_densify(e, t, s);
@@ -755,7 +780,10 @@ __device__ void run_task(const ExecEnv& e, const HTask& t, Smem& s, long long ti
     case T_GEMM: {
       int w = width_of(e, t.wa);
       bool zero = t.flags & F_ZERO_OUT;
-      if (w > 0 || zero)
+      if (f32 && (w > 0 || zero))
+        cta_gemm32(loc(e, t.c), t.ldc, t.m, t.n, w, t.alpha, loc(e, t.a), t.lda, false, loc(e, t.b), t.ldb,
+                   !(t.flags & F_B_TRANS), zero, (float*)s.jac);
+      else if (w > 0 || zero)
         cta_gemm(loc(e, t.c), t.ldc, t.m, t.n, w, t.alpha, loc(e, t.a), t.lda, false, loc(e, t.b), t.ldb,
                  !(t.flags & F_B_TRANS), zero);
       break;
