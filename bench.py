@@ -36,9 +36,12 @@ UNIT = "truncations/s"
 TASK_NAMES = ["NOP", "LU", "TRSM", "HMV", "DENSIFY", "GEMM", "ADD", "RKADD", "ROWMERGE", "COPY", "ZERO", "RANKSET"]
 FP64_PEAK_TFLOPS = 1.25     # GB300 nominal FP64 (vector and tensor) rate, 152 SMs at up to 2070 MHz
 WORKLOADS = {"laplace3d_32": hs.laplace3d_32, "laplace3d_64": hs.laplace3d_64, "laplace2d_64": hs.laplace2d_64,
-             "diffusion2d_batch64": hs.diffusion2d_batch}
+             "diffusion2d_batch64": hs.diffusion2d_batch,
+             # small case of the 3D recipe for profiling captures
+             "laplace3d_16": lambda: hs.small_laplace(16, 3, 64, 1e-4)}
 # bounded oracle sample: the same operator family, tolerance and leaf size at 16^3
 SAMPLE = {"laplace3d_32": lambda: hs.small_laplace(16, 3, 64, 1e-4),
+          "laplace3d_16": lambda: hs.small_laplace(16, 3, 64, 1e-4),
           "laplace3d_64": lambda: hs.small_laplace(16, 3, 64, 1e-4),
           "laplace2d_64": hs.laplace2d_64,
           "diffusion2d_batch64": lambda: hs.diffusion2d_batch()[0]}

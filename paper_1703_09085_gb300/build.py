@@ -1,7 +1,7 @@
 """Build libhmat.so in place: the CUDA kernels and the host library for sm_103a.
 
-Two translation units, compiled in parallel by nvcc and linked into one shared
-library next to this file.  No cmake, no torch extension machinery.
+The translation units are compiled in parallel by nvcc and linked into one
+shared library next to this file.  No cmake, no torch extension machinery.
 """
 from __future__ import annotations
 

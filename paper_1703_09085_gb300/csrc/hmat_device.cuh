@@ -677,6 +677,9 @@ static __device__ int trunc_core(const TruncIn& in, double eps, int cap, double*
 // QR + SVD path.  C = Q Vr(:, order), D = J(:, order) as in Fig. rkadd.
 // ---------------------------------------------------------------------------
 #define HM_RMAX 32
+#ifndef HM_CORE_SWEEPS
+#define HM_CORE_SWEEPS 2  // Jacobi sweeps on the pivoted R^T of the FP32 core
+#endif
 #define HM_F32_MIN_EPS 1e-5  // FP32 rounding (~1e-7) stays well below eps from here on
 
 struct RandIn {
@@ -1084,7 +1087,7 @@ static __device__ int trunc_rand(const RandIn& in, double eps, int cap, double* 
         Jf[idx] = (float)x;
       }
       jn2 = block_sum(a2, s);
-      core_f32(Jf, n, rr, cw, s, 4);
+      core_f32(Jf, n, rr, cw, s, HM_CORE_SWEEPS);
       form_q_f(Jf, n, n, rr, s.tauB, Qj, n);
       f += 2.0 * n * rr;
     } else {
@@ -1340,7 +1343,7 @@ static __device__ int trunc_rand32(const float* M, int m, int n, double scale, f
     for (int idx = tid; idx < n * r; idx += HM_THREADS) Jq[idx] = J[idx];
     __syncthreads();
     float* cw = (float*)(s.jac + HM_F32_SMEM / 2);  // 2 r^2 + 2 r floats
-    core_f32(Jq, n, r, cw, s, 4);
+    core_f32(Jq, n, r, cw, s, HM_CORE_SWEEPS);
     form_q_f(Jq, n, n, r, s.tauB, J, n);
     if (tid == 0) {
       double tail = res2;

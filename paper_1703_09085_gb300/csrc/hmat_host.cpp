@@ -1560,7 +1560,13 @@ RunResult launch_sched(hmat_ctx* ctx, const Sched& S, DevSched& D, double* hbase
   e.seed = 0x5EEDull;
   e.spin_iters = spin_limit > 0 ? spin_limit : (1ll << 28);
   e.spin_ns = 20ull * 1000000000ull;
-  int grid = ctx->num_sms * ctx->blocks_per_sm;
+  // One CTA per SM when the schedule's average parallelism (estimated work
+  // over its critical path) cannot keep two per SM busy: co-resident CTAs
+  // then only slow the critical path down (they share the SM's pipes).
+  int bps = ctx->blocks_per_sm;
+  double cp = S.critical_flops();
+  if (bps > 1 && cp > 0.0 && S.est_total < 2.0 * ctx->num_sms * cp) bps = 1;
+  int grid = ctx->num_sms * bps;
   cudaEvent_t e0, e1;
   HM_CUDA(cudaEventCreate(&e0));
   HM_CUDA(cudaEventCreate(&e1));
