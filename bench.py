@@ -35,6 +35,7 @@ METRIC = "H-LU setup truncations/s (accumulated updates) vs plain FP64 at equal 
 UNIT = "truncations/s"
 TASK_NAMES = ["NOP", "LU", "TRSM", "HMV", "DENSIFY", "GEMM", "ADD", "RKADD", "ROWMERGE", "COPY", "ZERO", "RANKSET"]
 FP64_PEAK_TFLOPS = 1.25     # GB300 nominal FP64 (vector and tensor) rate, 152 SMs at up to 2070 MHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 CUDA-core FMA rate: 152 SMs x 128 lanes x 2 x 2070 MHz
 WORKLOADS = {"laplace3d_32": hs.laplace3d_32, "laplace3d_64": hs.laplace3d_64, "laplace2d_64": hs.laplace2d_64,
              "diffusion2d_batch64": hs.diffusion2d_batch,
              # small case of the 3D recipe for profiling captures
@@ -139,6 +140,27 @@ def job_throughput(units: float, seconds: float, world: int, device=None):
     return units / seconds, seconds
 
 
+# DRAM bytes (read + write) of one exec_tasks launch, from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of the source tree whose
+# csrc hash is given; see profiles/launches_laplace3d_32.md.
+TRAFFIC = {}
+
+
+def csrc_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1703_09085_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(workload: str):
+    rec = TRAFFIC.get(workload)
+    return rec["bytes"] if rec and rec["csrc"] == csrc_hash() else None
+
+
 def workload_config(args, probs, world: int) -> dict:
     """The config object of both arms' JSON lines."""
     par = (f"instances sharded: {world} rank(s) x 64 own instances" if args.workload == "diffusion2d_batch64"
@@ -220,7 +242,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    step_ms, kern_ms, flops, truncs, tasks, sched = [], [], [], [], [], []
+    step_ms, kern_ms, flops, flops32, truncs, tasks, sched = [], [], [], [], [], [], []
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     for _ in range(args.steps):
@@ -233,6 +255,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         st = work[0].stats()  # batch totals
         kern_ms.append(1e3 * st["factor_seconds"])
         flops.append(st["flops"])
+        flops32.append(st["flops32"])
         truncs.append(st["truncations"])
         tasks.append(st["tasks"])
         sched.append(st["schedule_seconds"])
@@ -285,6 +308,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     peaks = measured_peaks()
     avg_kern_s = statistics.mean(kern_ms) / 1e3
     achieved = statistics.mean(flops) / avg_kern_s / 1e12
+    achieved32 = statistics.mean(flops32) / avg_kern_s / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -304,11 +328,16 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         "critical_path_tasks": st["levels"],
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic_per_launch(args.workload),
                      "kernel": "exec_tasks", "kernel_ms": statistics.mean(kern_ms),
                      "flops_per_launch": statistics.mean(flops),
-                     "peak_note": "FP64 nominal (no measured FP64 peak in MEASURED_PEAKS.json); "
-                                  "counts FP64 operations only"},
+                     "fp32": {"achieved": achieved32, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                              "frac": achieved32 / FP32_PEAK_TFLOPS, "flops_per_launch": statistics.mean(flops32)},
+                     "peak_note": "nominal FP64 (1.25 TFLOP/s) and FP32 (152 SMs x 128 lanes x 2 x 2070 MHz) "
+                                  "rates: the measured peaks file has no FP64 or FP32 vector figure; FP64 and "
+                                  "FP32 operations are counted on the device separately",
+                     "traffic_note": "DRAM read + write bytes of one launch from an ncu capture of this source "
+                                     "tree (profiles/); null when the kernel source changed since"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": 1e3 * e2e_s / args.steps},
         "clocks": clk,

@@ -115,6 +115,7 @@ typedef struct {
   double cp_seconds;
   double cp_type_seconds[16];
   int64_t cp_type_count[16];
+  double flops32;           /* FP32 operations of the mixed path (flops: FP64)    */
 } hmat_stats;
 
 /* Message of the last failure on this thread, copied into buf (NUL-terminated,

@@ -47,6 +47,11 @@ static __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+// FP32 operations of the running task: counted by thread 0 into s.bcast[7],
+// collected by the executor after the task.
+static __device__ __forceinline__ void count_f32(Smem& s, double f) {
+  if (threadIdx.x == 0) s.bcast[7] += f;
+}
 static __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -1089,6 +1094,7 @@ static __device__ int trunc_rand(const RandIn& in, double eps, int cap, double* 
       jn2 = block_sum(a2, s);
       core_f32(Jf, n, rr, cw, s, HM_CORE_SWEEPS);
       form_q_f(Jf, n, n, rr, s.tauB, Qj, n);
+      count_f32(s, 4.0 * n * rr * rr + 12.0 * rr * (double)s.ivals[3]);
       f += 2.0 * n * rr;
     } else {
       cta_jacobi(J, n, rr, Vr, s, 1e-10);
@@ -1322,6 +1328,8 @@ static __device__ int trunc_rand32(const float* M, int m, int n, double scale, f
     form_q_f(Y, m, m, r, s.tauA, Qf, m);
     // J = M^T Q (tiled FP32 product)
     cta_gemm32(J, n, n, r, m, 1.0, M, m, true, Qf, m, false, true, (float*)s.jac + HM_F32_STAGE);
+    // sketch, QR and Q of the sketch, J, residual
+    count_f32(s, (double)m * n * r + 4.0 * m * r * r + 4.0 * (double)m * n * r);
     float racc = 0.f;
     for (int64_t idx = tid; idx < (int64_t)m * n; idx += HM_THREADS) {
       int i = (int)(idx % m), c = (int)(idx / m);
@@ -1345,6 +1353,8 @@ static __device__ int trunc_rand32(const float* M, int m, int n, double scale, f
     float* cw = (float*)(s.jac + HM_F32_SMEM / 2);  // 2 r^2 + 2 r floats
     core_f32(Jq, n, r, cw, s, HM_CORE_SWEEPS);
     form_q_f(Jq, n, n, r, s.tauB, J, n);
+    // pivoted QR, Q_J, rotations (12 r per rotation: dots and updates)
+    count_f32(s, 4.0 * n * r * r + 12.0 * r * (double)s.ivals[3]);
     if (tid == 0) {
       double tail = res2;
       int k = r;
@@ -1370,6 +1380,7 @@ static __device__ int trunc_rand32(const float* M, int m, int n, double scale, f
       // M ~ (Q P W_k)(Q_J Vrot_k)^T = (Q P Wh)(Q_J Z)^T: C = Q P Wh, D = Q_J Z
       // (Y and Jq are free: the sketch's and J's reflectors have been used)
       core_f32_orth(cw, r, k, Y, Jq, s);
+      count_f32(s, 4.0 * r * k * k + 2.0 * (m + n) * (double)r * k);
       const float* Wh = Jq;
       const float* Z = cw;
       const int* perm = (const int*)(cw + 2 * r * r + r);
@@ -1419,6 +1430,7 @@ static __device__ int trunc_fact32(int m, int n, int l, const float* SAf, float*
   double* rq = ds + l;
   double* Vh = ds + 2 * l;  // l x k (ld l)
   cta_qr_f(SBf, n, n, l, tq, rq);
+  count_f32(s, 2.0 * n * l * l + (double)m * l * l);  // QR of SB, Mhat
   float sm = 0.f, sabs = 0.f;
   for (int idx = tid; idx < m * l; idx += HM_THREADS) {
     int i = idx % m, c = idx / m;
@@ -1441,6 +1453,7 @@ static __device__ int trunc_fact32(int m, int n, int l, const float* SAf, float*
   int k = trunc_rand32(Mh, m, l, S, pan, Om, eps, cap, U, ldu, Vh, l, status, s, flops, ok, seed, r0);
   if (!*ok) return 0;
   form_q_f(SBf, n, n, l, tq, QB, n);
+  count_f32(s, 2.0 * n * l * l + 2.0 * n * (double)l * k);  // Q_B, D = Q_B Dhat
   for (int idx = tid; idx < n * k; idx += HM_THREADS) {
     int c = idx % n, jj = idx / n;
     float a = 0.f;
@@ -1583,6 +1596,7 @@ static __device__ bool cta_trsm_f32(int kind, const double* N, int ld, int n, do
   for (int idx = threadIdx.x; idx < n * w; idx += HM_THREADS) Xs[idx] = (float)X[(int64_t)(idx / n) * ldx + idx % n];
   __syncthreads();
   cta_trsm_cols_t<float>(kind, Ns, n, n, Xs, n, w);
+  count_f32(s, (double)n * n * w);
   for (int idx = threadIdx.x; idx < n * w; idx += HM_THREADS) X[(int64_t)(idx / n) * ldx + idx % n] = (double)Xs[idx];
   __syncthreads();
   return true;

@@ -1426,6 +1426,7 @@ struct RunResult {
   double ms = 0.0;
   unsigned long long truncations = 0;
   double flops = 0.0;
+  double flops32 = 0.0;
   unsigned long long type_ns[16] = {0}, type_cnt[16] = {0}, wait_ns = 0;
   unsigned long long rand_ok = 0, rand_fail = 0, sketch_attempts = 0, sketch_cols = 0;
   unsigned long long bad[6] = {0, 0, 0, 0, 0, 0};
@@ -1532,6 +1533,7 @@ RunResult launch_sched(hmat_ctx* ctx, const Sched& S, DevSched& D, double* hbase
   e.counters = (unsigned long long*)dmp + 44;
   e.status = (int*)((unsigned long long*)dmp + 2);
   e.flops = (double*)((unsigned long long*)dmp + 3);
+  e.flops32 = (double*)((unsigned long long*)dmp + 4);
   e.type_ns = (unsigned long long*)dmp + 8;
   e.type_cnt = (unsigned long long*)dmp + 24;
   e.wait_ns = (unsigned long long*)dmp + 40;
@@ -1606,6 +1608,7 @@ RunResult launch_sched(hmat_ctx* ctx, const Sched& S, DevSched& D, double* hbase
   }
   rr.status = (int)(misc[2] & 0xffffffffu);
   std::memcpy(&rr.flops, &misc[3], sizeof(double));
+  std::memcpy(&rr.flops32, &misc[4], sizeof(double));
   return rr;
 }
 
@@ -2120,6 +2123,8 @@ void lu_batch(hmat_ctx* ctx, hmat* const* Hs, int count, const hmat_opts* opts) 
     st.tasks = (int64_t)S.tasks.size();
     st.truncations = (int64_t)rr.truncations;
     st.flops = rr.flops;
+  st.flops32 = rr.flops32;
+    st.flops32 = rr.flops32;
     st.rand_truncations = (int64_t)rr.rand_ok;
     st.rand_fallbacks = (int64_t)rr.rand_fail;
     st.sketch_attempts = (int64_t)rr.sketch_attempts;
@@ -2203,6 +2208,7 @@ void addmul_run(hmat_ctx* ctx, double alpha, const hmat* X, const hmat* Y, hmat*
   st.tasks = (int64_t)S.tasks.size();
   st.truncations = (int64_t)rr.truncations;
   st.flops = rr.flops;
+  st.flops32 = rr.flops32;
   st.rand_truncations = (int64_t)rr.rand_ok;
   st.rand_fallbacks = (int64_t)rr.rand_fail;
   st.sketch_attempts = (int64_t)rr.sketch_attempts;

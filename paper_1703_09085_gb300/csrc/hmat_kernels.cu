@@ -162,6 +162,11 @@ __device__ int form_m32(int m, int ncol, const M32Part* P, int np, bool has_base
     sabs += a * a;
   }
   double tm = block_sum((double)sm, s), ta = block_sum((double)sabs, s);
+  {
+    double f = 0.0;
+    for (int q = 0; q < np; ++q) f += 2.0 * m * (double)P[q].n * P[q].k;
+    count_f32(s, f);
+  }
   if (!isfinite(tm) || !isfinite(ta)) return 1;
   // FP32 rounding of the sums stays below ~3e-7 ||terms||_F (terms: the
   // entrywise sums of magnitudes); keep it under eps ||M||_F / 10
@@ -255,6 +260,7 @@ __device__ void task_hmv(const ExecEnv& e, const HTask& t, Smem& s, bool f32) {
       if (f32) {
         cta_gemm32(out + orow, t.ldc, orows, w, irows, t.alpha, N, L.lda, trans, in + irow, t.ldb, false, false,
                    (float*)s.jac);
+        count_f32(s, 2.0 * orows * (double)irows * w);
       } else {
         cta_gemm(out + orow, t.ldc, orows, w, irows, t.alpha, N, L.lda, trans, in + irow, t.ldb, false, false);
         __syncthreads();
@@ -275,6 +281,7 @@ __device__ void task_hmv(const ExecEnv& e, const HTask& t, Smem& s, bool f32) {
                    true, (float*)s.jac);
         cta_gemm32(out + orow + (int64_t)c0 * t.ldc, t.ldc, orows, cw, k, 1.0, Fout, ldout, false, zf, k, false,
                    false, (float*)s.jac);
+        count_f32(s, 2.0 * (double)k * cw * (irows + orows));
       }
     } else {
       int k = e.ranks[L.rank_slot];
@@ -780,9 +787,11 @@ __device__ void run_task(const ExecEnv& e, const HTask& t, Smem& s, long long ti
     case T_GEMM: {
       int w = width_of(e, t.wa);
       bool zero = t.flags & F_ZERO_OUT;
-      if (f32 && (w > 0 || zero))
+      if (f32 && (w > 0 || zero)) {
         cta_gemm32(loc(e, t.c), t.ldc, t.m, t.n, w, t.alpha, loc(e, t.a), t.lda, false, loc(e, t.b), t.ldb,
                    !(t.flags & F_B_TRANS), zero, (float*)s.jac);
+        count_f32(s, 2.0 * t.m * (double)t.n * w);
+      }
       else if (w > 0 || zero)
         cta_gemm(loc(e, t.c), t.ldc, t.m, t.n, w, t.alpha, loc(e, t.a), t.lda, false, loc(e, t.b), t.ldb,
                  !(t.flags & F_B_TRANS), zero);
@@ -858,12 +867,14 @@ __global__ void __launch_bounds__(HM_THREADS) exec_tasks(ExecEnv e) {
     if (t >= e.ntasks) break;
     if (!skip) {
       HTask task = e.tasks[t];
+      if (threadIdx.x == 0) s.bcast[7] = 0.0;
       if (threadIdx.x == 0 && task.type != T_RKADD && task.type != T_ROWMERGE) {
         double f = task_flops(e, task);
         if (f > 0.0) atomicAdd(e.flops, f);
       }
       run_task(e, task, s, t);
       __syncthreads();
+      if (threadIdx.x == 0 && s.bcast[7] > 0.0) atomicAdd(e.flops32, s.bcast[7]);
       if (threadIdx.x == 0 && task.type >= 0 && task.type < 16) {
         uint64_t dt = global_ns() - cur_t0;
         atomicAdd(e.type_ns + task.type, (unsigned long long)dt);

@@ -24,6 +24,7 @@ struct ExecEnv {
   int* status;                // device status word (hmat_status numbering)
   unsigned long long* counters;  // [0] truncations run, [1] randomised, [2] randomised fell back
   double* flops;              // FP64 operations counted by the tasks
+  double* flops32;            // FP32 operations counted by the tasks (mixed path)
   unsigned long long* type_ns;   // per task type: summed execution time (ns)
   unsigned long long* type_cnt;  // per task type: tasks run
   unsigned long long* wait_ns;   // summed time CTAs spent waiting on predecessors
