@@ -1405,6 +1405,9 @@ static __device__ int trunc_rand32(const float* M, int m, int n, double scale, f
   }
 }
 
+#define HM_FACT32_DIRECT 64  // largest stacked width truncated without a sketch
+static_assert(2 * HM_FACT32_DIRECT * HM_FACT32_DIRECT + 2 * HM_FACT32_DIRECT <= 2 * HM_JAC_SMEM,
+              "direct FP32 core exceeds s.jac");
 // ---------------------------------------------------------------------------
 // Mixed-precision truncation of a factored M = SA SB^T (m x n, stacked width
 // l), the steps of Fig. rkadd in FP32: SB = Q_B R_B (Householder), then
@@ -1449,6 +1452,63 @@ static __device__ int trunc_fact32(int m, int n, int l, const float* SAf, float*
   if (!isfinite(tm) || !isfinite(ta) || ta * 9e-14 > 1e-2 * eps * eps * tm) {
     *guard = 1;
     return 0;
+  }
+  if (l <= HM_FACT32_DIRECT) {
+    // Mhat has at most l <= 64 columns: its pivoted QR and a few Jacobi sweeps
+    // (core_f32) are the whole truncation, Mhat = (Q_J Vrot)(P W)^T, so
+    // C = Q_J Vrot(:, order) and D = Q_B P W(:, order) S, with no sketch
+    // (and no sketch that could miss).  s.jac is free here: the core's W,
+    // Vrot, norms and permutation sit at its start.
+    if (tid == 0) s.ivals[5] = s.ivals[6] = 0;
+    float* cw = (float*)s.jac;
+    core_f32(Mh, m, l, cw, s, HM_CORE_SWEEPS);
+    if (tid == 0) {
+      double total = 0.0;
+      for (int i = 0; i < l; ++i) total += s.sigma[i] * s.sigma[i];
+      double bound = eps * eps * total, tail = 0.0;
+      int k = l;
+      while (k > 0) {
+        double x = s.sigma[s.order[k - 1]];
+        if (tail + x * x <= bound) {
+          tail += x * x;
+          --k;
+        } else {
+          break;
+        }
+      }
+      if (k > cap) {
+        set_status(status, DS_RANK);
+        k = cap;
+      }
+      s.ivals[4] = k;
+    }
+    __syncthreads();
+    int k = s.ivals[4];
+    float* QJ = pan;  // m x l
+    form_q_f(Mh, m, m, l, s.tauB, QJ, m);
+    form_q_f(SBf, n, n, l, tq, QB, n);
+    const float* W = cw;
+    const float* Vrot = cw + l * l;
+    const int* perm = (const int*)(cw + 2 * l * l + l);
+    for (int idx = tid; idx < m * k; idx += HM_THREADS) {
+      int i = idx % m, jj = idx / m;
+      const float* vc = Vrot + (int64_t)s.order[jj] * l;
+      float a = 0.f;
+      for (int j = 0; j < l; ++j) a += QJ[(int64_t)j * m + i] * vc[j];
+      U[(int64_t)jj * ldu + i] = (double)a;
+    }
+    for (int idx = tid; idx < n * k; idx += HM_THREADS) {
+      int c = idx % n, jj = idx / n;
+      const float* wc = W + (int64_t)s.order[jj] * l;
+      float a = 0.f;
+      for (int j = 0; j < l; ++j) a += QB[(int64_t)perm[j] * n + c] * wc[j];
+      V[(int64_t)jj * ldv + c] = (double)a * S;
+    }
+    count_f32(s, 2.0 * m * l * l + 12.0 * l * (double)s.ivals[3] + 4.0 * (m + n) * (double)l * l +
+                     2.0 * (m + n) * (double)l * k);
+    __syncthreads();
+    *ok = 1;
+    return k;
   }
   int k = trunc_rand32(Mh, m, l, S, pan, Om, eps, cap, U, ldu, Vh, l, status, s, flops, ok, seed, r0);
   if (!*ok) return 0;
