@@ -904,7 +904,7 @@ static __device__ void core_f32_orth(float* cw, int r, int k, float* Wk, float* 
   __syncthreads();
 }
 
-// Small core of the FP32 randomised truncations.  J (p x r floats, ld p) is
+// Small core of the FP32 randomised truncations.  J (p x r floats, ld p, p >= r) is
 // factored in place, J P = Q_J R (cta_qrcp_f; reflectors and tau in s.tauB
 // for forming Q_J); one-sided Jacobi on R^T, at most max_sweeps sweeps (the
 // pivoted R^T has graded columns, so few sweeps come close to its SVD),
@@ -1410,7 +1410,7 @@ static_assert(2 * HM_FACT32_DIRECT * HM_FACT32_DIRECT + 2 * HM_FACT32_DIRECT <= 
               "direct FP32 core exceeds s.jac");
 // ---------------------------------------------------------------------------
 // Mixed-precision truncation of a factored M = SA SB^T (m x n, stacked width
-// l), the steps of Fig. rkadd in FP32: SB = Q_B R_B (Householder), then
+// l <= min(m, n)), the steps of Fig. rkadd in FP32: SB = Q_B R_B (Householder), then
 // Mhat = SA R_B^T (m x l) carries all of M (M = Mhat Q_B^T, Q_B orthonormal),
 // so truncating Mhat by trunc_rand32 truncates M with the same error, and
 // D = Q_B Dhat.  SAf, SBf: FP32 copies scaled so that |SAf SBf^T| <= 1
@@ -1453,8 +1453,9 @@ static __device__ int trunc_fact32(int m, int n, int l, const float* SAf, float*
     *guard = 1;
     return 0;
   }
-  if (l <= HM_FACT32_DIRECT) {
-    // Mhat has at most l <= 64 columns: its pivoted QR and a few Jacobi sweeps
+  if (l <= HM_FACT32_DIRECT && l <= m) {
+    // Mhat has at most l <= 64 columns (and at least as many rows, so that its
+    // R factor is l x l): its pivoted QR and a few Jacobi sweeps
     // (core_f32) are the whole truncation, Mhat = (Q_J Vrot)(P W)^T, so
     // C = Q_J Vrot(:, order) and D = Q_B P W(:, order) S, with no sketch
     // (and no sketch that could miss).  s.jac is free here: the core's W,

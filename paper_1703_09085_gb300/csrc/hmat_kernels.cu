@@ -425,8 +425,11 @@ __device__ void task_rkadd(const ExecEnv& e, const HTask& t, Smem& s, long long 
   }
   __syncthreads();
   double f = 0.0;
-  if (e.mixed && e.eps >= HM_F32_MIN_EPS && l >= e.rand_min_l && (int64_t)m * n <= HM_F32_MAX_MN &&
-      (int64_t)m * n <= 4 * (int64_t)(m + n) * l) {
+  // FP32 factored path (QR of the second factor) when l <= min(m, n); the
+  // explicit FP32 path for the identity cases and the other small blocks
+  bool fact = !aid && !bid && l <= m && l <= n;
+  if (e.mixed && e.eps >= HM_F32_MIN_EPS && l >= e.rand_min_l && (!fact || l > HM_FACT32_DIRECT) &&
+      (int64_t)m * n <= HM_F32_MAX_MN && (int64_t)m * n <= 4 * (int64_t)(m + n) * l) {
     // Mixed precision: M formed once (FP64 sums, FP32 copy), FP32 sketch and
     // projections, FP64 core.
     int Rr = m < n ? m : n;
@@ -474,8 +477,8 @@ __device__ void task_rkadd(const ExecEnv& e, const HTask& t, Smem& s, long long 
     }
     if (threadIdx.x == 0) atomicAdd(e.counters + 2, 1ull);
     count_sketch(e, s, ti, l, 0, 0);
-  } else if (e.mixed && e.eps >= HM_F32_MIN_EPS && l >= e.rand_min_l && !aid && !bid) {
-    // factored M: FP32 steps of Fig. rkadd with a randomised core
+  } else if (e.mixed && e.eps >= HM_F32_MIN_EPS && l >= e.rand_min_l && fact) {
+    // factored M: FP32 steps of Fig. rkadd (randomised core only for l > 64)
     int r0 = sketch_width(e, ti, kin, l, s);
     uint64_t seed = e.seed ^ ((uint64_t)blockIdx.x << 40) ^ (uint64_t)(t.rout + 3) * 0x9E3779B97F4A7C15ull;
     int ok = 0;
@@ -590,8 +593,9 @@ __device__ void task_rowmerge(const ExecEnv& e, const HTask& t, Smem& s, long lo
   double f = 0.0;
   int l = k0 + k1;
   int n = n0 + n1;
-  if (e.mixed && e.eps >= HM_F32_MIN_EPS && l >= e.rand_min_l && (int64_t)m * n <= HM_F32_MAX_MN &&
-      (int64_t)m * n <= 4 * (int64_t)(m + n) * l) {
+  bool fact = l <= m && l <= n;
+  if (e.mixed && e.eps >= HM_F32_MIN_EPS && l >= e.rand_min_l && (!fact || l > HM_FACT32_DIRECT) &&
+      (int64_t)m * n <= HM_F32_MAX_MN && (int64_t)m * n <= 4 * (int64_t)(m + n) * l) {
     int Rr = m < n ? m : n;
     if (Rr > HM_RMAX) Rr = HM_RMAX;
     int64_t mn = (int64_t)m * n, fl = mn + 2 * (int64_t)(m + n) * Rr;
@@ -636,8 +640,8 @@ __device__ void task_rowmerge(const ExecEnv& e, const HTask& t, Smem& s, long lo
     }
     if (threadIdx.x == 0) atomicAdd(e.counters + 2, 1ull);
     count_sketch(e, s, ti, l, 0, 0);
-  } else if (e.mixed && e.eps >= HM_F32_MIN_EPS && l >= e.rand_min_l) {
-    // [A_0 A_1] blockdiag(B_0, B_1)^T: FP32 steps of Fig. rkadd, randomised core
+  } else if (e.mixed && e.eps >= HM_F32_MIN_EPS && l >= e.rand_min_l && fact) {
+    // [A_0 A_1] blockdiag(B_0, B_1)^T: FP32 steps of Fig. rkadd
     int r0 = sketch_width(e, ti, k0 > k1 ? k0 : k1, l, s);
     uint64_t seed = e.seed ^ ((uint64_t)blockIdx.x << 40) ^ (uint64_t)(t.rout + 5) * 0x9E3779B97F4A7C15ull;
     int ok = 0;
