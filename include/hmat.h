@@ -186,10 +186,15 @@ hmat_status hmat_addeval(hmat_ctx* ctx, const hmat* H, double alpha, int trans, 
  * Fig. invert, products added by Fig. addproduct, flushed by Fig. flush.
  * A host-side symbolic pass turns the recursion into a dependency-ordered task
  * list that one persistent kernel executes.  precision HMAT_FP64 runs every
- * task in FP64; HMAT_MIXED runs the factor products and the tall parts of the
- * truncations in FP32 and keeps FP64 for R factors, the small core SVD and the
- * leaf LU.  Returns the device status (HMAT_ERR_SINGULAR, _RANK, _TIMEOUT,
- * _NONFINITE) after synchronising the stream. */
+ * task in FP64.  HMAT_MIXED with eps >= 1e-5 runs the truncations (QR of the
+ * stacked factor, the projected block, pivoted-QR and Jacobi core, sketches
+ * where used) and the leaf products and triangular solves in FP32 and keeps
+ * FP64 for the leaf LU of the diagonal blocks, the stored factors and the
+ * sums that decide the rank rule; every result still satisfies the rule of
+ * hmat_opts.eps (a failed check falls back to the exact FP64 truncation).
+ * HMAT_MIXED with eps < 1e-5 keeps FP64 truncations with FP32 sketches only.
+ * Returns the device status (HMAT_ERR_SINGULAR, _RANK, _TIMEOUT, _NONFINITE)
+ * after synchronising the stream. */
 hmat_status hmat_lu(hmat_ctx* ctx, hmat* H, const hmat_opts* opts);
 
 /* hmat_lu of count independent H-matrices (different trees and sizes allowed,

@@ -409,9 +409,11 @@ static __device__ void cta_jacobi_f(float* J, int p, int c, float* Vr, Smem& s, 
   }
 }
 
-// Householder QR of a float panel by the whole CTA (conventions of
-// warp_qr_f): warp 0 forms each reflector, every warp applies it to its share
-// of the remaining columns.
+// Householder QR of a float panel by the whole CTA: column j becomes the
+// reflector v_j (v_j[j] explicit, the rest below it, scaled by the column's
+// largest entry), tau[j] = 2 / (v_j . v_j), rdiag[j] the diagonal of R, the
+// part of R above the diagonal in place.  Warp 0 forms each reflector, every
+// warp applies it to its share of the remaining columns.
 static __device__ void cta_qr_f(float* X, int ld, int rows, int cols, double* tau, double* rdiag) {
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int q = rows < cols ? rows : cols;
@@ -704,57 +706,7 @@ static __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-// Warp 0: Householder QR of a float panel (conventions of warp_qr; tau and
-// the R diagonal are returned in FP64 arrays).
-static __device__ void warp_qr_f(float* X, int ld, int rows, int cols, double* tau, double* rdiag) {
-  if ((threadIdx.x >> 5) != 0) return;
-  int lane = threadIdx.x & 31;
-  int q = rows < cols ? rows : cols;
-  for (int j = 0; j < q; ++j) {
-    float* xj = X + (int64_t)j * ld;
-    float mx = 0.f;
-    for (int i = j + lane; i < rows; i += 32) mx = fmaxf(mx, fabsf(xj[i]));
-    mx = warp_max_f(mx);
-    if (mx < 1e-30f) {  // nothing left in this column (1/mx would overflow FP32)
-      if (lane == 0) {
-        tau[j] = 0.0;
-        rdiag[j] = 0.0;
-      }
-      __syncwarp();
-      continue;
-    }
-    float inv = 1.f / mx;
-    float tail = 0.f;
-    for (int i = j + 1 + lane; i < rows; i += 32) {
-      float v = xj[i] * inv;
-      tail += v * v;
-    }
-    tail = warp_sum_f(tail);
-    float v0 = xj[j] * inv;
-    float xn = sqrtf(tail + v0 * v0);
-    float alpha = v0 >= 0.f ? -xn : xn;
-    float v0n = v0 - alpha;
-    float tj = 2.f / (tail + v0n * v0n);
-    __syncwarp();
-    for (int i = j + 1 + lane; i < rows; i += 32) xj[i] *= inv;
-    if (lane == 0) {
-      xj[j] = v0n;
-      tau[j] = tj;
-      rdiag[j] = (double)alpha * mx;
-    }
-    __syncwarp();
-    for (int c = j + 1; c < cols; ++c) {
-      float* xc = X + (int64_t)c * ld;
-      float d = 0.f;
-      for (int i = j + lane; i < rows; i += 32) d += xj[i] * xc[i];
-      d = warp_sum_f(d) * tj;
-      for (int i = j + lane; i < rows; i += 32) xc[i] -= d * xj[i];
-    }
-    __syncwarp();
-  }
-}
-
-// Q = P_0 ... P_{q-1} [I; 0] (rows x q, ld ldq) from warp_qr_f reflectors;
+// Q = P_0 ... P_{q-1} [I; 0] (rows x q, ld ldq) from cta_qr_f / cta_qrcp_f reflectors;
 // each warp builds its own columns (P_j e_c needs only j <= c).
 static __device__ void form_q_f(const float* V, int ldv, int rows, int q, const double* tau, float* Q, int ldq) {
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
