@@ -39,7 +39,8 @@ def test_exports_every_declared_symbol(hm):
     assert sorted(hm.EXPORTS) == decl
 
 
-@pytest.mark.parametrize("N,d,leaf", [(4, 2, 4), (64, 2, 32), (16, 3, 64), (13, 2, 8), (21, 3, 32), (32, 3, 64)])
+@pytest.mark.parametrize("N,d,leaf", [(4, 2, 4), (64, 2, 32), (16, 3, 64), (13, 2, 8), (21, 3, 32), (32, 3, 64),
+                                      (97, 2, 32), (128, 2, 32), (64, 3, 64)])
 def test_trees_bit_exact_vs_oracle(hm, N, d, leaf):
     x = hs.grid_coords(N, d)
     ct = hm.ClusterTree(_NullCtx(), x, leaf)
@@ -53,6 +54,19 @@ def test_trees_bit_exact_vs_oracle(hm, N, d, leaf):
     a, b = bt.nodes(), ob.nodes()
     for key in ("t", "s", "level", "parent", "kind"):
         assert np.array_equal(a[key], b[key]), key
+
+
+def test_tree_edge_sizes(hm):
+    # one point, and fewer points than a leaf: a single leaf cluster and one
+    # dense block
+    for x in (np.array([[0.5, 0.5]]), hs.grid_coords(3, 2)):
+        ct = hm.ClusterTree(_NullCtx(), x, 16)
+        assert np.array_equal(ct.perm(), np.arange(x.shape[0]))
+        bt = hm.BlockTree(_NullCtx(), ct, ct, 2.0)
+        nd = bt.nodes()
+        assert len(nd["kind"]) == 1 and nd["kind"][0] == 1
+    with pytest.raises(hm.HmatError):
+        hm.ClusterTree(_NullCtx(), np.zeros((0, 2)), 16)  # no points
 
 
 def test_tree_rejects_bad_input(hm):
