@@ -171,8 +171,45 @@ def workload_config(args, probs, world: int) -> dict:
             "parallelism": par}
 
 
+def run_reference_hmul(args) -> None:
+    """The oracle's accumulated H-mult Z <- A - X X on a 16^3 sample, as the
+    reference arm of the H-mult workload."""
+    import oracle
+    oracle.build()
+    q = hs.small_laplace(16, 3, 64, 1e-4)
+    times, truncs = [], []
+    for i in range(args.warmup + args.steps):
+        oct_, obt, ocsr, OX = oracle.setup(q)
+        OX.lu(q.eps, True)
+        OZ = oracle.HMatrix.from_csr(obt, ocsr)
+        oracle.stats_reset()
+        t0 = time.perf_counter()
+        oracle.hmul(-1.0, OX, OX, OZ, q.eps, accumulated=True)
+        el = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(el)
+            truncs.append(oracle.stats()["truncations"])
+    value = sum(truncs) / sum(times)
+    p = hs.laplace3d_32()
+    line = {"impl": "reference", "metric": HMUL_METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": p.n, "leaf": p.leaf, "eta": p.eta, "eps": p.eps,
+                       "operand": "X = H-LU factors (eps 1e-4) of the 32^3 Laplacian, Z = A",
+                       "precision": args.precision, "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": "replicas1"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step one serial FP64 oracle H-mult (accumulated) of {q.name} "
+                                       f"(n={q.n}), the same recipe at a size the oracle finishes in seconds"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, rank: int, world: int) -> None:
     if rank != 0:
+        return
+    if args.workload == "hmul_3d32":
+        run_reference_hmul(args)
         return
     cfg = workload_config(args, rank_problems(args.workload, 0), world)
     p = SAMPLE[args.workload]()
@@ -349,6 +386,153 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     print(json.dumps(line), flush=True)
 
 
+HMUL_METRIC = "H-matrix multiplication Z <- blocktrunc(Z - X Y) truncations/s (accumulated updates) vs plain FP64"
+
+
+def run_hmul(args, rank: int, world: int, local_rank: int) -> None:
+    """H x H multiplication (hmat_addmul) on the factors of a 3D H-LU:
+    Z <- blocktrunc(A - X X), X = the H-LU of the 32^3 Laplacian (L and U in
+    one H-matrix), Z starting from A.  Each step restores Z and multiplies;
+    the symbolic pass runs in every step (hmat_addmul keeps no schedule)."""
+    import torch
+    import paper_1703_09085_gb300 as g
+    from paper_1703_09085_gb300 import build
+    build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    p = hs.laplace3d_32()
+    csr = p.matrix()
+    ctx = g.Context(local_rank, stream)
+    ct = g.ClusterTree(ctx, p.coords(), p.leaf)
+    bt = g.BlockTree(ctx, ct, ct, p.eta)
+    prec = g.HMAT_MIXED if args.precision == "mixed" else g.HMAT_FP64
+    X = g.HMatrix(ctx, bt, csr)
+    X.lu(p.eps, precision=g.HMAT_MIXED)  # the operand: the H-LU factors (setup, untimed)
+    Z0 = g.HMatrix(ctx, bt, csr)
+    Z = g.HMatrix(ctx, bt, csr)
+    flush = torch.empty(int(256 * 2**20) // 4, dtype=torch.float32, device=dev)
+
+    def step(precision=prec):
+        Z.copy_values_from(Z0)
+        g.addmul(ctx, -1.0, X, X, Z, p.eps, max_rank=args.max_rank, precision=precision)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    step_ms, kern_ms, flops, flops32, truncs, sched = [], [], [], [], [], []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        ev0.record(stream)
+        step()
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        st = Z.stats()
+        kern_ms.append(1e3 * st["factor_seconds"])
+        flops.append(st["flops"])
+        flops32.append(st["flops32"])
+        truncs.append(st["truncations"])
+        sched.append(st["schedule_seconds"])
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop() if clocks else None
+    value, _ = job_throughput(sum(truncs), sum(step_ms) / 1e3, world, dev)
+    st = Z.stats()
+    # end to end: Z from the host CSR arrays, the product, ranks back
+    h2d = 8 * (csr.rowptr.size + csr.colidx.size + csr.val.size) + 16 * csr.n
+    d2h = 8 * g.lib().hmat_blocktree_size(bt.h)
+    e2e_times = []
+    for i in range(1 + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Ze = g.HMatrix(ctx, bt, csr)
+        g.addmul(ctx, -1.0, X, X, Ze, p.eps, max_rank=args.max_rank, precision=prec)
+        Ze.ranks()
+        torch.cuda.synchronize()
+        if i >= 1:
+            e2e_times.append(time.perf_counter() - t0)
+        del Ze
+    e2e_value, e2e_s = job_throughput(sum(truncs), sum(e2e_times), world, dev)
+    if rank != 0:
+        return
+
+    def rel_error(Zm):
+        # ||(Z - (A - X X)) v|| / ||(A - X X) v|| for 4 seeded vectors (cluster order)
+        perm = ct.perm()
+        V = np.stack([hs.start_vector(p.n, 10 + j) for j in range(4)])  # (4, n), original order
+        Vp = V[:, perm]
+        tv = torch.from_numpy(np.ascontiguousarray(Vp)).cuda()
+        xv = torch.zeros_like(tv)
+        X.addeval(1.0, tv, xv)
+        xxv = torch.zeros_like(tv)
+        X.addeval(1.0, xv, xxv)
+        zv = torch.zeros_like(tv)
+        Zm.addeval(1.0, tv, zv)
+        av = np.stack([csr.matvec(V[j])[perm] for j in range(4)])
+        ref = av - xxv.cpu().numpy()
+        return float(np.linalg.norm(zv.cpu().numpy() - ref) / np.linalg.norm(ref))
+
+    err = rel_error(Z)
+    fp64 = None
+    if args.precision == "mixed" and not args.no_fp64:
+        ev0.record(stream)
+        step(g.HMAT_FP64)
+        ev1.record(stream)
+        ev1.synchronize()
+        s64 = Z.stats()
+        fp64 = {"ms": ev0.elapsed_time(ev1), "truncations": s64["truncations"],
+                "value": s64["truncations"] / (ev0.elapsed_time(ev1) / 1e3), "rel_error": rel_error(Z)}
+        fp64["speedup_of_chosen_form"] = fp64["ms"] / statistics.mean(step_ms)
+    avg_kern_s = statistics.mean(kern_ms) / 1e3
+    achieved = statistics.mean(flops) / avg_kern_s / 1e12
+    achieved32 = statistics.mean(flops32) / avg_kern_s / 1e12
+    line = {
+        "metric": HMUL_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
+        "config": {"workload": args.workload, "n": p.n, "leaf": p.leaf, "eta": p.eta, "eps": p.eps,
+                   "operand": "X = H-LU factors (eps 1e-4) of the 32^3 Laplacian, Z = A",
+                   "precision": args.precision, "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": f"replicas{world}"},
+        "truncations_per_step": int(statistics.mean(truncs)), "schedule_s": statistics.mean(sched),
+        "rel_error": err, "plain_fp64": fp64, "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "exec_tasks",
+                     "fp32": {"achieved": achieved32, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                              "frac": achieved32 / FP32_PEAK_TFLOPS}},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": 1e3 * e2e_s / args.steps},
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        q = hs.small_laplace(16, 3, 64, 1e-4)
+        t_all, n_tr, runs = 0.0, 0, 0
+        while t_all < 10.0 and runs < 20:
+            oct_, obt, ocsr, OX = oracle.setup(q)
+            OX.lu(q.eps, True)
+            OZ = oracle.HMatrix.from_csr(obt, ocsr)
+            oracle.stats_reset()
+            t0 = time.perf_counter()
+            oracle.hmul(-1.0, OX, OX, OZ, q.eps, accumulated=True)
+            t_all += time.perf_counter() - t0
+            n_tr += oracle.stats()["truncations"]
+            runs += 1
+        line["cpu_baseline"] = {"value": n_tr / t_all, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{runs} x serial FP64 oracle H-mult (accumulated) Z <- A - X X of "
+                                          f"{q.name} (n={q.n}), {t_all:.1f} s, {n_tr} truncations"}
+    print(json.dumps(line), flush=True)
+
+
 def precond_error(g, H, ct, csr, p, maxit=50, rtol=1e-3) -> float:
     import torch
     perm = ct.perm()
@@ -385,7 +569,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="laplace3d_32", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="laplace3d_32", choices=sorted(WORKLOADS) + ["hmul_3d32"])
     ap.add_argument("--max-rank", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparator")
@@ -402,7 +586,10 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
     try:
-        run_ours(args, rank, world, local_rank)
+        if args.workload == "hmul_3d32":
+            run_hmul(args, rank, world, local_rank)
+        else:
+            run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch
