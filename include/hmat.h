@@ -71,7 +71,9 @@ typedef struct hmat_mlp hmat_mlp;
  *             sketch that misses too much is
  *             widened and, at its limit, replaced by the exact QR + SVD.
  *  record_training  non-zero: every exact truncation records its features
- *             and rank (see hmat_lu_training_data). */
+ *             and rank (see hmat_lu_training_data).
+ *  seed       seed of the randomised sketches' Rademacher signs (0: a fixed
+ *             default); results are reproducible for a given seed. */
 enum { HMAT_FP64 = 0, HMAT_MIXED = 1 };
 typedef struct {
   double eps;
@@ -81,6 +83,7 @@ typedef struct {
   int reuse_schedule;
   const hmat_mlp* predictor;
   int record_training;
+  uint64_t seed;
 } hmat_opts;
 
 typedef struct {
@@ -243,8 +246,9 @@ hmat_status trunc_lowrank(hmat_ctx* ctx, int64_t m, int64_t n, int64_t k, double
  * pointers U[i] (ld m[i]) and V[i] (ld n[i]) (host array of device pointers).
  * k_new is a DEVICE array of count entries receiving the new ranks.  One CTA
  * per problem; the call synchronises the context stream before returning.
- * precision HMAT_MIXED (eps > 0, m n <= 2^20) first tries the randomised
- * range finder with an FP32 sketch and projection and an FP64 core, keeping
+ * precision HMAT_MIXED (eps >= 1e-5, m n <= 2^20) first tries the FP32
+ * randomised range finder of hmat_lu's mixed form (sketch, projection,
+ * pivoted-QR and Jacobi core in FP32, the residual summed in FP64), keeping
  * the same Frobenius rule (its rank may exceed the optimal one by what the
  * sketch missed); a problem whose sketch misses too much falls back to the
  * exact QR + SVD.  *randomised (host, may be NULL) receives how many problems

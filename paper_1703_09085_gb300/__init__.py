@@ -53,7 +53,7 @@ class HmatError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("max_rank", ctypes.c_int64), ("precision", ctypes.c_int),
                 ("spin_limit", ctypes.c_int64), ("reuse_schedule", ctypes.c_int), ("predictor", ctypes.c_void_p),
-                ("record_training", ctypes.c_int)]
+                ("record_training", ctypes.c_int), ("seed", ctypes.c_uint64)]
 
 
 class Stats(ctypes.Structure):

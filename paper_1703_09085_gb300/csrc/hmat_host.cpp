@@ -2,8 +2,9 @@
 //
 // Trees are built on the host (they are integer work, negligible next to the
 // arithmetic).  The numerical recursions -- H-LU with accumulated updates
-// (Section 6 with Section 4's addproduct / split / flush), the H-matrix solve
-// and the H x thin-dense product (Fig. addeval) -- are unrolled by a symbolic
+// (Section 6 with Section 4's addproduct / split / flush), H-matrix
+// multiplication (Section 4), the H-matrix solve and the H x thin-dense
+// product (Fig. addeval) -- are unrolled by a symbolic
 // pass into a task list in program order.  A task's predecessors are found by
 // tracking, per memory object, its last writer and the readers since; scratch
 // memory comes from size-classed free lists whose chunks are memory objects
@@ -1494,6 +1495,7 @@ struct LaunchOpts {
   const void* mlp = nullptr;
   bool record = false;
   std::vector<float>* rec_out = nullptr;
+  uint64_t seed = 0;  // 0: the default seed of the randomised sketches
 };
 
 void upload_sched(hmat_ctx* ctx, const Sched& S, DevSched& D) {
@@ -1559,7 +1561,7 @@ RunResult launch_sched(hmat_ctx* ctx, const Sched& S, DevSched& D, double* hbase
   e.eps = eps;
   e.mixed = mixed ? 1 : 0;
   e.rand_min_l = 8;
-  e.seed = 0x5EEDull;
+  e.seed = lo.seed ? lo.seed : 0x5EEDull;
   e.spin_iters = spin_limit > 0 ? spin_limit : (1ll << 28);
   e.spin_ns = 20ull * 1000000000ull;
   // One CTA per SM when the schedule's average parallelism (estimated work
@@ -2107,6 +2109,7 @@ void lu_batch(hmat_ctx* ctx, hmat* const* Hs, int count, const hmat_opts* opts) 
   lo.mlp = opts ? hm_internal::mlp_weights(opts->predictor) : nullptr;
   lo.record = opts && opts->record_training;
   lo.rec_out = &Hs[0]->train;
+  lo.seed = opts ? opts->seed : 0;
   RunResult rr = launch_sched(ctx, S, C->D, base, allranks.as<int>(), eps, spin, nullptr, nullptr, mixed, lo);
   for (int i = 0; i < count; ++i)
     HM_CUDA(cudaMemcpyAsync(Hs[i]->ranks.p, allranks.as<int>() + slotbase[(size_t)i], (size_t)Hs[i]->nslots * sizeof(int),
@@ -2200,6 +2203,7 @@ void addmul_run(hmat_ctx* ctx, double alpha, const hmat* X, const hmat* Y, hmat*
   lo.mlp = opts ? hm_internal::mlp_weights(opts->predictor) : nullptr;
   lo.record = opts && opts->record_training;
   lo.rec_out = &Z->train;
+  lo.seed = opts ? opts->seed : 0;
   RunResult rr = launch_sched(ctx, S, D, base, allranks.as<int>(), eps, spin, nullptr, nullptr, mixed, lo);
   HM_CUDA(cudaMemcpyAsync(Z->ranks.p, allranks.as<int>() + slotbase[2], (size_t)Z->nslots * sizeof(int),
                           cudaMemcpyDeviceToDevice, ctx->stream));
