@@ -143,7 +143,7 @@ def job_throughput(units: float, seconds: float, world: int, device=None):
 # DRAM bytes (read + write) of one exec_tasks launch, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the source tree whose
 # csrc hash is given; see profiles/launches_laplace3d_32.md.
-TRAFFIC = {"laplace3d_32": {"csrc": "91245e0a69e38028", "bytes": 2935490560 + 8779530496}}
+TRAFFIC = {"laplace3d_32": {"csrc": "0ddba7b1252bb0f3", "bytes": 2933867008 + 8772706560}}
 
 
 def csrc_hash() -> str:
