@@ -281,6 +281,10 @@ class HMatrix:
     def lu(self, eps: float, accumulated: bool = True):
         _check(lib().orc_hlu(self.h, ctypes.c_double(eps), ctypes.c_int(1 if accumulated else 0)))
 
+    def invert(self, eps: float):
+        """In place: the H-matrix inverse with accumulated updates (Fig. invert)."""
+        _check(lib().orc_hinv(self.h, ctypes.c_double(eps)))
+
     def solve(self, B, trans: bool = False) -> np.ndarray:
         B = _f64(B if np.ndim(B) == 2 else np.reshape(B, (-1, 1))).copy(order="F")
         _check(lib().orc_hsolve(self.h, ctypes.c_int64(B.shape[1]), _p(B), ctypes.c_int(1 if trans else 0)))

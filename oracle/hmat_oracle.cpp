@@ -36,6 +36,9 @@
 //    G22 - G21 G11^{-1} G12 of Section 6, with the accumulator split as in
 //    Fig. invert: lu(t1); flush + solve the off-diagonal blocks; addproduct
 //    the Schur update without flush; lu(t2) takes the accumulator.
+//  * Fig. invert: its last product, H_12 H_21', is accumulated for the block
+//    t_1 x t_1 and flushed into G_11 (the figure's index t_2 there is read as
+//    t_1, the block H_11' overwrites); a flushed accumulator is not reused.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -1349,6 +1352,100 @@ static void lu_acc(HMat& G, int b, Acc& acc, const TruncOpts& o) {
 }
 
 // ---------------------------------------------------------------------------
+// H-matrix inversion with accumulated updates (Section 6, Fig. invert).
+// ---------------------------------------------------------------------------
+// Inverse of a dense diagonal leaf: no-pivot LU, then U^{-1} L^{-1} applied to
+// the identity (the paper assumes every principal submatrix invertible).
+static void dense_inverse(Mat& A) {
+  Mat X = identity(A.m);
+  dense_lu(A);
+  dense_solve_L(A, X, 0);
+  dense_solve_U(A, X, 0);
+  A = X;
+}
+
+// Every leaf of the subtree of block b set to zero (dense leaves zero,
+// admissible leaves rank 0).
+static void zero_subtree(HMat& G, int b) {
+  if (G.kind(b) == DENSE) {
+    Mat& N = G.N[(size_t)b];
+    std::fill(N.a.begin(), N.a.end(), 0.0);
+  } else if (G.kind(b) == LOWRANK) {
+    G.R[(size_t)b].A = Mat(G.rows(b), 0);
+    G.R[(size_t)b].B = Mat(G.cols(b), 0);
+  } else {
+    for (int c : G.bt->nodes[(size_t)b].sons) zero_subtree(G, c);
+  }
+}
+
+// Fig. invert: G|_{t x t} <- (G|_{t x t} + pending updates in acc)^{-1}, with
+// H (same block tree) as the auxiliary storage of H_12 and H_21.  Readings:
+// the cluster tree is binary; a flushed accumulator is not used again (each
+// product gets a fresh one); the last product, H_12 H_21', is accumulated for
+// the block t_1 x t_1 and flushed into G_11 (the figure's index t_2 there is
+// read as t_1, the block that H_11' overwrites).
+static void invert_acc(HMat& G, HMat& H, int b, Acc& acc, const TruncOpts& o) {
+  if (G.kind(b) == DENSE) {
+    flush(acc, target_of(&G, b), o);
+    dense_inverse(G.N[(size_t)b]);
+    return;
+  }
+  if (G.kind(b) != NONLEAF) throw Error(ERR_ARG, "H-inverse: admissible diagonal block");
+  const CTree& T = *G.bt->R;
+  const CTree& C = *G.bt->C;
+  const CNode& t = G.tc(b);
+  if (t.sons.size() != 2) throw Error(ERR_ARG, "H-inverse: the cluster tree must be binary");
+  int t1 = t.sons[0], t2 = t.sons[1];
+  auto sub = split(acc, T, C, o);
+  acc.R.A = Mat(acc.R.A.m, 0);
+  acc.R.B = Mat(acc.R.B.m, 0);
+  acc.P.clear();
+  int b11 = child(*G.bt, b, t1, t1), b12 = child(*G.bt, b, t1, t2);
+  int b21 = child(*G.bt, b, t2, t1), b22 = child(*G.bt, b, t2, t2);
+  // 1. G_11 <- G_11^{-1}
+  invert_acc(G, H, b11, sub[0][0], o);
+  // 2. H_12 = G_11^{-1} G_12, H_21 = G_21 G_11^{-1} (after the pending updates
+  //    of G_12 and G_21 are flushed)
+  flush(sub[0][1], target_of(&G, b12), o);
+  flush(sub[1][0], target_of(&G, b21), o);
+  zero_subtree(H, b12);
+  zero_subtree(H, b21);
+  {
+    Acc a = acc_empty(t1, t2, T, C);
+    addproduct(1.0, G, b11, G, b12, a, o);
+    flush(a, target_of(&H, b12), o);
+  }
+  {
+    Acc a = acc_empty(t2, t1, T, C);
+    addproduct(1.0, G, b21, G, b11, a, o);
+    flush(a, target_of(&H, b21), o);
+  }
+  // 3. S = G_22 - H_21 G_12, left in the accumulator (not flushed)
+  addproduct(-1.0, H, b21, G, b12, sub[1][1], o);
+  // 4. G_22 <- S^{-1}
+  invert_acc(G, H, b22, sub[1][1], o);
+  // 5. G_12 <- H_12' = -H_12 S^{-1}, G_21 <- H_21' = -S^{-1} H_21
+  zero_subtree(G, b12);
+  zero_subtree(G, b21);
+  {
+    Acc a = acc_empty(t1, t2, T, C);
+    addproduct(-1.0, H, b12, G, b22, a, o);
+    flush(a, target_of(&G, b12), o);
+  }
+  {
+    Acc a = acc_empty(t2, t1, T, C);
+    addproduct(-1.0, G, b22, H, b21, a, o);
+    flush(a, target_of(&G, b21), o);
+  }
+  // 6. G_11 <- H_11' = G_11^{-1} - H_12 H_21'
+  {
+    Acc a = acc_empty(t1, t1, T, C);
+    addproduct(-1.0, H, b12, G, b21, a, o);
+    flush(a, target_of(&G, b11), o);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Standard H-LU: same recursion, every product applied at once (Remark after
 // the complexity theorem: rkadd in addproduct becomes rkupdate).
 // ---------------------------------------------------------------------------
@@ -1697,6 +1794,20 @@ int orc_hlu(void* h, double eps, int mode) {
     } else {
       lu_std(*G, 0, o);
     }
+    g_stats.seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  });
+}
+
+// In-place H-inversion with accumulated updates (Fig. invert).
+int orc_hinv(void* h, double eps) {
+  return guard([&] {
+    TruncOpts o;
+    o.eps = eps;
+    HMat* G = (HMat*)h;
+    std::unique_ptr<HMat> H(hmat_zero(G->bt));
+    auto t0 = std::chrono::steady_clock::now();
+    Acc acc = acc_empty(0, 0, *G->bt->R, *G->bt->C);
+    invert_acc(*G, *H, 0, acc, o);
     g_stats.seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   });
 }

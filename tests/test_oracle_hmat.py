@@ -158,3 +158,46 @@ def test_accumulated_fewer_truncations_same_quality():
     assert res[True][0] < res[False][0] and res[True][1] < res[False][1]
     assert res[True][2] < 2 * res[False][2] + 1e-12
     assert res[True][2] < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# H-matrix inversion with accumulated updates (Fig. invert)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("N,d,leaf", [(16, 2, 8), (8, 3, 16)])
+def test_hinv_eps0_is_the_inverse(N, d, leaf):
+    """eps = 0 keeps every non-zero singular value: the result is the inverse
+    of the permuted matrix (LAPACK's, as an independent reference)."""
+    p = hs.small_laplace(N, d, leaf, 0.0)
+    ct, bt, csr, H = oracle.setup(p)
+    A = H.to_dense()
+    H.invert(0.0)
+    Ai = np.linalg.inv(A)
+    assert np.abs(H.to_dense() - Ai).max() <= 1e-12 * np.abs(Ai).max()
+
+
+def test_hinv_diagonal_matrix_exact_at_any_eps():
+    """A diagonal matrix: every off-diagonal product is zero, so the
+    accumulated updates vanish and the inverse is exact whatever eps."""
+    p = hs.small_laplace(16, 2, 8, 1e-2)
+    x = p.coords()
+    ct = oracle.ClusterTree(x, p.leaf)
+    bt = oracle.BlockTree(ct, ct, p.eta)
+    n = p.n
+    diag = 1.0 + hs.uniform(5, n)
+    csr = hs.CSR(n, np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int64), diag)
+    H = oracle.HMatrix.from_csr(bt, csr)
+    H.invert(1e-2)
+    perm = ct.perm()
+    assert np.allclose(H.to_dense(), np.diag(1.0 / diag[perm]), rtol=1e-14, atol=0.0)
+
+
+def test_hinv_error_follows_eps():
+    """eps > 0: ||I - Hinv A||_2 is of the order of eps and falls with it."""
+    p = hs.small_laplace(16, 2, 8, 1e-4)
+    errs = []
+    for eps in (1e-4, 1e-6):
+        ct, bt, csr, H = oracle.setup(p)
+        A = H.to_dense()
+        H.invert(eps)
+        errs.append(np.linalg.norm(np.eye(p.n) - H.to_dense() @ A, 2))
+    assert errs[0] <= 1e-2 and errs[1] <= errs[0] / 20
