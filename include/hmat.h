@@ -221,6 +221,18 @@ hmat_status hmat_lu_batched(hmat_ctx* ctx, hmat** G, int count, const hmat_opts*
  * HMAT_ERR_ARG for aliasing or mismatched trees, device statuses as hmat_lu. */
 hmat_status hmat_addmul(hmat_ctx* ctx, double alpha, const hmat* X, const hmat* Y, hmat* Z, const hmat_opts* opts);
 
+/* In-place H-matrix inversion with accumulated updates (Section 6, Fig.
+ * invert): G <- G^{-1}, by the recursion on the binary cluster tree with the
+ * Schur complement S = G_22 - G_21 G_11^{-1} G_12, the updates of every block
+ * held in accumulators (split, addproduct, flush) and each block truncated
+ * once per flush.  Dense diagonal leaves are inverted by no-pivot LU (at most
+ * 67 x 67; larger leaves give HMAT_ERR_INTERNAL).  The auxiliary blocks H_12,
+ * H_21 live in an H-matrix allocated for the call.  opts as hmat_lu.  Runs as
+ * one persistent kernel launch and synchronises the stream; G's statistics
+ * describe the call.  Errors: HMAT_ERR_ARG for an admissible diagonal block or
+ * a cluster with more than two sons, device statuses as hmat_lu. */
+hmat_status hmat_invert(hmat_ctx* ctx, hmat* G, const hmat_opts* opts);
+
 /* Host-only analysis of the schedule hmat_lu would run for this matrix (no
  * device is touched): fills tasks, levels (longest dependency chain),
  * critical_flops / est_flops (static estimates with rank 8 for unknown

@@ -1367,6 +1367,99 @@ struct Sym {
     }
   }
 
+  // ---- H-matrix inversion with accumulated updates (Fig. invert) -------------
+  // Every leaf of M's subtree b set to zero (dense leaves zeroed, admissible
+  // leaves rank 0), and marked structurally zero for the products that follow.
+  void zero_leaves(hmat* M, int b) {
+    const BNodeH& nd = M->bt->nodes[(size_t)b];
+    if (nd.kind == 0) {
+      for (int k = 0; k < nd.nsons; ++k) zero_leaves(M, M->bt->sons[(size_t)(nd.son0 + k)]);
+      return;
+    }
+    if (M->zero[(size_t)b]) return;
+    HTask z = blank(nd.kind == 1 ? T_ZERO : T_RANKSET);
+    if (nd.kind == 1) {
+      z.m = (int)M->rows(b);
+      z.n = (int)M->cols(b);
+      z.c = hl(M, b);
+      z.ldc = z.m;
+    } else {
+      z.rout = sl(M, b);
+      z.wa = 0;
+    }
+    S.emit(z, {}, {obj_of(M, b)});
+    M->zero[(size_t)b] = 1;
+  }
+
+  STarget target_of(hmat* M, int b, int t, int r) {
+    STarget z;
+    z.M = M;
+    z.b = b;
+    z.t = t;
+    z.r = r;
+    return z;
+  }
+
+  // G|_{t x t} <- (G|_{t x t} + the updates pending in acc)^{-1}; H: auxiliary
+  // storage of H_12, H_21 on the same block tree.  The six steps of Fig.
+  // invert, with its last product accumulated for t_1 x t_1 and flushed into
+  // G_11, and a fresh accumulator for every product that is flushed.
+  void invert(hmat* G, hmat* H, int b, SAcc& acc) {
+    int kind = G->kind(b);
+    if (kind == 1) {
+      flush(acc, target_of(G, b, acc.t, acc.r));
+      HTask t = blank(T_INV);
+      t.m = (int)G->rows(b);
+      t.a = hl(G, b);
+      t.lda = t.m;
+      S.emit(t, {}, {obj_of(G, b)});
+      G->zero[(size_t)b] = 0;
+      return;
+    }
+    if (kind != 0) throw HmError(HMAT_ERR_ARG, "H-inverse: admissible diagonal block");
+    if (G->tc(b).nsons != 2) throw HmError(HMAT_ERR_ARG, "H-inverse: the cluster tree must be binary");
+    int c1 = G->tc(b).son[0], c2 = G->tc(b).son[1];
+    auto sub = split(acc);
+    acc.P.clear();
+    acc.R = SLow();
+    int b11 = G->bt->child(b, 0, 0), b12 = G->bt->child(b, 0, 1);
+    int b21 = G->bt->child(b, 1, 0), b22 = G->bt->child(b, 1, 1);
+    invert(G, H, b11, sub[0][0]);                                  // 1. G_11^{-1}
+    flush(sub[0][1], target_of(G, b12, c1, c2));
+    flush(sub[1][0], target_of(G, b21, c2, c1));
+    zero_leaves(H, b12);
+    zero_leaves(H, b21);
+    {
+      SAcc a = acc_new(c1, c2);                                    // 2. H_12 = G_11^{-1} G_12
+      addproduct(1.0, G, b11, G, b12, a);
+      flush(a, target_of(H, b12, c1, c2));
+    }
+    {
+      SAcc a = acc_new(c2, c1);                                    //    H_21 = G_21 G_11^{-1}
+      addproduct(1.0, G, b21, G, b11, a);
+      flush(a, target_of(H, b21, c2, c1));
+    }
+    addproduct(-1.0, H, b21, G, b12, sub[1][1]);                  // 3. S = G_22 - H_21 G_12
+    invert(G, H, b22, sub[1][1]);                                  // 4. S^{-1}
+    zero_leaves(G, b12);
+    zero_leaves(G, b21);
+    {
+      SAcc a = acc_new(c1, c2);                                    // 5. H_12' = -H_12 S^{-1}
+      addproduct(-1.0, H, b12, G, b22, a);
+      flush(a, target_of(G, b12, c1, c2));
+    }
+    {
+      SAcc a = acc_new(c2, c1);                                    //    H_21' = -S^{-1} H_21
+      addproduct(-1.0, G, b22, H, b21, a);
+      flush(a, target_of(G, b21, c2, c1));
+    }
+    {
+      SAcc a = acc_new(c1, c1);                                    // 6. H_11' = G_11^{-1} - H_12 H_21'
+      addproduct(-1.0, H, b12, G, b21, a);
+      flush(a, target_of(G, b11, c1, c1));
+    }
+  }
+
   void lu(hmat* G, int b, SAcc& acc) {
     int kind = G->kind(b);
     if (kind == 1) {
@@ -2151,6 +2244,88 @@ void lu_batch(hmat_ctx* ctx, hmat* const* Hs, int count, const hmat_opts* opts) 
   if (rr.status) throw HmError(rr.status, "hmat_lu: device status " + std::to_string(rr.status));
 }
 
+// In-place H-inversion with accumulated updates (Fig. invert): the auxiliary
+// H-matrix for H_12, H_21 lives for the call; one schedule, one launch.
+void invert_run(hmat_ctx* ctx, hmat* G, const hmat_opts* opts) {
+  check_ctx(ctx);
+  require(G && G->ctx == ctx, "null H-matrix or other context");
+  double eps = opts ? opts->eps : 0.0;
+  require(eps >= 0.0, "eps must be >= 0");
+  int64_t spin = opts ? opts->spin_limit : 0;
+  bool mixed = opts && opts->precision == HMAT_MIXED;
+  auto t0 = std::chrono::steady_clock::now();
+  // auxiliary H-matrix: the layout of G, all leaves zero
+  std::unique_ptr<hmat> H(new hmat());
+  H->ctx = ctx;
+  {
+    std::vector<int64_t> rp((size_t)G->n + 1, 0);
+    int64_t dummy_i = 0;
+    double dummy_v = 0.0;
+    layout_from_csr(H.get(), G->bt, G->n, rp.data(), &dummy_i, &dummy_v);
+    H->store.alloc((size_t)std::max<int64_t>(H->store_doubles, 1) * sizeof(double));
+    HM_CUDA(cudaMemsetAsync(H->store.p, 0, (size_t)std::max<int64_t>(H->store_doubles, 1) * sizeof(double),
+                            ctx->stream));
+    H->ranks.alloc((size_t)std::max(H->nslots, 1) * sizeof(int));
+    HM_CUDA(cudaMemsetAsync(H->ranks.p, 0, (size_t)std::max(H->nslots, 1) * sizeof(int), ctx->stream));
+  }
+  hmat* M[2] = {G, H.get()};
+  double* base = std::min(G->store.as<double>(), H->store.as<double>());
+  int slotbase[2] = {0, G->nslots};
+  int64_t mr = (opts && opts->max_rank > 0) ? opts->max_rank : DEFAULT_MAX_RANK;
+  mr = std::min<int64_t>(mr, G->max_rank);
+  Sched S;
+  DevSched D;
+  S.next_slot = G->nslots + H->nslots;
+  S.set_pool(0);
+  Sym sym(S, *G->bt->R, *G->bt->C, mr);
+  sym.mixed = mixed;
+  for (int i = 0; i < 2; ++i) sym.add_matrix(M[i], (int64_t)(M[i]->store.as<double>() - base), slotbase[i]);
+  SAcc root = sym.acc_new(0, 0);
+  sym.invert(G, H.get(), 0, root);
+  S.order_by_level();
+  upload_sched(ctx, S, D);
+  double sched_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  DevBuf allranks((size_t)std::max(S.next_slot, 1) * sizeof(int));
+  for (int i = 0; i < 2; ++i)
+    HM_CUDA(cudaMemcpyAsync(allranks.as<int>() + slotbase[i], M[i]->ranks.p, (size_t)M[i]->nslots * sizeof(int),
+                            cudaMemcpyDeviceToDevice, ctx->stream));
+  LaunchOpts lo;
+  lo.mlp = opts ? hm_internal::mlp_weights(opts->predictor) : nullptr;
+  lo.record = opts && opts->record_training;
+  lo.rec_out = &G->train;
+  lo.seed = opts ? opts->seed : 0;
+  RunResult rr = launch_sched(ctx, S, D, base, allranks.as<int>(), eps, spin, nullptr, nullptr, mixed, lo);
+  HM_CUDA(cudaMemcpyAsync(G->ranks.p, allranks.as<int>(), (size_t)G->nslots * sizeof(int), cudaMemcpyDeviceToDevice,
+                          ctx->stream));
+  HM_CUDA(cudaStreamSynchronize(ctx->stream));
+  G->cache.reset();  // a kept LU schedule no longer describes G's zero pattern
+  hmat_stats& st = G->st;
+  st.tasks = (int64_t)S.tasks.size();
+  st.truncations = (int64_t)rr.truncations;
+  st.flops = rr.flops;
+  st.flops32 = rr.flops32;
+  st.rand_truncations = (int64_t)rr.rand_ok;
+  st.rand_fallbacks = (int64_t)rr.rand_fail;
+  st.sketch_attempts = (int64_t)rr.sketch_attempts;
+  st.sketch_columns = (int64_t)rr.sketch_cols;
+  st.training_pairs = (int64_t)(G->train.size() / 7);
+  if (!rr.task_ns.empty()) critical_path(S, rr.task_ns, rr.task_aux, st);
+  for (int k = 0; k < 16; ++k) {
+    st.type_seconds[k] = rr.type_ns[k] * 1e-9;
+    st.type_count[k] = (int64_t)rr.type_cnt[k];
+  }
+  st.wait_seconds = rr.wait_ns * 1e-9;
+  st.factor_seconds = rr.ms * 1e-3;
+  st.schedule_seconds = sched_s;
+  st.schedule_reused = 0;
+  st.status = rr.status;
+  st.levels = S.levels();
+  st.critical_flops = S.critical_flops();
+  st.est_flops = S.est_total;
+  st.device_bytes = (int64_t)(G->store.bytes + G->ranks.bytes + H->store.bytes) + S.ws_top * 8;
+  if (rr.status) throw HmError(rr.status, "hmat_invert: device status " + std::to_string(rr.status));
+}
+
 // Z <- blocktrunc(Z + alpha X Y) in the accumulated form: one addproduct at
 // the root pair, one flush into Z, one launch.
 void addmul_run(hmat_ctx* ctx, double alpha, const hmat* X, const hmat* Y, hmat* Z, const hmat_opts* opts) {
@@ -2248,6 +2423,10 @@ hmat_status hmat_lu_batched(hmat_ctx* ctx, hmat** G, int count, const hmat_opts*
 
 hmat_status hmat_addmul(hmat_ctx* ctx, double alpha, const hmat* X, const hmat* Y, hmat* Z, const hmat_opts* opts) {
   return guarded([&] { addmul_run(ctx, alpha, X, Y, Z, opts); });
+}
+
+hmat_status hmat_invert(hmat_ctx* ctx, hmat* G, const hmat_opts* opts) {
+  return guarded([&] { invert_run(ctx, G, opts); });
 }
 
 hmat_status hmat_solve(hmat_ctx* ctx, const hmat* LU, int trans, int64_t nrhs, double* B, int64_t ldb) {

@@ -238,6 +238,34 @@ __device__ void note_exact(const ExecEnv& e, long long ti, int l, int k) {
 // ---------------------------------------------------------------------------
 // Task bodies
 // ---------------------------------------------------------------------------
+// Inverse of a dense diagonal leaf (H-inversion, leaf case of Fig. invert):
+// no-pivot LU and two triangular solves on the identity, in shared memory
+// (2 n^2 <= HM_JAC_SMEM doubles, n <= 67; larger leaves set DS_INTERNAL).
+__device__ void task_inv(const ExecEnv& e, const HTask& t, Smem& s) {
+  int n = t.m;
+  if (2 * (int64_t)n * n > HM_JAC_SMEM) {
+    if (threadIdx.x == 0) set_status(e.status, DS_INTERNAL);
+    return;
+  }
+  double* A = loc(e, t.a);
+  double* As = s.jac;
+  double* X = s.jac + (int64_t)n * n;
+  for (int idx = threadIdx.x; idx < n * n; idx += HM_THREADS) {
+    As[idx] = A[(int64_t)(idx / n) * t.lda + idx % n];
+    X[idx] = (idx % n == idx / n) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  cta_lu(As, n, n, e.status);
+  __syncthreads();
+  if (threadIdx.x == 0) s.ivals[11] = ld_acquire(e.status);  // one decision for the whole CTA
+  __syncthreads();
+  if (s.ivals[11] != 0) return;
+  cta_trsm_cols(TRSM_L, As, n, n, X, n, n);
+  cta_trsm_cols(TRSM_U, As, n, n, X, n, n);
+  for (int idx = threadIdx.x; idx < n * n; idx += HM_THREADS) A[(int64_t)(idx / n) * t.lda + idx % n] = X[idx];
+  __syncthreads();
+}
+
 __device__ void task_hmv(const ExecEnv& e, const HTask& t, Smem& s, bool f32) {
   bool trans = t.flags & F_TRANS;
   int w = width_of(e, t.wa);
@@ -743,6 +771,8 @@ __device__ double task_flops(const ExecEnv& e, const HTask& t) {
       return 2.0 / 3.0 * (double)t.m * t.m * t.m;
     case T_TRSM:
       return (double)t.m * t.m * width_of(e, t.wa);
+    case T_INV:
+      return 2.0 * t.m * (double)t.m * t.m;
     case T_GEMM:
       return 2.0 * t.m * t.n * (double)width_of(e, t.wa);
     case T_ADD:
@@ -821,6 +851,9 @@ __device__ void run_task(const ExecEnv& e, const HTask& t, Smem& s, long long ti
     }
     case T_RANKSET:
       if (threadIdx.x == 0) e.ranks[t.rout] = width_of(e, t.wa);
+      break;
+    case T_INV:
+      task_inv(e, t, s);
       break;
     case T_RKADD:
       task_rkadd(e, t, s, ti);

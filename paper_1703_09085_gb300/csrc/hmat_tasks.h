@@ -23,7 +23,8 @@ enum TaskType : int32_t {
   T_ROWMERGE = 8,    // Fig. rowmerge of two parts (a,b,wa) (c,d,wb) -> (e,f,rout)
   T_COPY = 9,        // copy m x n (ld) , optional transposition
   T_ZERO = 10,       // zero m x n (ld)
-  T_RANKSET = 11     // ranks[rout] = width (fixed or slot)
+  T_RANKSET = 11,    // ranks[rout] = width (fixed or slot)
+  T_INV = 12         // inverse of a dense diagonal leaf in place (a: N, m: size, lda)
 };
 
 // T_TRSM variants
