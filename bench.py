@@ -144,7 +144,7 @@ def job_throughput(units: float, seconds: float, world: int, device=None):
 # DRAM bytes (read + write) of one exec_tasks launch, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the source tree whose
 # csrc hash is given; see profiles/launches_laplace3d_32.md.
-TRAFFIC = {"laplace3d_32": {"csrc": "0ddba7b1252bb0f3", "bytes": 2933867008 + 8772706560}}
+TRAFFIC = {"laplace3d_32": {"csrc": "9d4de9a4b5326e84", "bytes": 2937054976 + 8743640576}}
 
 
 def csrc_hash() -> str:
