@@ -60,3 +60,30 @@ def test_batch_ranks_get_their_own_instances():
     assert not set(p.seed for p in r0) & set(p.seed for p in r1)
     # a single H-LU is replicated
     assert bench.rank_problems("laplace3d_32", 1)[0].n == bench.rank_problems("laplace3d_32", 0)[0].n
+
+
+def test_traffic_only_for_the_captured_sources(monkeypatch):
+    """roofline.traffic comes from an ncu capture of one source tree: it is
+    reported while the kernel sources hash the same, and null otherwise."""
+    sys.path.insert(0, ROOT)
+    import bench
+    h = bench.csrc_hash()
+    assert len(h) == 16 and h == bench.csrc_hash()
+    monkeypatch.setattr(bench, "TRAFFIC", {"laplace3d_32": {"csrc": h, "bytes": 123}})
+    assert bench.traffic_per_launch("laplace3d_32") == 123
+    monkeypatch.setattr(bench, "TRAFFIC", {"laplace3d_32": {"csrc": "0" * 16, "bytes": 123}})
+    assert bench.traffic_per_launch("laplace3d_32") is None
+    assert bench.traffic_per_launch("diffusion2d_batch64") is None
+
+
+def test_config_names_the_workload_and_its_sizes():
+    sys.path.insert(0, ROOT)
+    import argparse
+    import bench
+    args = argparse.Namespace(workload="laplace3d_32", precision="mixed", max_rank=0)
+    cfg = bench.workload_config(args, bench.rank_problems("laplace3d_32", 0), 1)
+    assert cfg["workload"] == "laplace3d_32" and cfg["n"] == 32 ** 3 and cfg["leaf"] == 64 and cfg["eps"] == 1e-4
+    assert "flushed" in cfg["l2"] and cfg["parallelism"] == "replicas1"
+    args.workload = "diffusion2d_batch64"
+    cfg = bench.workload_config(args, bench.rank_problems("diffusion2d_batch64", 0), 2)
+    assert cfg["instances"] == 64 and "sharded" in cfg["parallelism"]
