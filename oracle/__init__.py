@@ -281,6 +281,11 @@ class HMatrix:
     def lu(self, eps: float, accumulated: bool = True):
         _check(lib().orc_hlu(self.h, ctypes.c_double(eps), ctypes.c_int(1 if accumulated else 0)))
 
+    def cholesky(self, eps: float):
+        """In place: H-Cholesky with accumulated updates; the lower blocks hold L
+        (A = L L^T), the upper ones L^T."""
+        _check(lib().orc_hchol(self.h, ctypes.c_double(eps)))
+
     def invert(self, eps: float):
         """In place: the H-matrix inverse with accumulated updates (Fig. invert)."""
         _check(lib().orc_hinv(self.h, ctypes.c_double(eps)))

@@ -1352,6 +1352,85 @@ static void lu_acc(HMat& G, int b, Acc& acc, const TruncOpts& o) {
 }
 
 // ---------------------------------------------------------------------------
+// H-Cholesky with accumulated updates (Section 6: treated "in a similar way"
+// as the inversion).  G symmetric positive definite; afterwards the lower
+// blocks and the lower triangles of the diagonal leaves hold L (G = L L^T) and
+// the upper ones hold L^T, so that the LU's right solve X <- X U^{-1} with
+// U = L^T is X L^{-T}.
+// ---------------------------------------------------------------------------
+// Lower Cholesky factor of a dense SPD leaf in place, its transpose mirrored
+// into the strictly upper triangle.
+static void dense_chol(Mat& A) {
+  CatScope cat(2);
+  i64 n = A.m;
+  g_stats.dense_lu++;
+  count_flops((double)n * (double)n * (double)n / 3.0);
+  for (i64 k = 0; k < n; ++k) {
+    double d = A(k, k);
+    for (i64 j = 0; j < k; ++j) d -= A(k, j) * A(k, j);
+    if (!(d > 0.0) || !std::isfinite(d))
+      throw Error(ERR_SINGULAR, "dense Cholesky: non-positive pivot " + std::to_string(d) + " at row " +
+                                    std::to_string(k));
+    double lkk = std::sqrt(d);
+    A(k, k) = lkk;
+    for (i64 i = k + 1; i < n; ++i) {
+      double v = A(i, k);
+      for (i64 j = 0; j < k; ++j) v -= A(i, j) * A(k, j);
+      A(i, k) = v / lkk;
+    }
+  }
+  for (i64 j = 1; j < n; ++j)
+    for (i64 i = 0; i < j; ++i) A(i, j) = A(j, i);
+}
+
+// G's block dst (s x t) <- G's block src (t x s) transposed, leaf by leaf
+// (the block tree of one cluster tree is symmetric).
+static void transpose_block(HMat& G, int src, int dst) {
+  int kind = G.kind(src);
+  if (kind == DENSE) {
+    G.N[(size_t)dst] = transpose(G.N[(size_t)src]);
+  } else if (kind == LOWRANK) {
+    G.R[(size_t)dst].A = G.R[(size_t)src].B;
+    G.R[(size_t)dst].B = G.R[(size_t)src].A;
+  } else {
+    const CNode& t = G.tc(src);
+    const CNode& s = G.sc(src);
+    for (int ti : t.sons)
+      for (int sj : s.sons) transpose_block(G, child(*G.bt, src, ti, sj), child(*G.bt, dst, sj, ti));
+  }
+}
+
+// chol(t): the block Cholesky recursion on the binary cluster tree with the
+// accumulator split as for the LU: chol(t1); flush the (2,1) updates and solve
+// L21 = G21 L11^{-T}; mirror L21^T into the (1,2) block; addproduct the Schur
+// update -L21 L21^T without flush; chol(t2) takes the accumulator.  The (1,2)
+// accumulator is not used (its updates are the transposes of the (2,1) ones).
+static void chol_acc(HMat& G, int b, Acc& acc, const TruncOpts& o) {
+  if (G.kind(b) == DENSE) {
+    flush(acc, target_of(&G, b), o);
+    dense_chol(G.N[(size_t)b]);
+    return;
+  }
+  if (G.kind(b) != NONLEAF) throw Error(ERR_ARG, "H-Cholesky: admissible diagonal block");
+  const CTree& T = *G.bt->R;
+  const CNode& t = G.tc(b);
+  if (t.sons.size() != 2) throw Error(ERR_ARG, "H-Cholesky: the cluster tree must be binary");
+  auto sub = split(acc, T, *G.bt->C, o);
+  acc.R.A = Mat(acc.R.A.m, 0);
+  acc.R.B = Mat(acc.R.B.m, 0);
+  acc.P.clear();
+  int t1 = t.sons[0], t2 = t.sons[1];
+  int b11 = child(*G.bt, b, t1, t1), b12 = child(*G.bt, b, t1, t2);
+  int b21 = child(*G.bt, b, t2, t1), b22 = child(*G.bt, b, t2, t2);
+  chol_acc(G, b11, sub[0][0], o);
+  flush(sub[1][0], target_of(&G, b21), o);
+  trsm_U_acc(G, b11, b21, o);  // G21 L11^{-T}: U = L11^T sits in the upper part of block b11
+  transpose_block(G, b21, b12);
+  addproduct(-1.0, G, b21, G, b12, sub[1][1], o);
+  chol_acc(G, b22, sub[1][1], o);
+}
+
+// ---------------------------------------------------------------------------
 // H-matrix inversion with accumulated updates (Section 6, Fig. invert).
 // ---------------------------------------------------------------------------
 // Inverse of a dense diagonal leaf: no-pivot LU, then U^{-1} L^{-1} applied to
@@ -1794,6 +1873,19 @@ int orc_hlu(void* h, double eps, int mode) {
     } else {
       lu_std(*G, 0, o);
     }
+    g_stats.seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  });
+}
+
+// In-place H-Cholesky with accumulated updates (lower blocks: L, upper: L^T).
+int orc_hchol(void* h, double eps) {
+  return guard([&] {
+    TruncOpts o;
+    o.eps = eps;
+    HMat* G = (HMat*)h;
+    auto t0 = std::chrono::steady_clock::now();
+    Acc acc = acc_empty(0, 0, *G->bt->R, *G->bt->C);
+    chol_acc(*G, 0, acc, o);
     g_stats.seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   });
 }

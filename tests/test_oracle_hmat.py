@@ -201,3 +201,40 @@ def test_hinv_error_follows_eps():
         H.invert(eps)
         errs.append(np.linalg.norm(np.eye(p.n) - H.to_dense() @ A, 2))
     assert errs[0] <= 1e-2 and errs[1] <= errs[0] / 20
+
+
+# ---------------------------------------------------------------------------
+# H-Cholesky with accumulated updates (Section 6, treated like the inversion)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prob", ["laplace2d_16", "laplace3d_8", "diffusion2d_20"])
+def test_hchol_eps0_is_the_cholesky_factor(prob):
+    """eps = 0: the lower blocks hold LAPACK's Cholesky factor of the permuted
+    SPD matrix."""
+    p = {"laplace2d_16": hs.small_laplace(16, 2, 8, 0.0), "laplace3d_8": hs.small_laplace(8, 3, 16, 0.0),
+         "diffusion2d_20": hs.Problem("diffusion2d_20", 20, 2, 8, 2.0, 0.0, kind="diffusion", lc=0.1, seed=7)}[prob]
+    ct, bt, csr, H = oracle.setup(p)
+    A = H.to_dense()
+    H.cholesky(0.0)
+    Lr = np.linalg.cholesky(A)
+    assert np.abs(np.tril(H.to_dense()) - Lr).max() <= 1e-12 * np.abs(Lr).max()
+
+
+def test_hchol_error_follows_eps_and_halves_the_truncations():
+    """eps > 0: ||I - (L L^T)^{-1} A||_2 of the order of eps and falling with it;
+    the symmetric recursion truncates about half as often as the LU."""
+    p = hs.small_laplace(16, 2, 8, 1e-4)
+    errs = []
+    for eps in (1e-4, 1e-6):
+        ct, bt, csr, H = oracle.setup(p)
+        A = H.to_dense()
+        oracle.stats_reset()
+        H.cholesky(eps)
+        tc = oracle.stats()["truncations"]
+        L = np.tril(H.to_dense())
+        errs.append(np.linalg.norm(np.eye(p.n) - np.linalg.solve(L @ L.T, A), 2))
+    assert errs[0] <= 10 * 1e-4 and errs[1] <= errs[0] / 20
+    ct, bt, csr, H = oracle.setup(p)
+    oracle.stats_reset()
+    H.lu(1e-6, True)
+    tl = oracle.stats()["truncations"]
+    assert 0.4 * tl <= tc <= 0.6 * tl
