@@ -286,9 +286,10 @@ class HMatrix:
         (A = L L^T), the upper ones L^T."""
         _check(lib().orc_hchol(self.h, ctypes.c_double(eps)))
 
-    def invert(self, eps: float):
-        """In place: the H-matrix inverse with accumulated updates (Fig. invert)."""
-        _check(lib().orc_hinv(self.h, ctypes.c_double(eps)))
+    def invert(self, eps: float, accumulated: bool = True):
+        """In place: the H-matrix inverse with accumulated updates (Fig. invert),
+        or by the standard multiplication."""
+        _check(lib().orc_hinv(self.h, ctypes.c_double(eps), ctypes.c_int(1 if accumulated else 0)))
 
     def solve(self, B, trans: bool = False) -> np.ndarray:
         B = _f64(B if np.ndim(B) == 2 else np.reshape(B, (-1, 1))).copy(order="F")

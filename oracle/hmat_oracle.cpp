@@ -1524,6 +1524,34 @@ static void invert_acc(HMat& G, HMat& H, int b, Acc& acc, const TruncOpts& o) {
   }
 }
 
+// The same six steps with every product applied at once by the standard
+// multiplication (Section 4 before "Accumulated updates"): the standard
+// H-inversion the accumulated one is compared with.
+static void invert_std(HMat& G, HMat& H, int b, const TruncOpts& o) {
+  if (G.kind(b) == DENSE) {
+    dense_inverse(G.N[(size_t)b]);
+    return;
+  }
+  if (G.kind(b) != NONLEAF) throw Error(ERR_ARG, "H-inverse: admissible diagonal block");
+  const CNode& t = G.tc(b);
+  if (t.sons.size() != 2) throw Error(ERR_ARG, "H-inverse: the cluster tree must be binary");
+  int t1 = t.sons[0], t2 = t.sons[1];
+  int b11 = child(*G.bt, b, t1, t1), b12 = child(*G.bt, b, t1, t2);
+  int b21 = child(*G.bt, b, t2, t1), b22 = child(*G.bt, b, t2, t2);
+  invert_std(G, H, b11, o);
+  zero_subtree(H, b12);
+  zero_subtree(H, b21);
+  mult_std(1.0, G, b11, G, b12, target_of(&H, b12), o);
+  mult_std(1.0, G, b21, G, b11, target_of(&H, b21), o);
+  mult_std(-1.0, H, b21, G, b12, target_of(&G, b22), o);
+  invert_std(G, H, b22, o);
+  zero_subtree(G, b12);
+  zero_subtree(G, b21);
+  mult_std(-1.0, H, b12, G, b22, target_of(&G, b12), o);
+  mult_std(-1.0, G, b22, H, b21, target_of(&G, b21), o);
+  mult_std(-1.0, H, b12, G, b21, target_of(&G, b11), o);
+}
+
 // ---------------------------------------------------------------------------
 // Standard H-LU: same recursion, every product applied at once (Remark after
 // the complexity theorem: rkadd in addproduct becomes rkupdate).
@@ -1890,8 +1918,8 @@ int orc_hchol(void* h, double eps) {
   });
 }
 
-// In-place H-inversion with accumulated updates (Fig. invert).
-int orc_hinv(void* h, double eps) {
+// In-place H-inversion: accumulated (mode 1, Fig. invert) or standard (0).
+int orc_hinv(void* h, double eps, int mode) {
   return guard([&] {
     TruncOpts o;
     o.eps = eps;
@@ -1899,7 +1927,10 @@ int orc_hinv(void* h, double eps) {
     std::unique_ptr<HMat> H(hmat_zero(G->bt));
     auto t0 = std::chrono::steady_clock::now();
     Acc acc = acc_empty(0, 0, *G->bt->R, *G->bt->C);
-    invert_acc(*G, *H, 0, acc, o);
+    if (mode == 1)
+      invert_acc(*G, *H, 0, acc, o);
+    else
+      invert_std(*G, *H, 0, o);
     g_stats.seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   });
 }

@@ -238,3 +238,22 @@ def test_hchol_error_follows_eps_and_halves_the_truncations():
     H.lu(1e-6, True)
     tl = oracle.stats()["truncations"]
     assert 0.4 * tl <= tc <= 0.6 * tl
+
+
+def test_hinv_standard_and_accumulated_agree():
+    """The standard inversion (every product applied at once) and the
+    accumulated one (Fig. invert) agree to O(eps), reach errors within a small
+    factor of each other, and the accumulated one truncates less often."""
+    p = hs.small_laplace(16, 2, 8, 1e-4)
+    out = {}
+    for acc in (True, False):
+        ct, bt, csr, H = oracle.setup(p)
+        A = H.to_dense()
+        oracle.stats_reset()
+        H.invert(p.eps, accumulated=acc)
+        D = H.to_dense()
+        out[acc] = (D, np.linalg.norm(np.eye(p.n) - D @ A, 2), oracle.stats()["truncations"])
+    Ai = np.linalg.inv(A)
+    assert np.linalg.norm(out[True][0] - out[False][0], 2) <= 10 * p.eps * np.linalg.norm(Ai, 2)
+    assert out[True][1] <= 4 * out[False][1] and out[False][1] <= 4 * out[True][1]
+    assert out[True][2] < out[False][2]
