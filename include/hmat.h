@@ -233,6 +233,16 @@ hmat_status hmat_addmul(hmat_ctx* ctx, double alpha, const hmat* X, const hmat* 
  * a cluster with more than two sons, device statuses as hmat_lu. */
 hmat_status hmat_invert(hmat_ctx* ctx, hmat* G, const hmat_opts* opts);
 
+/* In-place H-Cholesky with accumulated updates for a symmetric positive
+ * definite G (Section 6: treated like the inversion): chol(t1); L21 =
+ * G21 L11^{-T}; L21^T mirrored into the (1,2) block; the Schur update
+ * -L21 L21^T accumulated for the (2,2) block; chol(t2).  Afterwards the lower
+ * blocks and the lower triangles of the diagonal leaves hold L (G = L L^T),
+ * the upper ones L^T.  Dense diagonal leaves up to 96 x 96 (larger give
+ * HMAT_ERR_INTERNAL); a non-positive pivot gives HMAT_ERR_SINGULAR.  opts as
+ * hmat_lu; one persistent launch; synchronises the stream. */
+hmat_status hmat_cholesky(hmat_ctx* ctx, hmat* G, const hmat_opts* opts);
+
 /* Host-only analysis of the schedule hmat_lu would run for this matrix (no
  * device is touched): fills tasks, levels (longest dependency chain),
  * critical_flops / est_flops (static estimates with rank 8 for unknown

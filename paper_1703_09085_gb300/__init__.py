@@ -40,7 +40,7 @@ EXPORTS = ["hmat_last_error", "hmat_ctx_create", "hmat_ctx_destroy", "hmat_clust
            "trunc_lowrank", "trunc_lowrank_batched", "hmat_stats_get", "hmat_ranks", "hmat_copy_values",
            "hmat_analyze_lu", "trunc_lowrank_noalloc", "hmat_lu_batched", "hmat_lu_training_data",
            "hmat_mlp_create", "hmat_mlp_destroy", "hmat_mlp_get_params", "hmat_mlp_set_params", "hmat_mlp_forward",
-           "hmat_mlp_grad", "hmat_mlp_train", "hmat_addmul", "hmat_invert"]
+           "hmat_mlp_grad", "hmat_mlp_train", "hmat_addmul", "hmat_invert", "hmat_cholesky"]
 MLP_NPARAM = 4673
 
 
@@ -217,6 +217,12 @@ class HMatrix:
         o = Opts(eps, max_rank, precision, spin_limit, int(reuse_schedule), predictor.h if predictor else None,
                  int(record_training))
         _check(lib().hmat_lu(self.ctx.h, self.h, ctypes.byref(o)))
+
+    def cholesky(self, eps: float, max_rank: int = 0, precision: int = HMAT_FP64, spin_limit: int = 0):
+        """In place: H-Cholesky with accumulated updates (hmat_cholesky); lower
+        blocks L, upper blocks L^T."""
+        o = Opts(eps, max_rank, precision, spin_limit, 0, None, 0)
+        _check(lib().hmat_cholesky(self.ctx.h, self.h, ctypes.byref(o)))
 
     def invert(self, eps: float, max_rank: int = 0, precision: int = HMAT_FP64, spin_limit: int = 0,
                predictor=None):

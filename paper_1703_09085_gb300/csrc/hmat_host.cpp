@@ -1367,6 +1367,97 @@ struct Sym {
     }
   }
 
+  // ---- H-Cholesky with accumulated updates -----------------------------------
+  // M's block dst (s x t) <- block src (t x s) transposed, leaf by leaf (the
+  // block tree of one cluster tree is symmetric): dense leaves by a transposed
+  // copy, low-rank leaves by swapping the factors and the rank.
+  void transpose_block(hmat* M, int src, int dst) {
+    const BNodeH& nd = M->bt->nodes[(size_t)src];
+    if (nd.kind == 0) {
+      int ns = M->tc(src).nsons, nr = M->sc(src).nsons;
+      for (int i = 0; i < ns; ++i)
+        for (int j = 0; j < nr; ++j) transpose_block(M, M->bt->child(src, i, j), M->bt->child(dst, j, i));
+      return;
+    }
+    int m = (int)M->rows(src), n = (int)M->cols(src);
+    if (nd.kind == 1) {
+      HTask c = blank(T_COPY);
+      c.flags = F_TRANS;
+      c.m = n;
+      c.n = m;
+      c.a = hl(M, src);
+      c.lda = m;
+      c.c = hl(M, dst);
+      c.ldc = n;
+      S.emit(c, {obj_of(M, src)}, {obj_of(M, dst)});
+    } else {
+      int cap = M->cap[(size_t)src];
+      HTask u = blank(T_COPY);  // U_dst (n x cap) <- V_src
+      u.m = n;
+      u.n = cap;
+      u.a = hv(M, src);
+      u.lda = n;
+      u.c = hl(M, dst);
+      u.ldc = n;
+      S.emit(u, {obj_of(M, src)}, {obj_of(M, dst)});
+      HTask v = blank(T_COPY);  // V_dst (m x cap) <- U_src
+      v.m = m;
+      v.n = cap;
+      v.a = hl(M, src);
+      v.lda = m;
+      v.c = hv(M, dst);
+      v.ldc = m;
+      S.emit(v, {obj_of(M, src)}, {obj_of(M, dst)});
+      HTask r = blank(T_RANKSET);
+      r.rout = sl(M, dst);
+      r.wa = -(sl(M, src) + 1);
+      S.emit(r, {obj_of(M, src)}, {obj_of(M, dst)});
+    }
+    M->zero[(size_t)dst] = M->zero[(size_t)src];
+  }
+
+  // chol(t): chol(t1); flush the (2,1) updates and solve L21 = G21 L11^{-T}
+  // (the LU's right solve, U = L11^T sits above the diagonal); mirror L21^T
+  // into the (1,2) block; addproduct the Schur update -L21 L21^T without flush;
+  // chol(t2) takes the accumulator.  The (1,2) accumulator is dropped: its
+  // updates are the transposes of the (2,1) ones.
+  void chol(hmat* G, int b, SAcc& acc) {
+    int kind = G->kind(b);
+    if (kind == 1) {
+      STarget z;
+      z.M = G;
+      z.b = b;
+      z.t = acc.t;
+      z.r = acc.r;
+      flush(acc, z);
+      HTask t = blank(T_CHOL);
+      t.m = (int)G->rows(b);
+      t.a = hl(G, b);
+      t.lda = t.m;
+      S.emit(t, {}, {obj_of(G, b)});
+      return;
+    }
+    if (kind != 0) throw HmError(HMAT_ERR_ARG, "H-Cholesky: admissible diagonal block");
+    if (G->tc(b).nsons != 2) throw HmError(HMAT_ERR_ARG, "H-Cholesky: the cluster tree must be binary");
+    int c1 = G->tc(b).son[0], c2 = G->tc(b).son[1];
+    auto sub = split(acc);
+    acc.P.clear();
+    acc.R = SLow();
+    int b11 = G->bt->child(b, 0, 0), b12 = G->bt->child(b, 0, 1);
+    int b21 = G->bt->child(b, 1, 0), b22 = G->bt->child(b, 1, 1);
+    chol(G, b11, sub[0][0]);
+    STarget z;
+    z.M = G;
+    z.b = b21;
+    z.t = c2;
+    z.r = c1;
+    flush(sub[1][0], z);
+    trsm_U(G, b11, b21);
+    transpose_block(G, b21, b12);
+    addproduct(-1.0, G, b21, G, b12, sub[1][1]);
+    chol(G, b22, sub[1][1]);
+  }
+
   // ---- H-matrix inversion with accumulated updates (Fig. invert) -------------
   // Every leaf of M's subtree b set to zero (dense leaves zeroed, admissible
   // leaves rank 0), and marked structurally zero for the products that follow.
@@ -2244,6 +2335,69 @@ void lu_batch(hmat_ctx* ctx, hmat* const* Hs, int count, const hmat_opts* opts) 
   if (rr.status) throw HmError(rr.status, "hmat_lu: device status " + std::to_string(rr.status));
 }
 
+// In-place H-Cholesky with accumulated updates: one schedule, one launch.
+void chol_run(hmat_ctx* ctx, hmat* G, const hmat_opts* opts) {
+  check_ctx(ctx);
+  require(G && G->ctx == ctx, "null H-matrix or other context");
+  double eps = opts ? opts->eps : 0.0;
+  require(eps >= 0.0, "eps must be >= 0");
+  int64_t spin = opts ? opts->spin_limit : 0;
+  bool mixed = opts && opts->precision == HMAT_MIXED;
+  auto t0 = std::chrono::steady_clock::now();
+  int64_t mr = (opts && opts->max_rank > 0) ? opts->max_rank : DEFAULT_MAX_RANK;
+  mr = std::min<int64_t>(mr, G->max_rank);
+  Sched S;
+  DevSched D;
+  S.next_slot = G->nslots;
+  S.set_pool(0);
+  Sym sym(S, *G->bt->R, *G->bt->C, mr);
+  sym.mixed = mixed;
+  sym.add_matrix(G);
+  SAcc root = sym.acc_new(0, 0);
+  sym.chol(G, 0, root);
+  S.order_by_level();
+  upload_sched(ctx, S, D);
+  double sched_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  DevBuf allranks((size_t)std::max(S.next_slot, 1) * sizeof(int));
+  HM_CUDA(cudaMemcpyAsync(allranks.as<int>(), G->ranks.p, (size_t)G->nslots * sizeof(int), cudaMemcpyDeviceToDevice,
+                          ctx->stream));
+  LaunchOpts lo;
+  lo.mlp = opts ? hm_internal::mlp_weights(opts->predictor) : nullptr;
+  lo.record = opts && opts->record_training;
+  lo.rec_out = &G->train;
+  lo.seed = opts ? opts->seed : 0;
+  RunResult rr = launch_sched(ctx, S, D, G->store.as<double>(), allranks.as<int>(), eps, spin, nullptr, nullptr,
+                              mixed, lo);
+  HM_CUDA(cudaMemcpyAsync(G->ranks.p, allranks.as<int>(), (size_t)G->nslots * sizeof(int), cudaMemcpyDeviceToDevice,
+                          ctx->stream));
+  HM_CUDA(cudaStreamSynchronize(ctx->stream));
+  G->cache.reset();
+  hmat_stats& st = G->st;
+  st.tasks = (int64_t)S.tasks.size();
+  st.truncations = (int64_t)rr.truncations;
+  st.flops = rr.flops;
+  st.flops32 = rr.flops32;
+  st.rand_truncations = (int64_t)rr.rand_ok;
+  st.rand_fallbacks = (int64_t)rr.rand_fail;
+  st.sketch_attempts = (int64_t)rr.sketch_attempts;
+  st.sketch_columns = (int64_t)rr.sketch_cols;
+  if (!rr.task_ns.empty()) critical_path(S, rr.task_ns, rr.task_aux, st);
+  for (int k = 0; k < 16; ++k) {
+    st.type_seconds[k] = rr.type_ns[k] * 1e-9;
+    st.type_count[k] = (int64_t)rr.type_cnt[k];
+  }
+  st.wait_seconds = rr.wait_ns * 1e-9;
+  st.factor_seconds = rr.ms * 1e-3;
+  st.schedule_seconds = sched_s;
+  st.schedule_reused = 0;
+  st.status = rr.status;
+  st.levels = S.levels();
+  st.critical_flops = S.critical_flops();
+  st.est_flops = S.est_total;
+  st.device_bytes = (int64_t)(G->store.bytes + G->ranks.bytes) + S.ws_top * 8;
+  if (rr.status) throw HmError(rr.status, "hmat_cholesky: device status " + std::to_string(rr.status));
+}
+
 // In-place H-inversion with accumulated updates (Fig. invert): the auxiliary
 // H-matrix for H_12, H_21 lives for the call; one schedule, one launch.
 void invert_run(hmat_ctx* ctx, hmat* G, const hmat_opts* opts) {
@@ -2427,6 +2581,10 @@ hmat_status hmat_addmul(hmat_ctx* ctx, double alpha, const hmat* X, const hmat* 
 
 hmat_status hmat_invert(hmat_ctx* ctx, hmat* G, const hmat_opts* opts) {
   return guarded([&] { invert_run(ctx, G, opts); });
+}
+
+hmat_status hmat_cholesky(hmat_ctx* ctx, hmat* G, const hmat_opts* opts) {
+  return guarded([&] { chol_run(ctx, G, opts); });
 }
 
 hmat_status hmat_solve(hmat_ctx* ctx, const hmat* LU, int trans, int64_t nrhs, double* B, int64_t ldb) {

@@ -266,6 +266,48 @@ __device__ void task_inv(const ExecEnv& e, const HTask& t, Smem& s) {
   __syncthreads();
 }
 
+// Cholesky of a dense SPD diagonal leaf (H-Cholesky, leaf case): the lower
+// factor L in the lower triangle, L^T mirrored into the strictly upper one,
+// right-looking in shared memory (n^2 <= HM_JAC_SMEM doubles, n <= 96;
+// larger leaves set DS_INTERNAL).  A non-positive pivot sets DS_SINGULAR.
+__device__ void task_chol(const ExecEnv& e, const HTask& t, Smem& s) {
+  int n = t.m;
+  if ((int64_t)n * n > HM_JAC_SMEM) {
+    if (threadIdx.x == 0) set_status(e.status, DS_INTERNAL);
+    return;
+  }
+  double* A = loc(e, t.a);
+  double* As = s.jac;
+  for (int idx = threadIdx.x; idx < n * n; idx += HM_THREADS) As[idx] = A[(int64_t)(idx / n) * t.lda + idx % n];
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      double d = As[k + (int64_t)k * n];
+      s.ivals[11] = (d > 0.0 && isfinite(d)) ? 0 : 1;
+      if (s.ivals[11]) set_status(e.status, DS_SINGULAR);
+      s.bcast[0] = s.ivals[11] ? 1.0 : sqrt(d);
+    }
+    __syncthreads();
+    if (s.ivals[11]) return;  // the same decision on every thread
+    double lkk = s.bcast[0];
+    double inv = 1.0 / lkk;
+    for (int i = k + 1 + threadIdx.x; i < n; i += HM_THREADS) As[i + (int64_t)k * n] *= inv;
+    __syncthreads();
+    if (threadIdx.x == 0) As[k + (int64_t)k * n] = lkk;
+    int rem = n - k - 1;
+    for (int idx = threadIdx.x; idx < rem * rem; idx += HM_THREADS) {
+      int i = k + 1 + idx % rem, j = k + 1 + idx / rem;
+      if (j <= i) As[i + (int64_t)j * n] -= As[i + (int64_t)k * n] * As[j + (int64_t)k * n];
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < n * n; idx += HM_THREADS) {
+    int i = idx % n, j = idx / n;
+    A[(int64_t)j * t.lda + i] = i >= j ? As[i + (int64_t)j * n] : As[j + (int64_t)i * n];
+  }
+  __syncthreads();
+}
+
 __device__ void task_hmv(const ExecEnv& e, const HTask& t, Smem& s, bool f32) {
   bool trans = t.flags & F_TRANS;
   int w = width_of(e, t.wa);
@@ -773,6 +815,8 @@ __device__ double task_flops(const ExecEnv& e, const HTask& t) {
       return (double)t.m * t.m * width_of(e, t.wa);
     case T_INV:
       return 2.0 * t.m * (double)t.m * t.m;
+    case T_CHOL:
+      return (double)t.m * t.m * t.m / 3.0;
     case T_GEMM:
       return 2.0 * t.m * t.n * (double)width_of(e, t.wa);
     case T_ADD:
@@ -854,6 +898,9 @@ __device__ void run_task(const ExecEnv& e, const HTask& t, Smem& s, long long ti
       break;
     case T_INV:
       task_inv(e, t, s);
+      break;
+    case T_CHOL:
+      task_chol(e, t, s);
       break;
     case T_RKADD:
       task_rkadd(e, t, s, ti);

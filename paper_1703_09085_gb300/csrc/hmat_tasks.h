@@ -24,7 +24,8 @@ enum TaskType : int32_t {
   T_COPY = 9,        // copy m x n (ld) , optional transposition
   T_ZERO = 10,       // zero m x n (ld)
   T_RANKSET = 11,    // ranks[rout] = width (fixed or slot)
-  T_INV = 12         // inverse of a dense diagonal leaf in place (a: N, m: size, lda)
+  T_INV = 12,        // inverse of a dense diagonal leaf in place (a: N, m: size, lda)
+  T_CHOL = 13        // Cholesky of a dense SPD diagonal leaf in place, L^T mirrored above
 };
 
 // T_TRSM variants
