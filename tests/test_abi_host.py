@@ -74,3 +74,21 @@ def test_tree_rejects_bad_input(hm):
         hm.ClusterTree(_NullCtx(), np.zeros((4, 2)), 1)  # duplicate points cannot be bisected
     with pytest.raises(hm.HmatError):
         hm.ClusterTree(_NullCtx(), np.zeros((4, 5)), 2)  # d must be 2 or 3
+
+
+@pytest.mark.parametrize("name,nargs", [
+    ("hmat_lu", 3), ("hmat_lu_batched", 4), ("hmat_invert", 3), ("hmat_cholesky", 3), ("hmat_addmul", 6),
+    ("hmat_solve", 6), ("hmat_addeval", 7), ("trunc_lowrank", 10), ("hmat_create_from_csr", 7),
+    ("hmat_clustertree_build", 6), ("hmat_blocktree_build", 5), ("hmat_copy_values", 3), ("hmat_to_dense", 3),
+    ("hmat_stats_get", 2), ("hmat_ranks", 2), ("hmat_mlp_create", 3), ("hmat_lu_training_data", 5),
+    ("hmat_analyze_lu", 7)])
+def test_null_arguments_return_a_status(hm, name, nargs):
+    """Every entry point checks its arguments on the host before touching a
+    device: null arguments give HMAT_ERR_ARG and a message, never a crash."""
+    import ctypes
+    L = hm.lib()
+    rc = getattr(L, name)(*([None] * nargs))
+    assert rc == hm.HMAT_ERR_ARG
+    buf = ctypes.create_string_buffer(256)
+    L.hmat_last_error(buf, ctypes.c_size_t(256))
+    assert buf.value
