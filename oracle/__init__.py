@@ -278,8 +278,13 @@ class HMatrix:
                                  ctypes.c_int(1 if trans else 0)))
         return Y
 
-    def lu(self, eps: float, accumulated: bool = True):
-        _check(lib().orc_hlu(self.h, ctypes.c_double(eps), ctypes.c_int(1 if accumulated else 0)))
+    def lu(self, eps: float, accumulated: bool = True, literal: bool = False):
+        """In place: H-LU, accumulated (Section 6 with the accumulators of
+        Section 4) or standard.  literal=True holds every accumulator in
+        low-rank form, as Section 4 states it, instead of keeping the blocks
+        with a leaf cluster dense."""
+        mode = (2 if literal else 1) if accumulated else 0
+        _check(lib().orc_hlu(self.h, ctypes.c_double(eps), ctypes.c_int(mode)))
 
     def cholesky(self, eps: float):
         """In place: H-Cholesky with accumulated updates; the lower blocks hold L
@@ -309,10 +314,11 @@ class HMatrix:
         return err.value, it.value
 
 
-def hmul(alpha: float, X: HMatrix, Y: HMatrix, Z: HMatrix, eps: float, accumulated: bool = True):
-    """Z <- blocktrunc(Z + alpha X Y) (Section 4)."""
-    _check(lib().orc_hmul(ctypes.c_double(alpha), X.h, Y.h, Z.h, ctypes.c_double(eps),
-                          ctypes.c_int(1 if accumulated else 0)))
+def hmul(alpha: float, X: HMatrix, Y: HMatrix, Z: HMatrix, eps: float, accumulated: bool = True,
+         literal: bool = False):
+    """Z <- blocktrunc(Z + alpha X Y) (Section 4); literal as in HMatrix.lu."""
+    mode = (2 if literal else 1) if accumulated else 0
+    _check(lib().orc_hmul(ctypes.c_double(alpha), X.h, Y.h, Z.h, ctypes.c_double(eps), ctypes.c_int(mode)))
 
 
 def setup(problem):

@@ -843,7 +843,21 @@ struct Acc {
   std::vector<Pending> P;
 };
 
+// The literal form of Section 4 (mode 2 of orc_hmul and orc_hlu): every
+// accumulator holds Rhat factorised, whatever its clusters, and each leaf case
+// of Fig. addproduct adds its product by rkadd, a truncation per product; the
+// flush then applies Rhat by rkupdate.  It is kept beside the default reading
+// (dense accumulators for blocks with a leaf cluster) so that the two can be
+// compared: they represent the same sum and differ by the extra truncations.
+static bool g_literal_acc = false;
+struct LiteralAccScope {
+  bool old;
+  explicit LiteralAccScope(bool on) : old(g_literal_acc) { g_literal_acc = on; }
+  ~LiteralAccScope() { g_literal_acc = old; }
+};
+
 static bool acc_is_dense(int t, int r, const CTree& RT, const CTree& CT) {
+  if (g_literal_acc) return false;
   return RT.nodes[(size_t)t].sons.empty() || CT.nodes[(size_t)r].sons.empty();
 }
 
@@ -1870,14 +1884,16 @@ int orc_addeval(void* h, double alpha, int64_t ncol, const double* X, double* Y,
 }
 
 // Z <- blocktrunc(Z + alpha X Y).  mode 1 = accumulated (addproduct at the
-// root, then flush), mode 0 = standard.
+// root, then flush), mode 2 = accumulated with the literal low-rank
+// accumulators of Section 4, mode 0 = standard.
 int orc_hmul(double alpha, void* X, void* Y, void* Z, double eps, int mode) {
   return guard([&] {
     TruncOpts o;
     o.eps = eps;
     HMat* Zm = (HMat*)Z;
+    LiteralAccScope lit(mode == 2);
     auto t0 = std::chrono::steady_clock::now();
-    if (mode == 1) {
+    if (mode >= 1) {
       Acc acc = acc_empty(0, 0, *Zm->bt->R, *Zm->bt->C);
       addproduct(alpha, *(HMat*)X, 0, *(HMat*)Y, 0, acc, o);
       flush(acc, target_of(Zm, 0), o);
@@ -1888,14 +1904,17 @@ int orc_hmul(double alpha, void* X, void* Y, void* Z, double eps, int mode) {
   });
 }
 
-// In-place H-LU: unit lower L and upper U share the H-matrix.
+// In-place H-LU: unit lower L and upper U share the H-matrix.  mode 1 =
+// accumulated, 2 = accumulated with the literal low-rank accumulators of
+// Section 4, 0 = standard.
 int orc_hlu(void* h, double eps, int mode) {
   return guard([&] {
     TruncOpts o;
     o.eps = eps;
     HMat* G = (HMat*)h;
+    LiteralAccScope lit(mode == 2);
     auto t0 = std::chrono::steady_clock::now();
-    if (mode == 1) {
+    if (mode >= 1) {
       Acc acc = acc_empty(0, 0, *G->bt->R, *G->bt->C);
       lu_acc(*G, 0, acc, o);
     } else {

@@ -257,3 +257,65 @@ def test_hinv_standard_and_accumulated_agree():
     assert np.linalg.norm(out[True][0] - out[False][0], 2) <= 10 * p.eps * np.linalg.norm(Ai, 2)
     assert out[True][1] <= 4 * out[False][1] and out[False][1] <= 4 * out[True][1]
     assert out[True][2] < out[False][2]
+
+
+# ---------------------------------------------------------------------------
+# The reading "dense accumulators for blocks with a leaf cluster" against the
+# literal low-rank accumulators of Section 4 (rkadd per addproduct leaf case)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("N,d,leaf", [(16, 2, 8), (8, 3, 16)])
+def test_literal_accumulators_exact_at_eps0(N, d, leaf):
+    """With eps = 0 the literal form loses nothing either: its H-LU is the
+    dense no-pivot LU of the permuted matrix."""
+    p = hs.small_laplace(N, d, leaf, 0.0)
+    ct, bt, csr, H = oracle.setup(p)
+    A = H.to_dense()
+    H.lu(0.0, True, literal=True)
+    ref = dense_lu_nopivot(A)
+    assert np.abs(H.to_dense() - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("N,d,leaf,eps", [(32, 2, 8, 1e-4), (8, 3, 16, 1e-4), (16, 2, 8, 1e-6)])
+def test_literal_accumulators_agree_with_dense_reading_lu(N, d, leaf, eps):
+    """Both accumulator forms represent the same sum (Section 4); they differ
+    by the truncations the literal one runs per product.  So the factors agree
+    to O(eps) and both preconditioner errors are O(eps).  The dense reading
+    replaces those truncations by exact sums: it truncates less often than the
+    literal form (and than the standard algorithm) and its error is no larger
+    than the literal form's (measured: 1.7x to 19x smaller on these grids) and
+    equal to the standard algorithm's within 1.5x."""
+    p = hs.small_laplace(N, d, leaf, eps)
+    out = {}
+    for mode in ("dense", "literal", "standard"):
+        ct, bt, csr, H = oracle.setup(p)
+        A = H.to_dense()
+        oracle.stats_reset()
+        H.lu(eps, mode != "standard", literal=mode == "literal")
+        out[mode] = (H.to_dense(), precond_error_dense(H.to_dense(), A), oracle.stats()["truncations"])
+    D0, e0, t0 = out["dense"]
+    D1, e1, t1 = out["literal"]
+    Ds, es, ts = out["standard"]
+    assert np.linalg.norm(D1 - D0, 2) <= 100 * eps * np.linalg.norm(D0, 2)
+    assert e0 <= 100 * eps and e1 <= 100 * eps
+    assert e0 <= 1.05 * e1
+    assert e0 <= 1.5 * es and es <= 1.5 * e0
+    assert t0 < ts < t1
+
+
+def test_literal_accumulators_agree_with_dense_reading_hmul():
+    """The same comparison for Z <- Z + X Y: both within O(eps) of the dense
+    product and of each other; the literal form truncates more often."""
+    ct, bt = trees(32, 2, 8)
+    X, Y = random_hmatrix(bt, 5, k=2), random_hmatrix(bt, 6, k=2)
+    ref = X.to_dense() @ Y.to_dense()
+    nrm = np.linalg.norm(ref, 2)
+    res, tr = {}, {}
+    for literal in (False, True):
+        Z = oracle.HMatrix.zero(bt)
+        oracle.stats_reset()
+        oracle.hmul(1.0, X, Y, Z, 1e-4, True, literal=literal)
+        tr[literal] = oracle.stats()["truncations"]
+        res[literal] = Z.to_dense()
+        assert np.linalg.norm(res[literal] - ref, 2) / nrm < 1e-3
+    assert np.linalg.norm(res[True] - res[False], 2) / nrm < 1e-3
+    assert tr[True] > tr[False]
