@@ -33,7 +33,7 @@ import hmat_synth as hs  # noqa: E402
 METRIC = "H-LU setup truncations/s (accumulated updates) vs plain FP64 at equal ||I-(LU)^-1 A||"
 UNIT = "truncations/s"
 TASK_NAMES = ["NOP", "LU", "TRSM", "HMV", "DENSIFY", "GEMM", "ADD", "RKADD", "ROWMERGE", "COPY", "ZERO", "RANKSET",
-              "INV"]
+              "INV", "CHOL"]
 FP64_PEAK_TFLOPS = 1.25     # GB300 nominal FP64 (vector and tensor) rate, 152 SMs at up to 2070 MHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 CUDA-core FMA rate: 152 SMs x 128 lanes x 2 x 2070 MHz
 WORKLOADS = {"laplace3d_32": hs.laplace3d_32, "laplace3d_64": hs.laplace3d_64, "laplace2d_64": hs.laplace2d_64,

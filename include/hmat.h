@@ -281,16 +281,19 @@ hmat_status trunc_lowrank_batched(hmat_ctx* ctx, int64_t count, const int64_t* m
 
 /* trunc_lowrank without any memory allocation (the paper has no counterpart:
  * this serves callers that cannot let the library allocate device memory,
- * e.g. code inside a CUDA graph capture, hosts that reserve all device memory
- * up front, or applications whose own pool owns the GPU).  Same arguments,
- * result and ld rules as trunc_lowrank (ld >= row count here).  Its scratch
+ * e.g. real-time hosts that reserve all device memory up front, where an
+ * allocation mid-run could fail or stall, or applications whose own pool owns
+ * the GPU and would lose track of memory taken behind its back).  Same
+ * arguments, result and ld rules as trunc_lowrank (row count <= ld <=
+ * 2^31 - 1 here; eps must be a number >= 0, else HMAT_ERR_ARG).  Its scratch
  * is a fixed 16 MiB device array compiled into the library, held by every GPU
  * that loads the library until exit; problems needing more than 2^21 - 32
  * doubles of scratch ((2m + n) k + 2 k^2) are rejected with HMAT_ERR_ARG.
  * The first call on a device looks the array's address up
- * (cudaGetSymbolAddress) and should come before any stream capture.  All
- * calls share the array, so calls that overlap on the GPU race: serialise them.
- * The call synchronises the context stream to return *k_new. */
+ * (cudaGetSymbolAddress) and should come before any stream capture begins
+ * on that device.  All calls share the array, so calls that overlap on the
+ * GPU race: serialise them.  The call synchronises the context stream to
+ * return *k_new. */
 hmat_status trunc_lowrank_noalloc(hmat_ctx* ctx, int64_t m, int64_t n, int64_t k, double* U, int64_t ldu, double* V,
                                   int64_t ldv, double eps, int64_t* k_new);
 

@@ -2310,7 +2310,6 @@ void lu_batch(hmat_ctx* ctx, hmat* const* Hs, int count, const hmat_opts* opts) 
     st.tasks = (int64_t)S.tasks.size();
     st.truncations = (int64_t)rr.truncations;
     st.flops = rr.flops;
-  st.flops32 = rr.flops32;
     st.flops32 = rr.flops32;
     st.rand_truncations = (int64_t)rr.rand_ok;
     st.rand_fallbacks = (int64_t)rr.rand_fail;

@@ -1,19 +1,22 @@
 // hmat_noalloc.cu -- truncation entry point that allocates no memory.
 //
-// Some callers cannot let a library allocate device memory: code running
-// inside a CUDA graph capture (where cudaMalloc is not allowed), real-time or
-// embedded hosts that reserve all device memory up front, and applications
-// whose own memory pool owns the whole GPU.  trunc_lowrank_noalloc serves
-// them: it does the same truncation as trunc_lowrank, but its scratch memory
-// is a fixed array compiled into the library instead of a cudaMalloc'ed
-// buffer.
+// Some callers cannot let a library allocate device memory: real-time or
+// embedded hosts that reserve all device memory up front (an allocation in
+// the middle of a run could fail or stall), and applications whose own memory
+// pool owns the whole GPU (memory taken behind the pool's back breaks its
+// accounting).  trunc_lowrank_noalloc serves them: it does the same
+// truncation as trunc_lowrank, but its scratch memory is a fixed array
+// compiled into the library instead of a cudaMalloc'ed buffer.  The call
+// reads the new rank back and synchronises the context stream before it
+// returns.
 //
 // The array is a file-scope __device__ variable of HM_NOALLOC_DOUBLES doubles
 // (16 MiB).  Every GPU that loads the library holds it until the process
 // exits, whether or not the entry point is used.  Host code cannot use the
 // array's name as a device address, so the first call on each device asks the
 // runtime for the address (cudaGetSymbolAddress, with that device current)
-// and caches it; that first call should come before any stream capture.
+// and caches it; that first call should come before any stream capture
+// begins on that device.
 // All calls share the one array: calls that overlap on the GPU (two streams,
 // or two host threads) race on it and must be serialised by the caller.
 #include <cuda_runtime.h>
@@ -102,8 +105,11 @@ hmat_status fail(hmat_status code, const std::string& msg) {
 extern "C" hmat_status trunc_lowrank_noalloc(hmat_ctx* ctx, int64_t m, int64_t n, int64_t k, double* U, int64_t ldu,
                                              double* V, int64_t ldv, double eps, int64_t* k_new) {
   if (!ctx || !U || !V || !k_new || m < 0 || n < 0 || k < 0 || ldu < std::max<int64_t>(m, 1) ||
-      ldv < std::max<int64_t>(n, 1) || eps < 0.0)
+      ldv < std::max<int64_t>(n, 1) || !(eps >= 0.0))
     return fail(HMAT_ERR_ARG, "trunc_lowrank_noalloc: bad arguments");
+  // the kernel indexes with 32-bit sizes and leading dimensions
+  if (ldu > INT32_MAX || ldv > INT32_MAX)
+    return fail(HMAT_ERR_ARG, "trunc_lowrank_noalloc: ldu and ldv must be at most 2^31 - 1");
   if (k > HM_LMAX) return fail(HMAT_ERR_ARG, "trunc_lowrank_noalloc: k must be <= 256");
   int64_t need = HM_NOALLOC_HEADER + (2 * m + n) * k + 2 * k * k;
   if (need > HM_NOALLOC_DOUBLES)

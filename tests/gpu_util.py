@@ -77,3 +77,20 @@ class GpuProblem:
             if done:
                 break
         return est
+
+
+def assert_matches_oracle(gp: GpuProblem, OH, rtol: float = 1e-10):
+    """The FP64 GPU result equals the oracle's entry by entry: every admissible
+    block has the oracle's rank (the block trees are the same, so the rank
+    vectors line up node by node) and the dense matrices agree to rtol
+    relative to the largest entry."""
+    rg = gp.H.ranks()
+    ro = OH.ranks()
+    assert rg.shape == ro.shape
+    diff = np.flatnonzero(rg != ro)
+    assert diff.size == 0, f"{diff.size} blocks differ in rank from the oracle (first {diff[:5]})"
+    D = gp.dense()
+    Do = OH.to_dense()
+    scale = np.abs(Do).max()
+    err = np.abs(D - Do).max()
+    assert err <= rtol * scale, f"max entry difference {err / scale:.3e} relative"

@@ -5,7 +5,7 @@ import pytest
 
 import hmat_synth as hs
 import oracle
-from gpu_util import GpuProblem, hm
+from gpu_util import GpuProblem, assert_matches_oracle, hm
 
 pytestmark = pytest.mark.gpu
 
@@ -22,7 +22,10 @@ def test_hchol_eps0_is_the_cholesky_factor(ctx):
     gp.H.cholesky(0.0)
     assert gp.H.stats()["status"] == 0
     Lr = np.linalg.cholesky(A)
-    assert np.abs(np.tril(gp.dense()) - Lr).max() <= 1e-10 * np.abs(Lr).max()
+    D = gp.dense()
+    assert np.abs(np.tril(D) - Lr).max() <= 1e-10 * np.abs(Lr).max()
+    # the upper blocks and upper triangles of the diagonal leaves hold L^T
+    assert np.abs(np.triu(D) - Lr.T).max() <= 1e-10 * np.abs(Lr).max()
 
 
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
@@ -41,3 +44,7 @@ def test_hchol_truncated_matches_oracle(ctx, shape, precision):
     Lo = np.tril(H.to_dense())
     err_orc = np.linalg.norm(np.eye(p.n) - np.linalg.solve(Lo @ Lo.T, A), 2)
     assert err_gpu <= 2.0 * err_orc and err_orc <= 2.0 * err_gpu
+    if precision == 0:
+        # FP64: the same truncations in the same order up to rounding, so the
+        # factor agrees with the oracle's entry by entry, L^T above included
+        assert_matches_oracle(gp, H)

@@ -5,7 +5,7 @@ import pytest
 
 import hmat_synth as hs
 import oracle
-from gpu_util import GpuProblem, from_dev, hm, to_dev
+from gpu_util import GpuProblem, assert_matches_oracle, from_dev, hm, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -58,17 +58,35 @@ def test_solve_after_exact_lu(ctx):
     assert np.abs(A.T @ from_dev(t) - b).max() <= 1e-10 * np.abs(b).max()
 
 
-def test_addeval_after_lu(ctx):
-    gp = GpuProblem(ctx, hs.small_laplace(32, 2, 16, 1e-6))
-    gp.H.lu(1e-6)
-    D = gp.dense()
+def test_addeval_after_lu_matches_oracle(ctx):
+    """Figs. addeval / addevaltrans on the H-LU factors: the GPU product equals
+    the oracle's addeval on the oracle's factors of the same matrix."""
+    p = hs.small_laplace(32, 2, 16, 1e-6)
+    gp = GpuProblem(ctx, p)
+    gp.H.lu(p.eps)
+    ct, bt, csr, OH = oracle.setup(p)
+    OH.lu(p.eps, True)
     X = hs.normal(5, 1024 * 4).reshape(1024, 4)
     Y0 = hs.normal(6, 1024 * 4).reshape(1024, 4)
     for trans in (False, True):
         y = to_dev(Y0)
         gp.H.addeval(-0.5, to_dev(X), y, trans=trans)
-        ref = Y0 - 0.5 * (D.T if trans else D) @ X
-        assert np.abs(from_dev(y) - ref).max() <= 1e-12 * np.abs(ref).max() * 10
+        ref = OH.addeval(-0.5, X, Y0, trans=trans)
+        assert np.abs(from_dev(y) - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("N,d,leaf,eps", [(16, 2, 8, 1e-4), (32, 2, 16, 1e-4), (8, 3, 16, 1e-4), (16, 3, 32, 1e-6)])
+def test_hlu_fp64_entries_match_oracle(ctx, N, d, leaf, eps):
+    """At eps > 0 the FP64 path runs the oracle's truncations in the oracle's
+    dependency order, so every admissible block gets the oracle's rank and the
+    factors agree entry by entry to 1e-10 relative."""
+    p = hs.small_laplace(N, d, leaf, eps)
+    gp = GpuProblem(ctx, p)
+    gp.H.lu(p.eps)
+    assert gp.H.stats()["status"] == 0
+    ct, bt, csr, OH = oracle.setup(p)
+    OH.lu(p.eps, True)
+    assert_matches_oracle(gp, OH)
 
 
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
