@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -118,12 +119,33 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def rank_problems(workload: str, rank: int):
+def instance_cost(n: int) -> float:
+    """Work model of one instance's H-LU for the partition: n log2(n)^2."""
+    return n * math.log2(max(n, 2)) ** 2
+
+
+def lpt_partition(costs, world: int):
+    """Greedy longest-processing-time assignment: instances in decreasing
+    cost, each to the rank with the least load so far (ties: lowest rank).
+    Returns the instance indices of every rank (ascending)."""
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    loads = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda q: (loads[q], q))
+        parts[r].append(i)
+        loads[r] += costs[i]
+    return [sorted(p) for p in parts]
+
+
+def rank_problems(workload: str, rank: int, world: int = 1):
     """This rank's problems.  A single H-LU does not shard, so every rank
-    factors a replica of it; the batch workload gives each rank its own
-    64 instances (seeds offset by 64 per rank), with no exchange."""
+    factors a replica of it.  The batch workload's 64 independent instances
+    are split over the ranks by LPT on n log2(n)^2, with no exchange."""
     if workload == "diffusion2d_batch64":
-        return hs.diffusion2d_batch(64, seed=2 + 64 * rank)
+        probs = hs.diffusion2d_batch(64, seed=2)
+        part = lpt_partition([instance_cost(p.n) for p in probs], world)[rank]
+        return [probs[i] for i in part]
     w = WORKLOADS[workload]()
     return w if isinstance(w, list) else [w]
 
@@ -163,8 +185,8 @@ def traffic_per_launch(workload: str):
 
 def workload_config(args, probs, world: int) -> dict:
     """The config object of both arms' JSON lines."""
-    par = (f"instances sharded: {world} rank(s) x 64 own instances" if args.workload == "diffusion2d_batch64"
-           else f"replicas{world}")
+    par = (f"instances sharded: 64 instances over {world} rank(s) by LPT on n log2(n)^2"
+           if args.workload == "diffusion2d_batch64" else f"replicas{world}")
     return {"workload": args.workload, "instances": len(probs), "n": sum(p.n for p in probs), "leaf": probs[0].leaf,
             "eta": probs[0].eta, "eps": probs[0].eps, "precision": args.precision,
             "max_rank": args.max_rank or 64, "l2": "flushed between steps (256 MiB write)",
@@ -250,7 +272,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
-    probs = rank_problems(args.workload, rank)
+    probs = rank_problems(args.workload, rank, world)
     eps = probs[0].eps
     assert all(p.eps == eps for p in probs)
     csrs = [p.matrix() for p in probs]
