@@ -6,10 +6,11 @@
 // sizes of the hot path); small square cores live in shared memory.
 //
 // Dense building blocks follow the textbook mathematics: Householder QR with
-// reflectors P = I - tau v v^T built from the column scaled by its largest
-// entry (so squared norms cannot under/overflow), one-sided Jacobi SVD
-// (Hestenes 1958; Demmel and Veselic 1992) with the parallel round-robin
-// ordering, no-pivot Gaussian elimination.
+// reflectors P = I - tau v v^T, v = x - alpha e_j (Golub and Van Loan,
+// Alg. 5.1.1; the column is scaled by its largest entry first where its
+// squares would leave the floating-point range), row-parallel over the CTA;
+// one-sided Jacobi SVD (Hestenes 1958; Demmel and Veselic 1992) with the
+// parallel round-robin ordering; no-pivot Gaussian elimination.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -19,7 +20,9 @@
 #define HM_THREADS 256
 #define HM_WARPS (HM_THREADS / 32)
 #define HM_LMAX 256            // largest stacked width of a truncation
-#define HM_JAC_SMEM 9216       // doubles of shared memory for the Jacobi core
+#ifndef HM_JAC_SMEM
+#define HM_JAC_SMEM 9216       // doubles of shared memory for the cores and staged panels
+#endif
 
 namespace hm {
 
@@ -34,6 +37,10 @@ struct Smem {
   double sigma[HM_LMAX];
   int order[HM_LMAX];
   int ivals[16];
+  // per-warp partial sums of the row-parallel FP32 factorisations (two
+  // buffers, used alternately so that one barrier per step suffices)
+  double redd[2][HM_WARPS * HM_LMAX];
+  double redm[2][2 * HM_WARPS];
   double jac[HM_JAC_SMEM];
 };
 
@@ -82,147 +89,12 @@ static __device__ __forceinline__ double block_max(double v, Smem& s) {
   return r;
 }
 
+// Set by set_status in the CTA whose error was the first recorded (the
+// executor clears it before each task and reports that task's index).
+static __shared__ int hm_status_won;
+
 static __device__ __forceinline__ void set_status(int* status, int code) {
-  atomicCAS(status, 0, code);
-}
-
-// ---------------------------------------------------------------------------
-// Householder QR in place: X (rows x cols, ld) -> reflectors v_j stored in
-// X(j:rows, j) (v scaled, first entry explicit), tau[j], R diagonal rdiag[j],
-// R(i, c) = X(i, c) for c > i.  q = min(rows, cols) reflectors.
-// ---------------------------------------------------------------------------
-static __device__ void cta_qr(double* X, int ld, int rows, int cols, double* tau, double* rdiag, Smem& s) {
-  int q = rows < cols ? rows : cols;
-  int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int j = 0; j < q; ++j) {
-    double* xj = X + (int64_t)j * ld;
-    double mx = 0.0;
-    for (int i = j + tid; i < rows; i += HM_THREADS) mx = fmax(mx, fabs(xj[i]));
-    mx = block_max(mx, s);
-    if (mx < 1e-290) {  // nothing left in this column (1/mx would overflow)
-      if (tid == 0) {
-        tau[j] = 0.0;
-        rdiag[j] = 0.0;
-      }
-      __syncthreads();
-      continue;
-    }
-    double inv = 1.0 / mx;
-    double tail = 0.0;
-    for (int i = j + 1 + tid; i < rows; i += HM_THREADS) {
-      double v = xj[i] * inv;
-      tail += v * v;
-    }
-    tail = block_sum(tail, s);
-    if (tid == 0) {
-      double v0 = xj[j] * inv;
-      double xn = sqrt(tail + v0 * v0);
-      double alpha = v0 >= 0.0 ? -xn : xn;
-      double v0n = v0 - alpha;
-      tau[j] = 2.0 / (tail + v0n * v0n);
-      rdiag[j] = alpha * mx;
-      s.bcast[0] = v0n;
-    }
-    __syncthreads();
-    for (int i = j + 1 + tid; i < rows; i += HM_THREADS) xj[i] *= inv;
-    if (tid == 0) xj[j] = s.bcast[0];
-    __syncthreads();
-    double tj = tau[j];
-    for (int c = j + 1 + warp; c < cols; c += HM_WARPS) {
-      double* xc = X + (int64_t)c * ld;
-      double d = 0.0;
-      for (int i = j + lane; i < rows; i += 32) d += xj[i] * xc[i];
-      d = warp_sum(d) * tj;
-      for (int i = j + lane; i < rows; i += 32) xc[i] -= d * xj[i];
-    }
-    __syncthreads();
-  }
-}
-
-// The same factorisation by warp 0 alone (no CTA barriers), for short
-// panels where barrier latency dominates.  The caller synchronises the CTA
-// before and after.  Butterfly (xor) reductions leave bit-identical sums on
-// every lane, so all lanes agree on every reflector.
-static __device__ void warp_qr(double* X, int ld, int rows, int cols, double* tau, double* rdiag) {
-  if ((threadIdx.x >> 5) != 0) return;
-  int lane = threadIdx.x & 31;
-  int q = rows < cols ? rows : cols;
-  for (int j = 0; j < q; ++j) {
-    double* xj = X + (int64_t)j * ld;
-    double mx = 0.0;
-    for (int i = j + lane; i < rows; i += 32) mx = fmax(mx, fabs(xj[i]));
-    mx = warp_max(mx);
-    if (mx < 1e-290) {  // nothing left in this column (1/mx would overflow)
-      if (lane == 0) {
-        tau[j] = 0.0;
-        rdiag[j] = 0.0;
-      }
-      __syncwarp();
-      continue;
-    }
-    double inv = 1.0 / mx;
-    double tail = 0.0;
-    for (int i = j + 1 + lane; i < rows; i += 32) {
-      double v = xj[i] * inv;
-      tail += v * v;
-    }
-    tail = warp_sum(tail);
-    double v0 = xj[j] * inv;
-    double xn = sqrt(tail + v0 * v0);
-    double alpha = v0 >= 0.0 ? -xn : xn;
-    double v0n = v0 - alpha;
-    double tj = 2.0 / (tail + v0n * v0n);
-    __syncwarp();
-    for (int i = j + 1 + lane; i < rows; i += 32) xj[i] *= inv;
-    if (lane == 0) {
-      xj[j] = v0n;
-      tau[j] = tj;
-      rdiag[j] = alpha * mx;
-    }
-    __syncwarp();
-    for (int c = j + 1; c < cols; ++c) {
-      double* xc = X + (int64_t)c * ld;
-      double d = 0.0;
-      for (int i = j + lane; i < rows; i += 32) d += xj[i] * xc[i];
-      d = warp_sum(d) * tj;
-      for (int i = j + lane; i < rows; i += 32) xc[i] -= d * xj[i];
-    }
-    __syncwarp();
-  }
-}
-
-// QR of a panel: warp-level for short panels, CTA-wide otherwise.
-static __device__ void panel_qr(double* X, int ld, int rows, int cols, double* tau, double* rdiag, Smem& s) {
-  if (rows <= 256) {
-    __syncthreads();
-    warp_qr(X, ld, rows, cols, tau, rdiag);
-    __syncthreads();
-  } else {
-    cta_qr(X, ld, rows, cols, tau, rdiag, s);
-  }
-}
-
-// Apply Q = P_0 P_1 ... P_{q-1} (reflectors of cta_qr stored in V) to the
-// matrix Y (rows x ncols, ld): Y <- Q Y.  Columns are independent, so each
-// warp applies every reflector (in reverse) to its own columns.
-static __device__ void cta_apply_q(const double* V, int ldv, int rows, int q, const double* tau, double* Y, int ldy,
-                            int ncols) {
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();
-  for (int c = warp; c < ncols; c += HM_WARPS) {
-    double* yc = Y + (int64_t)c * ldy;
-    for (int j = q - 1; j >= 0; --j) {
-      double tj = tau[j];
-      if (tj == 0.0) continue;
-      const double* vj = V + (int64_t)j * ldv;
-      double d = 0.0;
-      for (int i = j + lane; i < rows; i += 32) d += vj[i] * yc[i];
-      d = warp_sum(d) * tj;
-      for (int i = j + lane; i < rows; i += 32) yc[i] -= d * vj[i];
-      __syncwarp();
-    }
-  }
-  __syncthreads();
+  if (atomicCAS(status, 0, code) == 0) hm_status_won = 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -409,61 +281,396 @@ static __device__ void cta_jacobi_f(float* J, int p, int c, float* Vr, Smem& s, 
   }
 }
 
-// Householder QR of a float panel by the whole CTA: column j becomes the
-// reflector v_j (v_j[j] explicit, the rest below it, scaled by the column's
-// largest entry), tau[j] = 2 / (v_j . v_j), rdiag[j] the diagonal of R, the
-// part of R above the diagonal in place.  Warp 0 forms each reflector, every
-// warp applies it to its share of the remaining columns.
-static __device__ void cta_qr_f(float* X, int ld, int rows, int cols, double* tau, double* rdiag) {
+// ---------------------------------------------------------------------------
+// Row-parallel Householder factorisations (FP32 and FP64).  Row i of a panel
+// belongs to thread i mod HM_THREADS for the whole factorisation, so the
+// panel itself needs no barrier between steps; what crosses rows (the
+// column's largest entry and sum of squares, the products v^T x_c with the
+// trailing columns) is summed per warp and then over the warps in shared
+// memory.  Each thread works on up to HM_QCH columns at once, so a tall
+// panel in global memory has many independent loads in flight instead of one
+// dependent chain per warp.  Conventions: column j becomes the reflector v_j
+// (v_j[j] explicit, the rest below it), tau[j] = 2 / (v_j . v_j), rdiag[j]
+// the diagonal of R, R above the diagonal in place.
+// ---------------------------------------------------------------------------
+#define HM_QCH 8
+
+// first row >= j that belongs to this thread
+static __device__ __forceinline__ int own_row(int j) {
+  int t = threadIdx.x;
+  return t >= j ? t : t + ((j - t + HM_THREADS - 1) / HM_THREADS) * HM_THREADS;
+}
+
+template <class T>
+struct QrLimits;
+template <>
+struct QrLimits<float> {
+  static __device__ __forceinline__ float zero() { return 1e-30f; }  // nothing left in a column below this
+  static __device__ __forceinline__ float lo() { return 1e-10f; }    // squares safe between lo and hi
+  static __device__ __forceinline__ float hi() { return 1e15f; }
+};
+template <>
+struct QrLimits<double> {
+  static __device__ __forceinline__ double zero() { return 1e-290; }
+  static __device__ __forceinline__ double lo() { return 1e-140; }
+  static __device__ __forceinline__ double hi() { return 1e140; }
+};
+
+static __device__ __forceinline__ float wsum(float v) { return warp_sum_f(v); }
+static __device__ __forceinline__ double wsum(double v) { return warp_sum(v); }
+static __device__ __forceinline__ float wmax(float v) { return warp_max_f(v); }
+static __device__ __forceinline__ double wmax(double v) { return warp_max(v); }
+
+// reduction buffers of the row-parallel factorisations, typed
+template <class T>
+static __device__ __forceinline__ T* qr_red(Smem& s, int b) {
+  return reinterpret_cast<T*>(s.redd[b]);
+}
+template <class T>
+static __device__ __forceinline__ T* qr_redm(Smem& s, int b) {
+  return reinterpret_cast<T*>(s.redm[b]);
+}
+
+template <class T>
+struct Refl {
+  T tau, v0n, alpha;
+};
+
+// Reflector of column j from x0 = X(j, j) and the largest entry mx and the
+// sum of squares sq of the rows below j (both already summed over the CTA).
+// A column with nothing left gets tau = 0.  Entries so small (or so large)
+// that their squares leave the floating-point range are first scaled in
+// place by the column's largest entry (each thread its rows), with the sum
+// taken again.
+template <class T>
+static __device__ Refl<T> reflector_t(T* xj, int j, int rows, T x0, T mx, T sq, Smem& s) {
+  Refl<T> r;
+  T ma = fmax(mx, fabs(x0));
+  if (ma < QrLimits<T>::zero()) {
+    r.tau = T(0);
+    r.v0n = T(0);
+    r.alpha = T(0);
+    return r;
+  }
+  T scale = T(1);
+  if (ma < QrLimits<T>::lo() || ma > QrLimits<T>::hi()) {
+    T inv = T(1) / ma;
+    T t = T(0);
+    for (int i = own_row(j + 1); i < rows; i += HM_THREADS) {
+      T v = xj[i] * inv;
+      xj[i] = v;
+      t += v * v;
+    }
+    sq = (T)block_sum((double)t, s);
+    x0 *= inv;
+    scale = ma;
+  }
+  T xn = sqrt(sq + x0 * x0);
+  T alpha = x0 >= T(0) ? -xn : xn;
+  r.v0n = x0 - alpha;
+  r.tau = T(2) / (sq + r.v0n * r.v0n);
+  r.alpha = alpha * scale;
+  return r;
+}
+
+// Block totals of (max, sum of squares) partials through redm[b]; every
+// thread gets the totals.  One barrier.
+template <class T>
+static __device__ __forceinline__ void block_max_sq(T& pm, T& ps, int b, Smem& s) {
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T* rm = qr_redm<T>(s, b);
+  pm = wmax(pm);
+  ps = wsum(ps);
+  if (lane == 0) {
+    rm[warp] = pm;
+    rm[HM_WARPS + warp] = ps;
+  }
+  __syncthreads();
+  pm = T(0);
+  ps = T(0);
+#pragma unroll
+  for (int w = 0; w < HM_WARPS; ++w) {
+    pm = fmax(pm, rm[w]);
+    ps += rm[HM_WARPS + w];
+  }
+}
+
+// Per-warp partial products d_c = v_j . x_{c0 + cc} (rows >= j) of a chunk
+// of up to HM_QCH trailing columns into red (warp-major, HM_LMAX per warp).
+template <class T>
+static __device__ __forceinline__ void chunk_dots(const T* xj, T v0n, int j, int rows, const T* Xc, int ld, int nc,
+                                                  T* red, int slot) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T d[HM_QCH];
+#pragma unroll
+  for (int cc = 0; cc < HM_QCH; ++cc) d[cc] = T(0);
+  for (int i = own_row(j); i < rows; i += HM_THREADS) {
+    T v = i == j ? v0n : xj[i];
+    const T* xc = Xc + i;
+#pragma unroll
+    for (int cc = 0; cc < HM_QCH; ++cc)
+      if (cc < nc) d[cc] += v * xc[(int64_t)cc * ld];
+  }
+#pragma unroll
+  for (int cc = 0; cc < HM_QCH; ++cc) {
+    T t = wsum(d[cc]);
+    if (lane == 0 && cc < nc) red[warp * HM_LMAX + slot + cc] = t;
+  }
+}
+
+// Totals of a chunk's partial products, times tau.
+template <class T>
+static __device__ __forceinline__ void chunk_totals(const T* red, int slot, int nc, T tau, T* d) {
+#pragma unroll
+  for (int cc = 0; cc < HM_QCH; ++cc) {
+    T t = T(0);
+    if (cc < nc)
+#pragma unroll
+      for (int w = 0; w < HM_WARPS; ++w) t += red[w * HM_LMAX + slot + cc];
+    d[cc] = t * tau;
+  }
+}
+
+// Householder QR of a panel X (rows x cols, ld), row-parallel, two barriers
+// per column.  tau and rdiag may live in global or shared memory.
+template <class T>
+static __device__ void cta_qr_rows(T* X, int ld, int rows, int cols, double* tau, double* rdiag, Smem& s) {
+  int tid = threadIdx.x;
   int q = rows < cols ? rows : cols;
   __syncthreads();
-  for (int j = 0; j < q; ++j) {
-    float* xj = X + (int64_t)j * ld;
-    if (warp == 0) {
-      float mx = 0.f;
-      for (int i = j + lane; i < rows; i += 32) mx = fmaxf(mx, fabsf(xj[i]));
-      mx = warp_max_f(mx);
-      if (mx < 1e-30f) {  // nothing left in this column (1/mx would overflow FP32)
-        if (lane == 0) {
-          tau[j] = 0.0;
-          rdiag[j] = 0.0;
-        }
-      } else {
-        float inv = 1.f / mx;
-        float tail = 0.f;
-        for (int i = j + 1 + lane; i < rows; i += 32) {
-          float v = xj[i] * inv;
-          tail += v * v;
-        }
-        tail = warp_sum_f(tail);
-        float v0 = xj[j] * inv;
-        float xn = sqrtf(tail + v0 * v0);
-        float alpha = v0 >= 0.f ? -xn : xn;
-        float v0n = v0 - alpha;
-        float tj = 2.f / (tail + v0n * v0n);
-        __syncwarp();
-        for (int i = j + 1 + lane; i < rows; i += 32) xj[i] *= inv;
-        if (lane == 0) {
-          xj[j] = v0n;
-          tau[j] = tj;
-          rdiag[j] = (double)alpha * mx;
-        }
-      }
-    }
-    __syncthreads();
-    float tj = (float)tau[j];
-    if (tj != 0.f) {
-      for (int c = j + 1 + warp; c < cols; c += HM_WARPS) {
-        float* xc = X + (int64_t)c * ld;
-        float d = 0.f;
-        for (int i = j + lane; i < rows; i += 32) d += xj[i] * xc[i];
-        d = warp_sum_f(d) * tj;
-        for (int i = j + lane; i < rows; i += 32) xc[i] -= d * xj[i];
-      }
-    }
-    __syncthreads();
+  if (q <= 0) return;
+  T* red = qr_red<T>(s, 0);
+  T pm = T(0), ps = T(0);
+  for (int i = own_row(1); i < rows; i += HM_THREADS) {
+    T x = X[i];
+    pm = fmax(pm, fabs(x));
+    ps += x * x;
   }
+  T last_v0n = T(0);
+  bool last_pending = false;
+  for (int j = 0; j < q; ++j) {
+    T* xj = X + (int64_t)j * ld;
+    block_max_sq(pm, ps, j & 1, s);
+    Refl<T> r = reflector_t(xj, j, rows, xj[j], pm, ps, s);
+    if (tid == 0) {
+      tau[j] = (double)r.tau;
+      rdiag[j] = (double)r.alpha;
+    }
+    pm = T(0);
+    ps = T(0);
+    int nt = cols - j - 1;
+    if (r.tau != T(0) && nt > 0) {
+      for (int c0 = 0; c0 < nt; c0 += HM_QCH)
+        chunk_dots(xj, r.v0n, j, rows, X + (int64_t)(j + 1 + c0) * ld, ld, min(HM_QCH, nt - c0), red, c0);
+      __syncthreads();
+      for (int c0 = 0; c0 < nt; c0 += HM_QCH) {
+        int nc = min(HM_QCH, nt - c0);
+        T d[HM_QCH];
+        chunk_totals(red, c0, nc, r.tau, d);
+        T* Xc = X + (int64_t)(j + 1 + c0) * ld;
+        for (int i = own_row(j); i < rows; i += HM_THREADS) {
+          T v = i == j ? r.v0n : xj[i];
+#pragma unroll
+          for (int cc = 0; cc < HM_QCH; ++cc) {
+            if (cc < nc) {
+              T x = Xc[(int64_t)cc * ld + i] - d[cc] * v;
+              Xc[(int64_t)cc * ld + i] = x;
+              if (c0 + cc == 0 && i > j + 1) {
+                pm = fmax(pm, fabs(x));
+                ps += x * x;
+              }
+            }
+          }
+        }
+      }
+      if (own_row(j) == j) xj[j] = r.v0n;  // every thread has read X(j, j)
+    } else {
+      // a zero column (nothing to apply) or the last column: the next
+      // column's partials from its rows as they are; the last column's
+      // explicit first entry is written after the final barrier
+      if (j + 1 < q) {
+        const T* xn = X + (int64_t)(j + 1) * ld;
+        for (int i = own_row(j + 2); i < rows; i += HM_THREADS) {
+          T x = xn[i];
+          pm = fmax(pm, fabs(x));
+          ps += x * x;
+        }
+      }
+      last_pending = r.tau != T(0);
+      last_v0n = r.v0n;
+    }
+  }
+  __syncthreads();
+  if (last_pending && own_row(q - 1) == q - 1) X[(int64_t)(q - 1) * ld + q - 1] = last_v0n;
+  __syncthreads();
+}
+
+// Y (rows x k, ldy) <- P_0 P_1 ... P_{q-1} Y with the reflectors of a
+// row-parallel QR in V (tau as it left it), row-parallel: the reflectors are
+// applied in reverse order, one barrier each.
+template <class T>
+static __device__ void cta_apply_q_rows(const T* V, int ldv, int rows, int q, const double* tau, T* Y, int ldy, int k,
+                                        Smem& s) {
+  __syncthreads();
+  for (int j = q - 1; j >= 0; --j) {
+    T tj = (T)tau[j];
+    if (tj == T(0) || k <= 0) continue;
+    const T* vj = V + (int64_t)j * ldv;
+    T v0 = vj[j];
+    T* red = qr_red<T>(s, j & 1);
+    for (int c0 = 0; c0 < k; c0 += HM_QCH)
+      chunk_dots(vj, v0, j, rows, Y + (int64_t)c0 * ldy, ldy, min(HM_QCH, k - c0), red, c0);
+    __syncthreads();
+    for (int c0 = 0; c0 < k; c0 += HM_QCH) {
+      int nc = min(HM_QCH, k - c0);
+      T d[HM_QCH];
+      chunk_totals(red, c0, nc, tj, d);
+      T* Yc = Y + (int64_t)c0 * ldy;
+      for (int i = own_row(j); i < rows; i += HM_THREADS) {
+        T v = vj[i];
+#pragma unroll
+        for (int cc = 0; cc < HM_QCH; ++cc)
+          if (cc < nc) Yc[(int64_t)cc * ldy + i] -= d[cc] * v;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+static __device__ void cta_qr_f(float* X, int ld, int rows, int cols, double* tau, double* rdiag, Smem& s) {
+  cta_qr_rows<float>(X, ld, rows, cols, tau, rdiag, s);
+}
+static __device__ void cta_apply_qf(const float* V, int ldv, int rows, int q, const double* tau, float* Y, int ldy,
+                                    int k, Smem& s) {
+  cta_apply_q_rows<float>(V, ldv, rows, q, tau, Y, ldy, k, s);
+}
+
+// Q = P_0 ... P_{q-1} [I; 0] (rows x q, ld ldq) from the reflectors of a
+// row-parallel FP32 QR.
+static __device__ void form_q_f(const float* V, int ldv, int rows, int q, const double* tau, float* Q, int ldq,
+                                Smem& s) {
+  __syncthreads();
+  for (int c = 0; c < q; ++c)
+    for (int i = threadIdx.x; i < rows; i += HM_THREADS) Q[(int64_t)c * ldq + i] = (i == c) ? 1.f : 0.f;
+  cta_apply_qf(V, ldv, rows, q, tau, Q, ldq, q, s);
+}
+
+// Column-pivoted Householder QR of a float panel, X P = Q R, row-parallel
+// (conventions of cta_qr_f; perm[j] = the original column now at j).  The
+// pivot is the trailing column of largest remaining norm; those norms are
+// summed afresh at every step from the updated rows (no downdating), so
+// every thread takes the same pivot from the same shared sums.  Three
+// barriers per column.
+static __device__ void cta_qrcp_f(float* X, int ld, int rows, int cols, double* tau, double* rdiag, int* perm,
+                                  Smem& s) {
+  int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int q = rows < cols ? rows : cols;
+  float* dred = qr_red<float>(s, 0);  // partial products with the reflector
+  float* nred = qr_red<float>(s, 1);  // partial squared norms of the trailing columns
+  __syncthreads();
+  for (int c = tid; c < cols; c += HM_THREADS) perm[c] = c;
+  // squared norms of the whole columns
+  for (int c0 = 0; c0 < cols; c0 += HM_QCH) {
+    int nc = min(HM_QCH, cols - c0);
+    float d[HM_QCH];
+#pragma unroll
+    for (int cc = 0; cc < HM_QCH; ++cc) d[cc] = 0.f;
+    for (int i = tid; i < rows; i += HM_THREADS)
+#pragma unroll
+      for (int cc = 0; cc < HM_QCH; ++cc)
+        if (cc < nc) {
+          float x = X[(int64_t)(c0 + cc) * ld + i];
+          d[cc] += x * x;
+        }
+#pragma unroll
+    for (int cc = 0; cc < HM_QCH; ++cc) {
+      float t = wsum(d[cc]);
+      if (lane == 0 && cc < nc) nred[warp * HM_LMAX + c0 + cc] = t;
+    }
+  }
+  __syncthreads();
+  for (int j = 0; j < q; ++j) {
+    // pivot: the same scan of the same sums on every thread
+    int pv = j;
+    float best = -1.f;
+    for (int c = j; c < cols; ++c) {
+      float t = 0.f;
+#pragma unroll
+      for (int w = 0; w < HM_WARPS; ++w) t += nred[w * HM_LMAX + c];
+      if (t > best) {
+        best = t;
+        pv = c;
+      }
+    }
+    float* xj = X + (int64_t)j * ld;
+    float pm = 0.f, ps = 0.f;
+    if (pv != j) {
+      float* xp = X + (int64_t)pv * ld;
+      for (int i = tid; i < rows; i += HM_THREADS) {
+        float a = xj[i], b = xp[i];
+        xj[i] = b;
+        xp[i] = a;
+        if (i > j) {
+          pm = fmaxf(pm, fabsf(b));
+          ps += b * b;
+        }
+      }
+    } else {
+      for (int i = own_row(j + 1); i < rows; i += HM_THREADS) {
+        float x = xj[i];
+        pm = fmaxf(pm, fabsf(x));
+        ps += x * x;
+      }
+    }
+    block_max_sq(pm, ps, j & 1, s);  // also: every thread is past its pivot scan
+    if (tid == 0 && pv != j) {
+      int u = perm[j];
+      perm[j] = perm[pv];
+      perm[pv] = u;
+    }
+    Refl<float> r = reflector_t(xj, j, rows, xj[j], pm, ps, s);
+    if (tid == 0) {
+      tau[j] = r.tau;
+      rdiag[j] = r.alpha;
+    }
+    int nt = cols - j - 1;
+    if (r.tau != 0.f && nt > 0) {
+      for (int c0 = 0; c0 < nt; c0 += HM_QCH)
+        chunk_dots(xj, r.v0n, j, rows, X + (int64_t)(j + 1 + c0) * ld, ld, min(HM_QCH, nt - c0), dred, c0);
+      __syncthreads();
+    }
+    // update the trailing columns and sum their squared norms below row j
+    for (int c0 = 0; c0 < nt; c0 += HM_QCH) {
+      int nc = min(HM_QCH, nt - c0);
+      float d[HM_QCH], sq[HM_QCH];
+      if (r.tau != 0.f) chunk_totals(dred, c0, nc, r.tau, d);
+#pragma unroll
+      for (int cc = 0; cc < HM_QCH; ++cc) sq[cc] = 0.f;
+      float* Xc = X + (int64_t)(j + 1 + c0) * ld;
+      for (int i = own_row(j); i < rows; i += HM_THREADS) {
+        float v = i == j ? r.v0n : xj[i];
+#pragma unroll
+        for (int cc = 0; cc < HM_QCH; ++cc) {
+          if (cc < nc) {
+            float x = Xc[(int64_t)cc * ld + i];
+            if (r.tau != 0.f) {
+              x -= d[cc] * v;
+              Xc[(int64_t)cc * ld + i] = x;
+            }
+            if (i > j) sq[cc] += x * x;
+          }
+        }
+      }
+#pragma unroll
+      for (int cc = 0; cc < HM_QCH; ++cc) {
+        float t = wsum(sq[cc]);
+        if (lane == 0 && cc < nc) nred[warp * HM_LMAX + j + 1 + c0 + cc] = t;
+      }
+    }
+    __syncthreads();  // the next pivot scan reads the new sums
+    if (r.tau != 0.f && own_row(j) == j) xj[j] = r.v0n;
+  }
+  __syncthreads();
 }
 
 
@@ -562,7 +769,7 @@ static __device__ int trunc_core(const TruncIn& in, double eps, int cap, double*
   int qs = q[0] + (in.nb > 1 ? q[1] : 0);
   // tauB / rdiagB hold both blocks' reflectors at offsets qoff.
   for (int j = 0; j < in.nb; ++j)
-    panel_qr(in.SB[j], in.n[j], in.n[j], in.k[j], s.tauB + qoff[j], s.rdiagB + qoff[j], s);
+    cta_qr_rows<double>(in.SB[j], in.n[j], in.n[j], in.k[j], s.tauB + qoff[j], s.rdiagB + qoff[j], s);
   if (m == 0 || qs == 0) return 0;
   // Ahat = [SA_0 R_0^T, SA_1 R_1^T]  (m x qs)
   for (int j = 0; j < in.nb; ++j) {
@@ -578,7 +785,7 @@ static __device__ int trunc_core(const TruncIn& in, double eps, int cap, double*
   }
   __syncthreads();
   // QR of Ahat
-  panel_qr(in.W, m, m, qs, s.tauA, s.rdiagA, s);
+  cta_qr_rows<double>(in.W, m, m, qs, s.tauA, s.rdiagA, s);
   int qa = m < qs ? m : qs;
   // Jacobi core: case A (qa == qs): J = R_A (qs x qs); case B: J = R_A^T (qs x qa)
   bool caseA = (qa == qs);
@@ -656,10 +863,10 @@ static __device__ int trunc_core(const TruncIn& in, double eps, int cap, double*
     voff += nj;
   }
   __syncthreads();
-  cta_apply_q(in.W, m, m, qa, s.tauA, U, ldu, k);
+  cta_apply_q_rows<double>(in.W, m, m, qa, s.tauA, U, ldu, k, s);
   voff = 0;
   for (int j = 0; j < in.nb; ++j) {
-    cta_apply_q(in.SB[j], in.n[j], in.n[j], q[j], s.tauB + qoff[j], V + voff, ldv, k);
+    cta_apply_q_rows<double>(in.SB[j], in.n[j], in.n[j], q[j], s.tauB + qoff[j], V + voff, ldv, k, s);
     voff += in.n[j];
   }
   return k;
@@ -706,128 +913,6 @@ static __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-// Q = P_0 ... P_{q-1} [I; 0] (rows x q, ld ldq) from cta_qr_f / cta_qrcp_f reflectors;
-// each warp builds its own columns (P_j e_c needs only j <= c).
-static __device__ void form_q_f(const float* V, int ldv, int rows, int q, const double* tau, float* Q, int ldq) {
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();
-  for (int c = warp; c < q; c += HM_WARPS) {
-    float* qc = Q + (int64_t)c * ldq;
-    for (int i = lane; i < rows; i += 32) qc[i] = (i == c) ? 1.f : 0.f;
-    __syncwarp();
-    for (int j = c; j >= 0; --j) {
-      float tj = (float)tau[j];
-      if (tj == 0.f) continue;
-      const float* vj = V + (int64_t)j * ldv;
-      float d = 0.f;
-      for (int i = j + lane; i < rows; i += 32) d += vj[i] * qc[i];
-      d = warp_sum_f(d) * tj;
-      for (int i = j + lane; i < rows; i += 32) qc[i] -= d * vj[i];
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-}
-
-// Column-pivoted Householder QR of a float panel by the CTA, X P = Q R
-// (conventions of cta_qr_f; perm[j] = the original column now at j; nrm:
-// cols floats of scratch for the trailing column norms, recomputed after
-// each step rather than downdated).
-static __device__ void cta_qrcp_f(float* X, int ld, int rows, int cols, double* tau, double* rdiag, int* perm,
-                                  float* nrm, Smem& s) {
-  int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int q = rows < cols ? rows : cols;
-  for (int c = tid; c < cols; c += HM_THREADS) perm[c] = c;
-  for (int c = warp; c < cols; c += HM_WARPS) {
-    const float* xc = X + (int64_t)c * ld;
-    float d = 0.f;
-    for (int i = lane; i < rows; i += 32) d += xc[i] * xc[i];
-    d = warp_sum_f(d);
-    if (lane == 0) nrm[c] = d;
-  }
-  __syncthreads();
-  for (int j = 0; j < q; ++j) {
-    if (tid == 0) {
-      int pv = j;
-      float best = nrm[j];
-      for (int c = j + 1; c < cols; ++c)
-        if (nrm[c] > best) {
-          best = nrm[c];
-          pv = c;
-        }
-      s.ivals[10] = pv;
-    }
-    __syncthreads();
-    int pv = s.ivals[10];
-    if (pv != j) {
-      float* xa = X + (int64_t)j * ld;
-      float* xb = X + (int64_t)pv * ld;
-      for (int i = tid; i < rows; i += HM_THREADS) {
-        float t = xa[i];
-        xa[i] = xb[i];
-        xb[i] = t;
-      }
-      if (tid == 0) {
-        float t = nrm[j];
-        nrm[j] = nrm[pv];
-        nrm[pv] = t;
-        int u = perm[j];
-        perm[j] = perm[pv];
-        perm[pv] = u;
-      }
-    }
-    __syncthreads();
-    float* xj = X + (int64_t)j * ld;
-    if (warp == 0) {
-      float mx = 0.f;
-      for (int i = j + lane; i < rows; i += 32) mx = fmaxf(mx, fabsf(xj[i]));
-      mx = warp_max_f(mx);
-      if (mx < 1e-30f) {
-        if (lane == 0) {
-          tau[j] = 0.0;
-          rdiag[j] = 0.0;
-        }
-      } else {
-        float inv = 1.f / mx;
-        float tail = 0.f;
-        for (int i = j + 1 + lane; i < rows; i += 32) {
-          float v = xj[i] * inv;
-          tail += v * v;
-        }
-        tail = warp_sum_f(tail);
-        float v0 = xj[j] * inv;
-        float xn = sqrtf(tail + v0 * v0);
-        float alpha = v0 >= 0.f ? -xn : xn;
-        float v0n = v0 - alpha;
-        float tj = 2.f / (tail + v0n * v0n);
-        __syncwarp();
-        for (int i = j + 1 + lane; i < rows; i += 32) xj[i] *= inv;
-        if (lane == 0) {
-          xj[j] = v0n;
-          tau[j] = tj;
-          rdiag[j] = (double)alpha * mx;
-        }
-      }
-    }
-    __syncthreads();
-    float tj = (float)tau[j];
-    for (int c = j + 1 + warp; c < cols; c += HM_WARPS) {
-      float* xc = X + (int64_t)c * ld;
-      if (tj != 0.f) {
-        float d = 0.f;
-        for (int i = j + lane; i < rows; i += 32) d += xj[i] * xc[i];
-        d = warp_sum_f(d) * tj;
-        for (int i = j + lane; i < rows; i += 32) xc[i] -= d * xj[i];
-      }
-      float t = 0.f;
-      for (int i = j + 1 + lane; i < rows; i += 32) t += xc[i] * xc[i];
-      t = warp_sum_f(t);
-      if (lane == 0) nrm[c] = t;
-    }
-    __syncthreads();
-  }
-}
-
 // Orthonormal C for the kept part of a core_f32 result: the kept columns of
 // W (in decreasing order of norm) are factored Wk = Wh T (FP32 Householder,
 // Wh explicit in r x k), and Z = Vrot(:, kept) T^T (r x k, written over W),
@@ -841,8 +926,8 @@ static __device__ void core_f32_orth(float* cw, int r, int k, float* Wk, float* 
     int i = idx % r, jj = idx / r;
     Wk[idx] = W[i + (int64_t)s.order[jj] * r];
   }
-  cta_qr_f(Wk, r, r, k, s.tauA, s.rdiagA);
-  form_q_f(Wk, r, r, k, s.tauA, Wh, r);
+  cta_qr_f(Wk, r, r, k, s.tauA, s.rdiagA, s);
+  form_q_f(Wk, r, r, k, s.tauA, Wh, r, s);
   float* Z = cw;
   for (int idx = tid; idx < r * k; idx += HM_THREADS) {
     int j = idx % r, jj = idx / r;
@@ -870,7 +955,7 @@ static __device__ void core_f32(float* J, int p, int r, float* cw, Smem& s, int 
   float* Vrot = W + r * r;
   float* nrm = Vrot + r * r;
   int* perm = (int*)(nrm + r);
-  cta_qrcp_f(J, p, p, r, s.tauB, s.rdiagB, perm, nrm, s);
+  cta_qrcp_f(J, p, p, r, s.tauB, s.rdiagB, perm, s);
   // X = R^T: X[i][c] = R[c][i], nonzero for c <= i
   for (int idx = tid; idx < r * r; idx += HM_THREADS) {
     int i = idx % r, c = idx / r;
@@ -1001,10 +1086,10 @@ static __device__ int trunc_rand(const RandIn& in, double eps, int cap, double* 
     __syncthreads();
     // Q = orth(Y): Householder, then explicit Q = P_0 ... P_{r-1} [I; 0]
     int rr = r < m ? r : m;
-    panel_qr(Y, m, m, r, s.tauA, s.rdiagA, s);
+    cta_qr_rows<double>(Y, m, m, r, s.tauA, s.rdiagA, s);
     for (int idx = tid; idx < m * rr; idx += HM_THREADS) Qx[idx] = (idx % m == idx / m) ? 1.0 : 0.0;
     __syncthreads();
-    cta_apply_q(Y, m, m, rr, s.tauA, Qx, m, rr);
+    cta_apply_q_rows<double>(Y, m, m, rr, s.tauA, Qx, m, rr, s);
     // J = M^T Q (n x rr) in FP64
     if (!factored) {
       for (int idx = tid; idx < n * rr; idx += HM_THREADS) {
@@ -1045,7 +1130,7 @@ static __device__ int trunc_rand(const RandIn& in, double eps, int cap, double* 
       }
       jn2 = block_sum(a2, s);
       core_f32(Jf, n, rr, cw, s, HM_CORE_SWEEPS);
-      form_q_f(Jf, n, n, rr, s.tauB, Qj, n);
+      form_q_f(Jf, n, n, rr, s.tauB, Qj, n, s);
       count_f32(s, 4.0 * n * rr * rr + 12.0 * rr * (double)s.ivals[3]);
       f += 2.0 * n * rr;
     } else {
@@ -1223,7 +1308,9 @@ static __device__ void cta_gemm32(TC* C, int ldc, int m, int n, int kk, double a
   __syncthreads();
 }
 
-#define HM_F32_SMEM 12160  // floats of s.jac the FP32 work space may use
+// floats of s.jac the FP32 work space may use (the rest: the core's W, Vrot,
+// norms and permutation, then the staging of cta_gemm32)
+#define HM_F32_SMEM ((2 * HM_JAC_SMEM - 6400) & ~127)
 // after it: the core's W, Vrot, norms, permutation (2 RMAX^2 + 2 RMAX floats),
 // then the staging of cta_gemm32 (HM_G32_SMEM floats), up to the end of s.jac
 #define HM_F32_STAGE (HM_F32_SMEM + 2 * HM_RMAX * HM_RMAX + 2 * HM_RMAX)
@@ -1276,8 +1363,8 @@ static __device__ int trunc_rand32(const float* M, int m, int n, double scale, f
       Y[(int64_t)j * m + i] = a;
     }
     __syncthreads();
-    cta_qr_f(Y, m, m, r, s.tauA, s.rdiagA);
-    form_q_f(Y, m, m, r, s.tauA, Qf, m);
+    cta_qr_f(Y, m, m, r, s.tauA, s.rdiagA, s);
+    form_q_f(Y, m, m, r, s.tauA, Qf, m, s);
     // J = M^T Q (tiled FP32 product)
     cta_gemm32(J, n, n, r, m, 1.0, M, m, true, Qf, m, false, true, (float*)s.jac + HM_F32_STAGE);
     // sketch, QR and Q of the sketch, J, residual
@@ -1304,7 +1391,7 @@ static __device__ int trunc_rand32(const float* M, int m, int n, double scale, f
     __syncthreads();
     float* cw = (float*)(s.jac + HM_F32_SMEM / 2);  // 2 r^2 + 2 r floats
     core_f32(Jq, n, r, cw, s, HM_CORE_SWEEPS);
-    form_q_f(Jq, n, n, r, s.tauB, J, n);
+    form_q_f(Jq, n, n, r, s.tauB, J, n, s);
     // pivoted QR, Q_J, rotations (12 r per rotation: dots and updates)
     count_f32(s, 4.0 * n * r * r + 12.0 * r * (double)s.ivals[3]);
     if (tid == 0) {
@@ -1384,7 +1471,7 @@ static __device__ int trunc_fact32(int m, int n, int l, const float* SAf, float*
   double* tq = ds;
   double* rq = ds + l;
   double* Vh = ds + 2 * l;  // l x k (ld l)
-  cta_qr_f(SBf, n, n, l, tq, rq);
+  cta_qr_f(SBf, n, n, l, tq, rq, s);
   count_f32(s, 2.0 * n * l * l + (double)m * l * l);  // QR of SB, Mhat
   float sm = 0.f, sabs = 0.f;
   for (int idx = tid; idx < m * l; idx += HM_THREADS) {
@@ -1437,35 +1524,35 @@ static __device__ int trunc_fact32(int m, int n, int l, const float* SAf, float*
     }
     __syncthreads();
     int k = s.ivals[4];
-    float* QJ = pan;  // m x l
-    form_q_f(Mh, m, m, l, s.tauB, QJ, m);
-    form_q_f(SBf, n, n, l, tq, QB, n);
+    // C = Q_J [Vrot(:, order); 0] and D = Q_B [P W(:, order); 0] S: the
+    // reflectors applied to the k kept columns (m x k in pan, n x k in QB)
     const float* W = cw;
     const float* Vrot = cw + l * l;
     const int* perm = (const int*)(cw + 2 * l * l + l);
+    float* Cf = (float*)SAf;  // SAf is dead once Mhat is formed
+    float* Df = QB;
     for (int idx = tid; idx < m * k; idx += HM_THREADS) {
       int i = idx % m, jj = idx / m;
-      const float* vc = Vrot + (int64_t)s.order[jj] * l;
-      float a = 0.f;
-      for (int j = 0; j < l; ++j) a += QJ[(int64_t)j * m + i] * vc[j];
-      U[(int64_t)jj * ldu + i] = (double)a;
+      Cf[idx] = i < l ? Vrot[(int64_t)s.order[jj] * l + i] : 0.f;
     }
-    for (int idx = tid; idx < n * k; idx += HM_THREADS) {
-      int c = idx % n, jj = idx / n;
-      const float* wc = W + (int64_t)s.order[jj] * l;
-      float a = 0.f;
-      for (int j = 0; j < l; ++j) a += QB[(int64_t)perm[j] * n + c] * wc[j];
-      V[(int64_t)jj * ldv + c] = (double)a * S;
+    for (int idx = tid; idx < n * k; idx += HM_THREADS) Df[idx] = 0.f;
+    __syncthreads();
+    for (int idx = tid; idx < l * k; idx += HM_THREADS) {
+      int j = idx % l, jj = idx / l;
+      Df[(int64_t)jj * n + perm[j]] = W[(int64_t)s.order[jj] * l + j];
     }
-    count_f32(s, 2.0 * m * l * l + 12.0 * l * (double)s.ivals[3] + 4.0 * (m + n) * (double)l * l +
-                     2.0 * (m + n) * (double)l * k);
+    cta_apply_qf(Mh, m, m, l, s.tauB, Cf, m, k, s);
+    cta_apply_qf(SBf, n, n, l, tq, Df, n, k, s);
+    for (int idx = tid; idx < m * k; idx += HM_THREADS) U[(int64_t)(idx / m) * ldu + idx % m] = (double)Cf[idx];
+    for (int idx = tid; idx < n * k; idx += HM_THREADS) V[(int64_t)(idx / n) * ldv + idx % n] = (double)Df[idx] * S;
+    count_f32(s, 2.0 * m * l * l + 12.0 * l * (double)s.ivals[3] + 4.0 * (m + n) * (double)l * k);
     __syncthreads();
     *ok = 1;
     return k;
   }
   int k = trunc_rand32(Mh, m, l, S, pan, Om, eps, cap, U, ldu, Vh, l, status, s, flops, ok, seed, r0);
   if (!*ok) return 0;
-  form_q_f(SBf, n, n, l, tq, QB, n);
+  form_q_f(SBf, n, n, l, tq, QB, n, s);
   count_f32(s, 2.0 * n * l * l + 2.0 * n * (double)l * k);  // Q_B, D = Q_B Dhat
   for (int idx = tid; idx < n * k; idx += HM_THREADS) {
     int c = idx % n, jj = idx / n;
@@ -1480,6 +1567,62 @@ static __device__ int trunc_fact32(int m, int n, int l, const float* SAf, float*
 // Scratch of trunc_fact32 past the FP32 factor copies: floats, then doubles.
 __host__ __device__ inline int64_t fact32_floats(int64_t m, int64_t n, int64_t l) {
   return m * l + n * l + 2 * (m + l) * HM_RMAX + l + 2;
+}
+
+// FP32 factored truncation of M = SA [blockdiag(SB0, SB1)]^T (m x n, n = n0 +
+// n1, l = k0 + k1 <= min(m, n); SB1 may be null): the factors are copied to
+// FP32, each scaled by its largest entry, then trunc_fact32.  ws: the float
+// copies and trunc_fact32's scratch (or shared memory, for the direct path
+// when it all fits).  Returns the rank; *ok = 0 when the caller must fall
+// back to the exact truncation; *S_out = the scale of M.
+static __device__ int fact32_run(int m, int n, int l, const double* SA, const double* SB0, int n0, int k0,
+                                 const double* SB1, int n1, int k1, double* ws, double eps, int cap, double* U, int ldu,
+                                 double* V, int ldv, int* status, Smem& s, uint64_t seed, int r0, double* f, int* ok,
+                                 double* S_out) {
+  int tid = threadIdx.x;
+  *ok = 0;
+  *S_out = 0.0;
+  double ma = 0.0, mb = 0.0;
+  for (int idx = tid; idx < m * l; idx += HM_THREADS) ma = fmax(ma, fabs(SA[idx]));
+  for (int idx = tid; idx < n0 * k0; idx += HM_THREADS) mb = fmax(mb, fabs(SB0[idx]));
+  for (int idx = tid; idx < n1 * k1; idx += HM_THREADS) mb = fmax(mb, fabs(SB1[idx]));
+  ma = block_max(ma, s);
+  mb = block_max(mb, s);
+  double S = ma * mb;
+  *S_out = S;
+  if (!(S > 0.0) || !isfinite(S)) return 0;
+  float* SAf = (float*)ws;
+  float* SBf = SAf + (int64_t)m * l;
+  float* fs = SBf + (int64_t)n * l;
+  int64_t nf = (int64_t)m * l + (int64_t)n * l + fact32_floats(m, n, l);
+  double* ds = ws + (nf + 1) / 2;
+  // The direct path (no sketch) with everything in shared memory when it
+  // fits: the core's W, Vrot, norms and permutation at the start of s.jac,
+  // then SAf (later C), SBf, Mhat, Q_B's columns (later D), the QR's tau and
+  // R diagonal.
+  int64_t cwsz = (2 * (int64_t)l * l + 2 * l + 3) & ~(int64_t)3;
+  int64_t panel = 2 * (int64_t)(m + n) * l;
+  if (l <= HM_FACT32_DIRECT && l <= m && cwsz + panel + 4 * l + 8 <= 2 * (int64_t)HM_JAC_SMEM) {
+    SAf = (float*)s.jac + cwsz;
+    SBf = SAf + (int64_t)m * l;
+    fs = SBf + (int64_t)n * l;
+    ds = (double*)(((uintptr_t)(fs + (int64_t)(m + n) * l) + 7) & ~(uintptr_t)7);
+  }
+  double ia = 1.0 / ma, ib = 1.0 / mb;
+  for (int idx = tid; idx < m * l; idx += HM_THREADS) SAf[idx] = (float)(SA[idx] * ia);
+  for (int idx = tid; idx < n * l; idx += HM_THREADS) {
+    int c = idx % n, j = idx / n;
+    double v = 0.0;
+    if (j < k0) {
+      if (c < n0) v = SB0[(int64_t)j * n0 + c];
+    } else if (c >= n0) {
+      v = SB1[(int64_t)(j - k0) * n1 + (c - n0)];
+    }
+    SBf[idx] = (float)(v * ib);
+  }
+  __syncthreads();
+  int guard = 0;
+  return trunc_fact32(m, n, l, SAf, SBf, S, fs, ds, eps, cap, U, ldu, V, ldv, status, s, f, ok, &guard, seed, r0);
 }
 
 // Doubles of scratch trunc_rand needs.

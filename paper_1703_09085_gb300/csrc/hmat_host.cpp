@@ -263,6 +263,7 @@ struct hmat {
   std::shared_ptr<SchedCache> cache;  // schedule kept by hmat_lu(reuse_schedule)
   std::vector<float> train;           // training pairs recorded by the last hmat_lu
   hmat_ctx* ctx = nullptr;
+  int device = 0;                  // the context's device (the context may go first)
   const hmat_btree* bt = nullptr;
   int64_t n = 0;
   int64_t max_rank = DEFAULT_MAX_RANK;
@@ -1615,6 +1616,7 @@ struct RunResult {
   unsigned long long type_ns[16] = {0}, type_cnt[16] = {0}, wait_ns = 0;
   unsigned long long rand_ok = 0, rand_fail = 0, sketch_attempts = 0, sketch_cols = 0;
   unsigned long long bad[6] = {0, 0, 0, 0, 0, 0};
+  long long fail_task = -1;  // task that recorded the device status first (-1: none)
   std::vector<uint32_t> task_ns;  // filled when profiling
   std::vector<uint32_t> task_aux;
 };
@@ -1665,6 +1667,34 @@ void critical_path(const Sched& S, const std::vector<uint32_t>& ns, const std::v
                    a >> 24);
   }
   if (f) std::fclose(f);
+}
+
+const char* task_name(int type) {
+  static const char* names[] = {"NOP", "leaf LU", "leaf TRSM", "H x thin dense", "densify", "GEMM", "add",
+                                "rkadd", "rowmerge", "copy", "zero", "rankset", "leaf inverse", "leaf Cholesky"};
+  return type >= 0 && type < 14 ? names[type] : "?";
+}
+
+// " in task i (kind, sizes)" and, for a dense diagonal leaf task, the
+// block-tree node of that leaf: the context of a device status.
+std::string describe_failure(const Sched& S, long long ft, hmat* const* Hs, int count, const double* base) {
+  if (ft < 0 || ft >= (long long)S.tasks.size()) return "";
+  const HTask& t = S.tasks[(size_t)ft];
+  std::string out = " in task " + std::to_string(ft) + " (" + task_name(t.type) + ", " + std::to_string(t.m) + " x " +
+                    std::to_string(t.type == T_LU || t.type == T_CHOL || t.type == T_INV ? t.m : t.n) + ")";
+  if ((t.type == T_LU || t.type == T_CHOL || t.type == T_INV) && t.a >= 0 && ((t.a >> 60) & 3) == 0) {
+    for (int i = 0; i < count; ++i) {
+      int64_t hoff = (int64_t)(Hs[i]->store.as<double>() - base);
+      for (size_t b = 0; b < Hs[i]->bt->nodes.size(); ++b)
+        if (Hs[i]->kind((int)b) == 1 && Hs[i]->loc[b] + hoff == t.a) {
+          const CNodeH& c = Hs[i]->tc((int)b);
+          out += ": dense diagonal leaf, block-tree node " + std::to_string(b) + (count > 1 ? " of matrix " + std::to_string(i) : "") +
+                 ", permuted rows " + std::to_string(c.off) + ".." + std::to_string(c.off + c.size - 1);
+          return out;
+        }
+    }
+  }
+  return out;
 }
 
 // A schedule uploaded to the device, with its scratch arena.
@@ -1718,6 +1748,7 @@ RunResult launch_sched(hmat_ctx* ctx, const Sched& S, DevSched& D, double* hbase
   e.head = (unsigned long long*)dmp;
   e.counters = (unsigned long long*)dmp + 44;
   e.status = (int*)((unsigned long long*)dmp + 2);
+  e.fail_task = (long long*)dmp + 5;
   e.flops = (double*)((unsigned long long*)dmp + 3);
   e.flops32 = (double*)((unsigned long long*)dmp + 4);
   e.type_ns = (unsigned long long*)dmp + 8;
@@ -1793,6 +1824,7 @@ RunResult launch_sched(hmat_ctx* ctx, const Sched& S, DevSched& D, double* hbase
                        cudaMemcpyDeviceToHost));
   }
   rr.status = (int)(misc[2] & 0xffffffffu);
+  rr.fail_task = (long long)misc[5] - 1;
   std::memcpy(&rr.flops, &misc[3], sizeof(double));
   std::memcpy(&rr.flops32, &misc[4], sizeof(double));
   return rr;
@@ -2043,6 +2075,7 @@ hmat_status hmat_create_from_csr(hmat_ctx* ctx, const hmat_btree* bt, int64_t n,
     require((int64_t)bt->R->perm.size() == n && (int64_t)bt->C->perm.size() == n, "csr: size does not match the trees");
     std::unique_ptr<hmat> H(new hmat());
     H->ctx = ctx;
+    H->device = ctx->device;
     std::vector<DenseLeafDesc> dl = layout_from_csr(H.get(), bt, n, rowptr, colidx, val);
     int64_t off = H->store_doubles;
     size_t nb = bt->nodes.size();
@@ -2062,15 +2095,17 @@ hmat_status hmat_create_from_csr(hmat_ctx* ctx, const hmat_btree* bt, int64_t n,
     upload(dperm, perm, st);
     upload(diperm, iperm, st);
     upload(ddl, dl, st);
-    dplaced.alloc(sizeof(unsigned long long));
-    HM_CUDA(cudaMemsetAsync(dplaced.p, 0, sizeof(unsigned long long), st));
+    dplaced.alloc(2 * sizeof(unsigned long long));
+    HM_CUDA(cudaMemsetAsync(dplaced.p, 0, 2 * sizeof(unsigned long long), st));
     HM_CUDA(launch_csr_scatter(ddl.as<DenseLeafDesc>(), (int)dl.size(), drp.as<int64_t>(), dci.as<int64_t>(),
                                dva.as<double>(), dperm.as<int64_t>(), diperm.as<int64_t>(), H->store.as<double>(),
                                dplaced.as<unsigned long long>(), st));
-    unsigned long long placed = 0;
-    HM_CUDA(cudaMemcpyAsync(&placed, dplaced.p, sizeof(placed), cudaMemcpyDeviceToHost, st));
+    unsigned long long placed[2] = {0, 0};
+    HM_CUDA(cudaMemcpyAsync(placed, dplaced.p, sizeof(placed), cudaMemcpyDeviceToHost, st));
     HM_CUDA(cudaStreamSynchronize(st));
-    require((int64_t)placed == nnz, "csr: entries inside admissible blocks (rank > 0) are not supported");
+    require((int64_t)placed[0] == nnz, "csr: entries inside admissible blocks (rank > 0) are not supported");
+    if (placed[1])
+      throw HmError(HMAT_ERR_NONFINITE, "csr: " + std::to_string(placed[1]) + " non-finite values");
     (void)nb;
     H->st.device_bytes = (int64_t)(H->store.bytes + H->ranks.bytes);
     *out = H.release();
@@ -2079,8 +2114,11 @@ hmat_status hmat_create_from_csr(hmat_ctx* ctx, const hmat_btree* bt, int64_t n,
 
 hmat_status hmat_destroy(hmat* H) {
   return guarded([&] {
-    if (H && H->ctx) cudaSetDevice(H->ctx->device);
+    // the context may already be gone: use the device recorded at creation,
+    // and leave no error of this call behind for a later launch check
+    if (H) cudaSetDevice(H->device);
     delete H;
+    (void)cudaGetLastError();
   });
 }
 
@@ -2331,7 +2369,9 @@ void lu_batch(hmat_ctx* ctx, hmat* const* Hs, int count, const hmat_opts* opts) 
     st.est_flops = S.est_total;
     st.device_bytes = (int64_t)(Hs[i]->store.bytes + Hs[i]->ranks.bytes) + S.ws_top * 8;
   }
-  if (rr.status) throw HmError(rr.status, "hmat_lu: device status " + std::to_string(rr.status));
+  if (rr.status)
+    throw HmError(rr.status, "hmat_lu: device status " + std::to_string(rr.status) +
+                                 describe_failure(S, rr.fail_task, Hs, count, base));
 }
 
 // In-place H-Cholesky with accumulated updates: one schedule, one launch.
@@ -2394,7 +2434,11 @@ void chol_run(hmat_ctx* ctx, hmat* G, const hmat_opts* opts) {
   st.critical_flops = S.critical_flops();
   st.est_flops = S.est_total;
   st.device_bytes = (int64_t)(G->store.bytes + G->ranks.bytes) + S.ws_top * 8;
-  if (rr.status) throw HmError(rr.status, "hmat_cholesky: device status " + std::to_string(rr.status));
+  if (rr.status) {
+    hmat* Gs[1] = {G};
+    throw HmError(rr.status, "hmat_cholesky: device status " + std::to_string(rr.status) +
+                                 describe_failure(S, rr.fail_task, Gs, 1, G->store.as<double>()));
+  }
 }
 
 // In-place H-inversion with accumulated updates (Fig. invert): the auxiliary
@@ -2410,6 +2454,7 @@ void invert_run(hmat_ctx* ctx, hmat* G, const hmat_opts* opts) {
   // auxiliary H-matrix: the layout of G, all leaves zero
   std::unique_ptr<hmat> H(new hmat());
   H->ctx = ctx;
+  H->device = ctx->device;
   {
     std::vector<int64_t> rp((size_t)G->n + 1, 0);
     int64_t dummy_i = 0;
@@ -2609,6 +2654,15 @@ hmat_status hmat_solve(hmat_ctx* ctx, const hmat* LU, int trans, int64_t nrhs, d
   });
 }
 
+// Extra scratch (doubles) of one problem of trunc_lowrank_batched in the
+// mixed form: the explicit FP32 path (M, sketch panels, signs) or the
+// factored one (FP32 copies, Mhat, Q_B, panels; tau, R diagonal, core).
+static int64_t mixed_ws(int64_t m, int64_t n, int64_t l) {
+  int64_t expl = (m * n + 2 * (m + n) * RMAX + n) / 2 + 64;
+  int64_t fact = (2 * (m + n) * l + 2 * (m + l) * RMAX + l + 3) / 2 + 2 * l + l * RMAX + 64;
+  return std::max(expl, fact);
+}
+
 hmat_status trunc_lowrank_batched(hmat_ctx* ctx, int64_t count, const int64_t* m, const int64_t* n, const int64_t* k,
                                   double* const* U, double* const* V, double eps, int64_t* k_new, int precision,
                                   int64_t* randomised) {
@@ -2620,8 +2674,7 @@ hmat_status trunc_lowrank_batched(hmat_ctx* ctx, int64_t count, const int64_t* m
     std::vector<TruncProblem> P((size_t)count);
     for (int64_t i = 0; i < count; ++i) {
       require(m[i] >= 0 && n[i] >= 0 && k[i] >= 0 && k[i] <= HM_LMAX_HOST, "trunc_lowrank: k must be <= 256");
-      total += (2 * m[i] + n[i]) * k[i] + 2 * k[i] * k[i] + 64;
-      if (precision == HMAT_MIXED) total += (m[i] * n[i] + 2 * (m[i] + n[i]) * RMAX + n[i]) / 2 + 64;
+      total += (2 * m[i] + n[i]) * k[i] + 2 * k[i] * k[i] + 64 + (precision == HMAT_MIXED ? mixed_ws(m[i], n[i], k[i]) : 0);
     }
     DevBuf ws((size_t)total * sizeof(double));
     int64_t off = 0;
@@ -2636,8 +2689,7 @@ hmat_status trunc_lowrank_batched(hmat_ctx* ctx, int64_t count, const int64_t* m
       p.V = V[i];
       p.ws = ws.as<double>() + off;
       p.k_new = k_new + i;
-      off += (2 * m[i] + n[i]) * k[i] + 2 * k[i] * k[i] + 64;
-      if (precision == HMAT_MIXED) off += (m[i] * n[i] + 2 * (m[i] + n[i]) * RMAX + n[i]) / 2 + 64;
+      off += (2 * m[i] + n[i]) * k[i] + 2 * k[i] * k[i] + 64 + (precision == HMAT_MIXED ? mixed_ws(m[i], n[i], k[i]) : 0);
     }
     DevBuf dp, dst(2 * sizeof(int));
     upload(dp, P, ctx->stream);

@@ -406,37 +406,9 @@ __device__ void task_densify(const ExecEnv& e, const HTask& t, Smem& s) {
 __device__ int task_fact32(const ExecEnv& e, const HTask& t, Smem& s, int m, int n, int l, const double* SA,
                            const double* SB0, int n0, int k0, const double* SB1, int n1, int k1, double* ws,
                            uint64_t seed, int r0, double* f, int* ok) {
-  int tid = threadIdx.x;
-  *ok = 0;
-  double ma = 0.0, mb = 0.0;
-  for (int idx = tid; idx < m * l; idx += HM_THREADS) ma = fmax(ma, fabs(SA[idx]));
-  for (int idx = tid; idx < n0 * k0; idx += HM_THREADS) mb = fmax(mb, fabs(SB0[idx]));
-  for (int idx = tid; idx < n1 * k1; idx += HM_THREADS) mb = fmax(mb, fabs(SB1[idx]));
-  ma = block_max(ma, s);
-  mb = block_max(mb, s);
-  double S = ma * mb;
-  if (!(S > 0.0) || !isfinite(S)) return 0;
-  float* SAf = (float*)ws;
-  float* SBf = SAf + (int64_t)m * l;
-  float* fs = SBf + (int64_t)n * l;
-  int64_t nf = (int64_t)m * l + (int64_t)n * l + fact32_floats(m, n, l);
-  double* ds = ws + (nf + 1) / 2;
-  double ia = 1.0 / ma, ib = 1.0 / mb;
-  for (int idx = tid; idx < m * l; idx += HM_THREADS) SAf[idx] = (float)(SA[idx] * ia);
-  for (int idx = tid; idx < n * l; idx += HM_THREADS) {
-    int c = idx % n, j = idx / n;
-    double v = 0.0;
-    if (j < k0) {
-      if (c < n0) v = SB0[(int64_t)j * n0 + c];
-    } else if (c >= n0) {
-      v = SB1[(int64_t)(j - k0) * n1 + (c - n0)];
-    }
-    SBf[idx] = (float)(v * ib);
-  }
-  __syncthreads();
-  int guard = 0;
-  int k = trunc_fact32(m, n, l, SAf, SBf, S, fs, ds, e.eps, t.cap, loc(e, t.e), t.lde, loc(e, t.f), t.ldf, e.status,
-                       s, f, ok, &guard, seed, r0);
+  double S = 0.0;
+  int k = fact32_run(m, n, l, SA, SB0, n0, k0, SB1, n1, k1, ws, e.eps, t.cap, loc(e, t.e), t.lde, loc(e, t.f), t.ldf,
+                     e.status, s, seed, r0, f, ok, &S);
   if (*ok && !cta_finite(loc(e, t.e), t.lde, m, k, loc(e, t.f), t.ldf, n)) {
     *ok = 0;
     record_bad(e, 11, m, n, l, k, S);
@@ -913,7 +885,7 @@ __device__ void run_task(const ExecEnv& e, const HTask& t, Smem& s, long long ti
   }
 }
 
-__global__ void __launch_bounds__(HM_THREADS) exec_tasks(ExecEnv e) {
+__global__ void __launch_bounds__(HM_THREADS, 1) exec_tasks(ExecEnv e) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& s = *reinterpret_cast<Smem*>(smem_raw);
   __shared__ long long cur;
@@ -941,6 +913,7 @@ __global__ void __launch_bounds__(HM_THREADS) exec_tasks(ExecEnv e) {
           }
         }
         if (ld_acquire(e.status) != 0) skip = 1;
+        hm_status_won = 0;
         uint64_t t1 = global_ns();
         atomicAdd(e.wait_ns, (unsigned long long)(t1 - t0));
         cur_t0 = t1;
@@ -958,6 +931,7 @@ __global__ void __launch_bounds__(HM_THREADS) exec_tasks(ExecEnv e) {
       }
       run_task(e, task, s, t);
       __syncthreads();
+      if (threadIdx.x == 0 && hm_status_won) *e.fail_task = t + 1;
       if (threadIdx.x == 0 && s.bcast[7] > 0.0) atomicAdd(e.flops32, s.bcast[7]);
       if (threadIdx.x == 0 && task.type >= 0 && task.type < 16) {
         uint64_t dt = global_ns() - cur_t0;
@@ -996,7 +970,20 @@ __global__ void __launch_bounds__(HM_THREADS) trunc_batched(const TruncProblem* 
   __syncthreads();
   int cap = l < m ? l : m;
   if (n < cap) cap = n;
-  if (mixed && eps >= HM_F32_MIN_EPS && (int64_t)m * n <= HM_F32_MAX_MN && l > 0) {
+  if (mixed && eps >= HM_F32_MIN_EPS && l > 0 && l <= m && l <= n && l <= HM_FACT32_DIRECT) {
+    // factored stack: the FP32 steps of Fig. rkadd, no sketch (as hmat_lu's mixed form)
+    int ok = 0;
+    double S = 0.0, f = 0.0;
+    int k = fact32_run(m, n, l, SA, SB, n, l, nullptr, 0, 0, Jg + 2 * (int64_t)l * l, eps, cap, P.U, P.ldu, P.V, P.ldv,
+                       status, s, 0x5EEDull + blockIdx.x, l, &f, &ok, &S);
+    if (ok && cta_finite(P.U, P.ldu, m, k, P.V, P.ldv, n)) {
+      if (threadIdx.x == 0) {
+        P.k_new[0] = k;
+        atomicAdd(status + 1, 1);
+      }
+      return;
+    }
+  } else if (mixed && eps >= HM_F32_MIN_EPS && (int64_t)m * n <= HM_F32_MAX_MN && l > 0) {
     int Rr = m < n ? m : n;
     if (Rr > HM_RMAX) Rr = HM_RMAX;
     int64_t mn = (int64_t)m * n, fl = mn + 2 * (int64_t)(m + n) * Rr;
@@ -1048,18 +1035,21 @@ __global__ void csr_scatter(const DenseLeafDesc* leaves, int nleaves, const int6
   int b = blockIdx.x;
   if (b >= nleaves) return;
   DenseLeafDesc L = leaves[b];
-  unsigned long long cnt = 0;
+  unsigned long long cnt = 0, bad = 0;
   for (int i = threadIdx.x; i < L.rows; i += blockDim.x) {
     int64_t p = perm[L.roff + i];
     for (int64_t e = rowptr[p]; e < rowptr[p + 1]; ++e) {
       int64_t j = iperm[colidx[e]] - L.coff;
       if (j >= 0 && j < L.cols) {
-        hbase[L.off + i + j * (int64_t)L.rows] += val[e];
+        double v = val[e];
+        hbase[L.off + i + j * (int64_t)L.rows] += v;
         ++cnt;
+        if (!isfinite(v)) ++bad;
       }
     }
   }
   if (cnt) atomicAdd(placed, cnt);
+  if (bad) atomicAdd(placed + 1, bad);
 }
 
 __global__ void to_dense_kernel(const LeafRef* leaves, int nleaves, const double* hbase, const int* ranks,
@@ -1086,6 +1076,7 @@ __global__ void to_dense_kernel(const LeafRef* leaves, int nleaves, const double
 size_t smem_bytes() { return sizeof(Smem); }
 
 cudaError_t launch_exec(const ExecEnv& env, int grid, cudaStream_t st) {
+  (void)cudaGetLastError();  // a stale error of an earlier call is not this launch's
   exec_tasks<<<grid, HM_THREADS, sizeof(Smem), st>>>(env);
   return cudaGetLastError();
 }
@@ -1100,6 +1091,7 @@ cudaError_t launch_trunc_batched(const TruncProblem* probs, int count, double ep
                                  cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(trunc_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
   if (e != cudaSuccess) return e;
+  (void)cudaGetLastError();
   trunc_batched<<<count, HM_THREADS, sizeof(Smem), st>>>(probs, eps, status, mixed);
   return cudaGetLastError();
 }
@@ -1108,6 +1100,7 @@ cudaError_t launch_csr_scatter(const DenseLeafDesc* leaves, int nleaves, const i
                                const double* val, const int64_t* perm, const int64_t* iperm, double* hbase,
                                unsigned long long* placed, cudaStream_t st) {
   if (nleaves == 0) return cudaSuccess;
+  (void)cudaGetLastError();
   csr_scatter<<<nleaves, 128, 0, st>>>(leaves, nleaves, rowptr, colidx, val, perm, iperm, hbase, placed);
   return cudaGetLastError();
 }
@@ -1115,6 +1108,7 @@ cudaError_t launch_csr_scatter(const DenseLeafDesc* leaves, int nleaves, const i
 cudaError_t launch_to_dense(const LeafRef* leaves, int nleaves, const double* hbase, const int* ranks, double* out,
                             int64_t ldo, cudaStream_t st) {
   if (nleaves == 0) return cudaSuccess;
+  (void)cudaGetLastError();
   to_dense_kernel<<<nleaves, 256, 0, st>>>(leaves, nleaves, hbase, ranks, out, ldo);
   return cudaGetLastError();
 }

@@ -22,6 +22,7 @@ struct ExecEnv {
   int* done;                  // per task, 0 -> 1 when finished
   unsigned long long* head;   // next task to take
   int* status;                // device status word (hmat_status numbering)
+  long long* fail_task;       // 1 + index of the task that set the status first
   unsigned long long* counters;  // [0] truncations run, [1] randomised, [2] randomised fell back
   double* flops;              // FP64 operations counted by the tasks
   double* flops32;            // FP32 operations counted by the tasks (mixed path)
