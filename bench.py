@@ -40,13 +40,44 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 CUDA-core FMA rate: 152
 WORKLOADS = {"laplace3d_32": hs.laplace3d_32, "laplace3d_64": hs.laplace3d_64, "laplace2d_64": hs.laplace2d_64,
              "diffusion2d_batch64": hs.diffusion2d_batch,
              # small case of the 3D recipe for profiling captures
-             "laplace3d_16": lambda: hs.small_laplace(16, 3, 64, 1e-4)}
+             "laplace3d_16": lambda: hs.small_laplace(16, 3, 64, 1e-4),
+             # the stress case: 80^3 variable-coefficient diffusion, two tolerances, PCG check
+             "diffusion3d_80": lambda: hs.diffusion3d_80(1e-3),
+             "diffusion3d_80_eps1e-5": lambda: hs.diffusion3d_80(1e-5)}
+PCG_WORKLOADS = ("diffusion3d_80", "diffusion3d_80_eps1e-5")
 # bounded oracle sample: the same operator family, tolerance and leaf size at 16^3
 SAMPLE = {"laplace3d_32": lambda: hs.small_laplace(16, 3, 64, 1e-4),
           "laplace3d_16": lambda: hs.small_laplace(16, 3, 64, 1e-4),
           "laplace3d_64": lambda: hs.small_laplace(16, 3, 64, 1e-4),
           "laplace2d_64": hs.laplace2d_64,
-          "diffusion2d_batch64": lambda: hs.diffusion2d_batch()[0]}
+          "diffusion2d_batch64": lambda: hs.diffusion2d_batch()[0],
+          "diffusion3d_80": lambda: hs.Problem("diffusion3d_16", 16, 3, 64, 2.0, 1e-3, kind="diffusion", lc=0.05,
+                                               seed=4),
+          "diffusion3d_80_eps1e-5": lambda: hs.Problem("diffusion3d_16", 16, 3, 64, 2.0, 1e-5, kind="diffusion",
+                                                       lc=0.05, seed=4)}
+
+
+T_START = time.time()
+FALLBACK_HBM_GBS = 6800.0  # an earlier GB300 measurement, used only without the measured peaks file
+# plain FP64 factorisation time over the mixed one, for the time guard of the
+# comparator (measured at 64^3; a guess errs towards skipping)
+FP64_OVER_MIXED = 12.0
+STANDARD_OVER_ACC = 3.0  # the same for the standard form (the paper: factor 2 to 3)
+TRAFFIC_NOTE = ("DRAM read + write bytes of one launch from an ncu capture of this source tree (profiles/), "
+                "scaled by the truncations where the capture is of a smaller case; null when the kernel source "
+                "changed since")
+
+
+def oracle_values(workload: str):
+    """The oracle's stored values for the workload (tests/golden/, written by
+    a script that calls only the oracle), or None."""
+    path = os.path.join(ROOT, "tests", "golden", f"oracle_{workload}.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    return {k: d[k] for k in ("precond_error", "truncations", "mean_rank", "blocktree_sha256", "oracle_lu_seconds",
+                              "oracle_cores") if k in d} | {"source": os.path.relpath(path, ROOT)}
 
 
 def measured_peaks() -> dict:
@@ -233,8 +264,11 @@ def run_reference(args, rank: int, world: int) -> None:
     if args.workload == "hmul_3d32":
         run_reference_hmul(args)
         return
-    cfg = workload_config(args, rank_problems(args.workload, 0), world)
     p = SAMPLE[args.workload]()
+    # the sample's own configuration: the oracle runs a smaller case of the
+    # same recipe, so this line is not the GPU line's problem size
+    cfg = {"workload": p.name, "n": p.n, "leaf": p.leaf, "eta": p.eta, "eps": p.eps, "sample_of": args.workload,
+           "precision": "fp64", "parallelism": "1 host core"}
     import oracle
     oracle.build()
     times, truncs = [], []
@@ -286,10 +320,10 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     flush = torch.empty(int(256 * 2**20) // 4, dtype=torch.float32, device=dev)
     prec = g.HMAT_MIXED if args.precision == "mixed" else g.HMAT_FP64
 
-    def step(precision=prec):
+    def step(precision=prec, mode=g.HMAT_ACCUMULATED):
         for wk, pr in zip(work, pristine):
             wk.copy_values_from(pr)
-        g.lu_batched(ctx, work, eps, max_rank=args.max_rank, precision=precision, reuse_schedule=True)
+        g.lu_batched(ctx, work, eps, max_rank=args.max_rank, precision=precision, reuse_schedule=True, mode=mode)
 
     sched_first = None
     for i in range(args.warmup):
@@ -301,7 +335,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    step_ms, kern_ms, flops, flops32, truncs, tasks, sched = [], [], [], [], [], [], []
+    step_ms, kern_ms, flops, flops32, truncs, tasks, sched, nbytes = [], [], [], [], [], [], [], []
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     for _ in range(args.steps):
@@ -315,6 +349,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         kern_ms.append(1e3 * st["factor_seconds"])
         flops.append(st["flops"])
         flops32.append(st["flops32"])
+        nbytes.append(st["bytes"])
         truncs.append(st["truncations"])
         tasks.append(st["tasks"])
         sched.append(st["schedule_seconds"])
@@ -322,7 +357,11 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop() if clocks else None
-    value, total_s = job_throughput(sum(truncs), sum(step_ms) / 1e3, world, dev)
+    # the symbolic pass (host) of the first call counted in every step, so that
+    # the headline is the whole setup; the kept schedule saves it in practice
+    # when the same sparsity pattern is factored again
+    value, total_s = job_throughput(sum(truncs), sum(step_ms) / 1e3 + args.steps * sched_first, world, dev)
+    value_numeric, _ = job_throughput(sum(truncs), sum(step_ms) / 1e3, world, dev)
     st = work[0].stats()
 
     # end to end through the public API with host buffers: CSR -> device,
@@ -330,7 +369,8 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     h2d = sum(8 * (c.rowptr.size + c.colidx.size + c.val.size) + 16 * c.n for c in csrs)
     d2h = sum(8 * g.lib().hmat_blocktree_size(bt.h) for bt in bts)
     e2e_times = []
-    for i in range(1 + args.steps):
+    e2e_steps = min(args.steps, 2)
+    for i in range(1 + e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         Hs = [g.HMatrix(ctx, bt, c) for bt, c in zip(bts, csrs)]
@@ -341,7 +381,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         if i >= 1:
             e2e_times.append(time.perf_counter() - t0)
         del Hs
-    e2e_value, e2e_s = job_throughput(sum(truncs), sum(e2e_times), world, dev)
+    e2e_value, e2e_s = job_throughput(statistics.mean(truncs) * e2e_steps, sum(e2e_times), world, dev)
 
     if rank != 0:
         return
@@ -351,9 +391,24 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     perr = [precond_error(g, work[i], cts[i], csrs[i], probs[i]) for i in range(nq)]
     types = {name: {"count": st["type_count"][i], "cta_s": st["type_seconds"][i]}
              for i, name in enumerate(TASK_NAMES) if st["type_count"][i]}
+    pcg = None
+    if args.workload in PCG_WORKLOADS:
+        # 8 seeded N(0, 1) right-hand sides (seed 4), FP64 CG to 1e-10
+        p0 = probs[0]
+        B = np.stack([hs.normal(4 + c, p0.n) for c in range(8)])  # (8, n), original ordering
+        Bt = torch.from_numpy(B).to(dev)
+        Xt = torch.zeros_like(Bt)
+        t0 = time.perf_counter()
+        its, res = work[0].pcg(csrs[0], Bt, Xt, rtol=1e-10, maxit=1000)
+        pcg = {"rhs": 8, "rtol": 1e-10, "iterations": [int(x) for x in its], "rel_residual": [float(x) for x in res],
+               "seconds": time.perf_counter() - t0}
     # the plain FP64 accumulated form on the same GPU, same matrices: the comparator
     fp64 = None
-    if args.precision == "mixed" and not args.no_fp64:
+    est = FP64_OVER_MIXED * statistics.mean(step_ms) / 1e3
+    if args.precision == "mixed" and not args.no_fp64 and time.time() - T_START + est > args.time_budget:
+        fp64 = {"skipped": f"the plain FP64 factorisation (about {est:.0f} s) would end past the bench's time "
+                           f"budget of {args.time_budget:.0f} s"}
+    elif args.precision == "mixed" and not args.no_fp64:
         ev0.record(stream)
         step(g.HMAT_FP64)
         ev1.record(stream)
@@ -363,44 +418,81 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
                 "value": s64["truncations"] / (ev0.elapsed_time(ev1) / 1e3),
                 "precond_error": [precond_error(g, work[i], cts[i], csrs[i], probs[i]) for i in range(nq)],
                 "kernel_s": s64["factor_seconds"], "flops": s64["flops"]}
-        fp64["speedup_of_chosen_form"] = fp64["setup_s"] / (statistics.mean(step_ms) / 1e3)
+        fp64["schedule_s"] = s64["schedule_seconds"]
+        fp64["note"] = "setup_s includes this first FP64 call's symbolic pass (inside the events)"
+        fp64["speedup_of_chosen_form"] = fp64["setup_s"] / (statistics.mean(step_ms) / 1e3 + sched_first)
+    # the standard form (every product applied at once, Section 4) in the
+    # chosen precision: the paper's comparison, time and truncations
+    standard = None
+    est = STANDARD_OVER_ACC * statistics.mean(step_ms) / 1e3
+    if not args.no_standard and time.time() - T_START + est > args.time_budget:
+        standard = {"skipped": f"the standard-form factorisation (about {est:.0f} s) would end past the bench's "
+                               f"time budget of {args.time_budget:.0f} s"}
+    elif not args.no_standard:
+        ev0.record(stream)
+        step(prec, g.HMAT_STANDARD)
+        ev1.record(stream)
+        ev1.synchronize()
+        sstd = work[0].stats()
+        t_std = ev0.elapsed_time(ev1) / 1e3
+        # (its first call builds its schedule inside the events)
+        standard = {"setup_s": t_std, "numeric_s": t_std - sstd["schedule_seconds"],
+                    "schedule_s": sstd["schedule_seconds"], "truncations": sstd["truncations"],
+                    "precond_error": [precond_error(g, work[i], cts[i], csrs[i], probs[i]) for i in range(nq)],
+                    "time_ratio_standard_over_accumulated": t_std / (statistics.mean(step_ms) / 1e3 + sched_first),
+                    "truncation_ratio_standard_over_accumulated": sstd["truncations"] / statistics.mean(truncs)}
     peaks = measured_peaks()
     avg_kern_s = statistics.mean(kern_ms) / 1e3
     achieved = statistics.mean(flops) / avg_kern_s / 1e12
     achieved32 = statistics.mean(flops32) / avg_kern_s / 1e12
+    hbm_peak = peaks.get("hbm_gbs") or FALLBACK_HBM_GBS
+    achieved_gbs = statistics.mean(nbytes) / avg_kern_s / 1e9
+    ref = oracle_values(args.workload)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": statistics.mean(step_ms) + 1e3 * sched_first, "higher_is_better": True,
+        "scaling": "strong" if args.workload == "diffusion2d_batch64" else "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
         "config": workload_config(args, probs, world),
-        "setup_s": statistics.mean(step_ms) / 1e3,
+        "setup_s": statistics.mean(step_ms) / 1e3 + sched_first,
+        "numeric_s": statistics.mean(step_ms) / 1e3,
+        "value_numeric_only": value_numeric,
         "truncations_per_step": int(statistics.mean(truncs)),
         "tasks_per_step": int(statistics.mean(tasks)),
         "schedule_s": statistics.mean(sched),
         "schedule_s_first_call": sched_first,
-        "schedule_note": "timed steps reuse the kept schedule (reuse_schedule); e2e builds it every step",
+        "schedule_note": "setup_s and value include the first call's symbolic pass in every step (the timed "
+                         "numeric steps reuse its schedule); e2e builds it every step",
         "tree_build_s": tree_s,
         "precond_error": perr if len(probs) > 1 else perr[0],
+        "oracle": ref,
+        "pcg": pcg,
         "randomised_truncations": st["rand_truncations"], "randomised_fallbacks": st["rand_fallbacks"],
         "plain_fp64": fp64,
+        "standard_form": standard,
         "task_types": types,
         "critical_path_tasks": st["levels"],
         "gpu_launches": args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic_per_launch(args.workload),
+        "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved_gbs / hbm_peak, "traffic": traffic_per_launch(args.workload),
                      "kernel": "exec_tasks", "kernel_ms": statistics.mean(kern_ms),
-                     "flops_per_launch": statistics.mean(flops),
-                     "fp32": {"achieved": achieved32, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "bytes_per_launch": statistics.mean(nbytes),
+                     "peak_note": ("measured" if peaks.get("hbm_gbs") else "fallback") + " HBM copy bandwidth; "
+                                  "achieved = algorithmic bytes per launch (counted on the device per task: "
+                                  "8 [(m + n) l + (m + n) k] per truncation, leaves and thin blocks read and "
+                                  "written once) / the launch's CUDA-event time",
+                     "fp64": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                              "frac": achieved / FP64_PEAK_TFLOPS, "flops_per_launch": statistics.mean(flops)},
+                     "fp32": {"bound": "alu", "achieved": achieved32, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                               "frac": achieved32 / FP32_PEAK_TFLOPS, "flops_per_launch": statistics.mean(flops32)},
-                     "peak_note": "nominal FP64 (1.25 TFLOP/s) and FP32 (152 SMs x 128 lanes x 2 x 2070 MHz) "
-                                  "rates: the measured peaks file has no FP64 or FP32 vector figure; FP64 and "
-                                  "FP32 operations are counted on the device separately",
-                     "traffic_note": "DRAM read + write bytes of one launch from an ncu capture of this source "
-                                     "tree (profiles/); null when the kernel source changed since"},
+                     "alu_peak_note": "nominal FP64 (1.25 TFLOP/s) and FP32 (152 SMs x 128 lanes x 2 x 2070 MHz) "
+                                      "rates: the measured peaks file has no FP64 or FP32 vector figure",
+                     "traffic_note": TRAFFIC_NOTE},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "ms_per_step": 1e3 * e2e_s / args.steps},
+                "ms_per_step": 1e3 * e2e_s / e2e_steps, "steps": e2e_steps},
         "clocks": clk,
         "device_bytes": st["device_bytes"],
+        "bench_wall_s": time.time() - T_START,
         "peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")},
     }
     if world == 1 and not args.no_cpu:
@@ -435,9 +527,9 @@ def run_hmul(args, rank: int, world: int, local_rank: int) -> None:
     Z = g.HMatrix(ctx, bt, csr)
     flush = torch.empty(int(256 * 2**20) // 4, dtype=torch.float32, device=dev)
 
-    def step(precision=prec):
+    def step(precision=prec, mode=g.HMAT_ACCUMULATED):
         Z.copy_values_from(Z0)
-        g.addmul(ctx, -1.0, X, X, Z, p.eps, max_rank=args.max_rank, precision=precision)
+        g.addmul(ctx, -1.0, X, X, Z, p.eps, max_rank=args.max_rank, precision=precision, mode=mode)
 
     for _ in range(args.warmup):
         step()
@@ -504,7 +596,11 @@ def run_hmul(args, rank: int, world: int, local_rank: int) -> None:
 
     err = rel_error(Z)
     fp64 = None
-    if args.precision == "mixed" and not args.no_fp64:
+    est = FP64_OVER_MIXED * statistics.mean(step_ms) / 1e3
+    if args.precision == "mixed" and not args.no_fp64 and time.time() - T_START + est > args.time_budget:
+        fp64 = {"skipped": f"the plain FP64 factorisation (about {est:.0f} s) would end past the bench's time "
+                           f"budget of {args.time_budget:.0f} s"}
+    elif args.precision == "mixed" and not args.no_fp64:
         ev0.record(stream)
         step(g.HMAT_FP64)
         ev1.record(stream)
@@ -513,6 +609,18 @@ def run_hmul(args, rank: int, world: int, local_rank: int) -> None:
         fp64 = {"ms": ev0.elapsed_time(ev1), "truncations": s64["truncations"],
                 "value": s64["truncations"] / (ev0.elapsed_time(ev1) / 1e3), "rel_error": rel_error(Z)}
         fp64["speedup_of_chosen_form"] = fp64["ms"] / statistics.mean(step_ms)
+    # the standard multiplication (every product applied at once) in the
+    # chosen precision: the paper's Exp. 1 comparison
+    standard = None
+    if not args.no_standard:
+        ev0.record(stream)
+        step(prec, g.HMAT_STANDARD)
+        ev1.record(stream)
+        ev1.synchronize()
+        sst = Z.stats()
+        standard = {"ms": ev0.elapsed_time(ev1), "truncations": sst["truncations"], "rel_error": rel_error(Z),
+                    "time_ratio_standard_over_accumulated": ev0.elapsed_time(ev1) / statistics.mean(step_ms),
+                    "truncation_ratio_standard_over_accumulated": sst["truncations"] / statistics.mean(truncs)}
     avg_kern_s = statistics.mean(kern_ms) / 1e3
     achieved = statistics.mean(flops) / avg_kern_s / 1e12
     achieved32 = statistics.mean(flops32) / avg_kern_s / 1e12
@@ -525,7 +633,7 @@ def run_hmul(args, rank: int, world: int, local_rank: int) -> None:
                    "precision": args.precision, "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"replicas{world}"},
         "truncations_per_step": int(statistics.mean(truncs)), "schedule_s": statistics.mean(sched),
-        "rel_error": err, "plain_fp64": fp64, "gpu_launches": args.steps,
+        "rel_error": err, "plain_fp64": fp64, "standard_form": standard, "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "exec_tasks",
                      "fp32": {"achieved": achieved32, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -588,14 +696,17 @@ def precond_error(g, H, ct, csr, p, maxit=50, rtol=1e-3) -> float:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="laplace3d_32", choices=sorted(WORKLOADS) + ["hmul_3d32"])
+    ap.add_argument("--workload", default="laplace3d_64", choices=sorted(WORKLOADS) + ["hmul_3d32"])
     ap.add_argument("--max-rank", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparator")
+    ap.add_argument("--no-standard", action="store_true", help="skip the standard-form comparator")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--time-budget", type=float, default=1650.0,
+                    help="seconds after which the optional comparators are skipped")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

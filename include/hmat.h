@@ -73,8 +73,21 @@ typedef struct hmat_mlp hmat_mlp;
  *  record_training  non-zero: every exact truncation records its features
  *             and rank (see hmat_lu_training_data).
  *  seed       seed of the randomised sketches' Rademacher signs (0: a fixed
- *             default); results are reproducible for a given seed. */
+ *             default); results are reproducible for a given seed.
+ *  mode       HMAT_ACCUMULATED (0, default): products collected in
+ *             accumulators and truncated once per block and flush (Section 4,
+ *             Figs. addproduct, split, flush); HMAT_STANDARD (1): every
+ *             product of a leaf pair applied at once by rkupdate (Section 4,
+ *             the multiplication before "Accumulated updates"; the remark
+ *             after the complexity theorem), for hmat_lu, hmat_lu_batched
+ *             and hmat_addmul.
+ *  rank_rule  HMAT_REL_FRO (0, default): the Frobenius rule above;
+ *             HMAT_REL_SPEC (1): the smallest k with sigma_{k+1} <= eps
+ *             sigma_1, available with precision HMAT_FP64 (HMAT_ERR_ARG with
+ *             HMAT_MIXED, whose checks bound the Frobenius residual). */
 enum { HMAT_FP64 = 0, HMAT_MIXED = 1 };
+enum { HMAT_ACCUMULATED = 0, HMAT_STANDARD = 1 };
+enum { HMAT_REL_FRO = 0, HMAT_REL_SPEC = 1 };
 typedef struct {
   double eps;
   int64_t max_rank;
@@ -84,6 +97,8 @@ typedef struct {
   const hmat_mlp* predictor;
   int record_training;
   uint64_t seed;
+  int mode;
+  int rank_rule;
 } hmat_opts;
 
 typedef struct {
@@ -119,6 +134,10 @@ typedef struct {
   double cp_type_seconds[16];
   int64_t cp_type_count[16];
   double flops32;           /* FP32 operations of the mixed path (flops: FP64)    */
+  double bytes;             /* algorithmic bytes the tasks must move: stacked
+                               factors read and truncated factors written
+                               (8 [(m + n) l + (m + n) k] per truncation),
+                               dense leaves and thin blocks read and written */
 } hmat_stats;
 
 /* Message of the last failure on this thread, copied into buf (NUL-terminated,
@@ -244,7 +263,9 @@ hmat_status hmat_invert(hmat_ctx* ctx, hmat* G, const hmat_opts* opts);
 hmat_status hmat_cholesky(hmat_ctx* ctx, hmat* G, const hmat_opts* opts);
 
 /* Host-only analysis of the schedule hmat_lu would run for this matrix (no
- * device is touched): fills tasks, levels (longest dependency chain),
+ * device is touched): fills tasks, truncations (the schedule's truncation
+ * tasks; at run time those of zero products are skipped), levels (longest
+ * dependency chain),
  * critical_flops / est_flops (static estimates with rank 8 for unknown
  * ranks), schedule_seconds and the workspace size in device_bytes. */
 hmat_status hmat_analyze_lu(const hmat_btree* bt, int64_t n, const int64_t* rowptr, const int64_t* colidx,
@@ -253,6 +274,22 @@ hmat_status hmat_analyze_lu(const hmat_btree* bt, int64_t n, const int64_t* rowp
 /* B <- (LU)^{-1} B (trans = 0) or (LU)^{-T} B (trans = 1) with the factors of
  * hmat_lu; B: device, n x nrhs, leading dimension ldb, permuted ordering. */
 hmat_status hmat_solve(hmat_ctx* ctx, const hmat* LU, int trans, int64_t nrhs, double* B, int64_t ldb);
+
+/* Preconditioned conjugate gradients for A X = B with the factors of
+ * hmat_lu as the preconditioner z = (LU)^{-1} r (the paper measures the
+ * factors' quality by ||I - (LU)^{-1} A||_2, Section 7; the CG count on an
+ * SPD stiffness matrix is the practical form of that measure; Hestenes and
+ * Stiefel's method, not in the paper).  A: the matrix the factors approximate,
+ * host CSR in the ORIGINAL ordering (rowptr[n+1], colidx, val, copied).
+ * B, X: device, n x nrhs column-major (ld n), original ordering; x_0 = 0.
+ * Every column runs until ||r|| <= rtol ||b|| or maxit steps; iters and
+ * relres (host, nrhs) receive the steps taken and the true relative residual
+ * ||b - A x|| / ||b|| at the end.  The solves reuse one task schedule.
+ * (LU)^{-1} of an SPD matrix is symmetric up to the truncation error, which
+ * CG tolerates as long as that error is small.  Synchronous. */
+hmat_status hmat_pcg(hmat_ctx* ctx, const hmat* LU, int64_t n, const int64_t* rowptr, const int64_t* colidx,
+                     const double* val, int64_t nrhs, const double* B, double* X, double rtol, int64_t maxit,
+                     int64_t* iters, double* relres);
 
 /* Truncation of one low-rank matrix in place (Section 3, "Truncation"): with
  * R = U V^T, U (m x k, ldu) and V (n x k, ldv) in device memory, overwrite the

@@ -86,6 +86,12 @@ def stats_reset():
     lib().orc_stats_reset()
 
 
+def set_rank_rule(rule: int):
+    """0: relative Frobenius (default), 1: relative spectral (smallest k with
+    sigma_{k+1} <= eps sigma_1); applies to every later truncation."""
+    lib().orc_set_rank_rule(ctypes.c_int(rule))
+
+
 def trace_enable(on: bool = True):
     """Record (rows, cols, stacked width, new rank) of every truncation
     (rowmerge SVDs have a negative width)."""
@@ -300,6 +306,22 @@ class HMatrix:
         B = _f64(B if np.ndim(B) == 2 else np.reshape(B, (-1, 1))).copy(order="F")
         _check(lib().orc_hsolve(self.h, ctypes.c_int64(B.shape[1]), _p(B), ctypes.c_int(1 if trans else 0)))
         return B
+
+    def pcg(self, csr, B, rtol: float = 1e-10, maxit: int = 500):
+        """Preconditioned CG for A X = B (B: n x nrhs, original ordering) with
+        these H-LU factors as the preconditioner; returns X, iterations and
+        final relative residuals per column."""
+        B = _f64(B if np.ndim(B) == 2 else np.reshape(B, (-1, 1)))
+        n, nrhs = B.shape
+        X = np.zeros((n, nrhs), order="F")
+        its = np.zeros(nrhs, np.int64)
+        res = np.zeros(nrhs)
+        rp = np.ascontiguousarray(csr.rowptr, np.int64)
+        ci = np.ascontiguousarray(csr.colidx, np.int64)
+        va = np.ascontiguousarray(csr.val, np.float64)
+        _check(lib().orc_pcg(self.h, ctypes.c_int64(n), _p(rp, I64P), _p(ci, I64P), _p(va), ctypes.c_int64(nrhs),
+                             _p(B), _p(X), ctypes.c_double(rtol), ctypes.c_int64(maxit), _p(its, I64P), _p(res)))
+        return X, its, res
 
     def precond_error(self, csr, v0, maxit: int = 50, rtol: float = 1e-3):
         rp = np.ascontiguousarray(csr.rowptr, np.int64)

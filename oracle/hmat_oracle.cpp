@@ -335,9 +335,23 @@ static void svd_thin(const Mat& M, Mat& U, std::vector<double>& s, Mat& V) {
   }
 }
 
+// Rank rule of "choose new rank k": 0 relative Frobenius (the default), 1
+// relative spectral (smallest k with s_{k+1} <= eps s_1).  Set for a call by
+// orc_set_rank_rule.
+static int g_rank_rule = 0;
+
 // "Choose new rank k" (Fig. rkadd / Fig. rowmerge): smallest k with
-// sum_{i>k} s_i^2 <= eps^2 sum_i s_i^2, optionally capped at max_rank.
+// sum_{i>k} s_i^2 <= eps^2 sum_i s_i^2 (or, under the spectral rule, the
+// number of s_i > eps s_1), optionally capped at max_rank.  s is in
+// decreasing order.
 static i64 choose_rank(const std::vector<double>& s, double eps, i64 max_rank) {
+  if (g_rank_rule == 1) {
+    i64 k = 0;
+    double s1 = s.empty() ? 0.0 : s[0];
+    while (k < (i64)s.size() && s[(size_t)k] > eps * s1) ++k;
+    if (max_rank >= 0 && k > max_rank) k = max_rank;
+    return k;
+  }
   double total = 0.0;
   for (double x : s) total += x * x;
   i64 k = (i64)s.size();
@@ -1709,6 +1723,7 @@ extern "C" {
 const char* orc_last_error() { return g_err.c_str(); }
 
 void orc_stats_reset() { g_stats = Stats(); }
+void orc_set_rank_rule(int rule) { g_rank_rule = rule == 1 ? 1 : 0; }
 void orc_trace_enable(int on) {
   g_trace_on = on != 0;
   g_trace.clear();
@@ -1968,6 +1983,65 @@ int orc_hsolve(void* h, int64_t nrhs, double* B, int trans) {
       hsolve_Lt(*G, 0, X, 0);
     }
     to_colmajor(X, B, n);
+  });
+}
+
+// Preconditioned conjugate gradients (Hestenes and Stiefel 1952) for
+// A x = b with the H-LU factors as the preconditioner, z = (LU)^{-1} r, for
+// nrhs right-hand sides one after the other, in the permuted ordering.  B, X:
+// n x nrhs column-major in the ORIGINAL ordering; x_0 = 0.  A column stops
+// when ||r_k|| <= rtol ||b|| or after maxit steps; iters[c] and relres[c]
+// (the true relative residual ||b - A x|| / ||b|| at the end) are returned.
+// The preconditioned CG assumes a symmetric preconditioner: (LU)^{-1} of an
+// SPD matrix is symmetric up to the truncation error of the factors.
+int orc_pcg(void* h, int64_t n, const int64_t* rowptr, const int64_t* colidx, const double* val, int64_t nrhs,
+            const double* B, double* X, double rtol, int64_t maxit, int64_t* iters, double* relres) {
+  return guard([&] {
+    HMat* G = (HMat*)h;
+    const std::vector<i64>& perm = G->bt->R->perm;
+    std::vector<i64> iperm((size_t)n);
+    for (i64 i = 0; i < n; ++i) iperm[(size_t)perm[(size_t)i]] = i;
+    auto dot = [&](const std::vector<double>& a, const std::vector<double>& b) {
+      double t = 0.0;
+      for (i64 i = 0; i < n; ++i) t += a[(size_t)i] * b[(size_t)i];
+      return t;
+    };
+    auto precond = [&](const std::vector<double>& r, std::vector<double>& z) {
+      Mat Z = from_colmajor(n, 1, r.data(), n);
+      hsolve_L(*G, 0, Z, 0);
+      hsolve_U(*G, 0, Z, 0);
+      z.assign(Z.a.begin(), Z.a.end());
+    };
+    for (i64 c = 0; c < nrhs; ++c) {
+      std::vector<double> b((size_t)n), x((size_t)n, 0.0), r, z, p, q;
+      for (i64 i = 0; i < n; ++i) b[(size_t)i] = B[c * n + perm[(size_t)i]];
+      r = b;
+      double nb = std::sqrt(dot(b, b));
+      precond(r, z);
+      p = z;
+      double rz = dot(r, z);
+      i64 it = 0;
+      while (it < maxit && std::sqrt(dot(r, r)) > rtol * nb) {
+        csr_perm_matvec(n, rowptr, colidx, val, perm, iperm, false, p, q);
+        double alpha = rz / dot(p, q);
+        for (i64 i = 0; i < n; ++i) {
+          x[(size_t)i] += alpha * p[(size_t)i];
+          r[(size_t)i] -= alpha * q[(size_t)i];
+        }
+        precond(r, z);
+        double rz1 = dot(r, z);
+        double beta = rz1 / rz;
+        rz = rz1;
+        for (i64 i = 0; i < n; ++i) p[(size_t)i] = z[(size_t)i] + beta * p[(size_t)i];
+        ++it;
+      }
+      csr_perm_matvec(n, rowptr, colidx, val, perm, iperm, false, x, q);
+      double res = 0.0;
+      for (i64 i = 0; i < n; ++i) res += (b[(size_t)i] - q[(size_t)i]) * (b[(size_t)i] - q[(size_t)i]);
+      iters[c] = it;
+      relres[c] = nb > 0.0 ? std::sqrt(res) / nb : 0.0;
+      for (i64 i = 0; i < n; ++i) X[c * n + perm[(size_t)i]] = x[(size_t)i];
+    }
   });
 }
 

@@ -28,6 +28,8 @@ STATUS = {0: "HMAT_OK", 1: "HMAT_ERR_ARG", 2: "HMAT_ERR_NOMEM", 3: "HMAT_ERR_SIN
           4: "HMAT_ERR_NONFINITE", 5: "HMAT_ERR_RANK", 6: "HMAT_ERR_TIMEOUT", 7: "HMAT_ERR_CUDA",
           9: "HMAT_ERR_INTERNAL"}
 HMAT_FP64, HMAT_MIXED = 0, 1
+HMAT_ACCUMULATED, HMAT_STANDARD = 0, 1
+HMAT_REL_FRO, HMAT_REL_SPEC = 0, 1
 
 for _code, _name in STATUS.items():  # HMAT_OK, HMAT_ERR_ARG, ... as module constants
     globals()[_name] = _code
@@ -40,7 +42,7 @@ EXPORTS = ["hmat_last_error", "hmat_ctx_create", "hmat_ctx_destroy", "hmat_clust
            "trunc_lowrank", "trunc_lowrank_batched", "hmat_stats_get", "hmat_ranks", "hmat_copy_values",
            "hmat_analyze_lu", "trunc_lowrank_noalloc", "hmat_lu_batched", "hmat_lu_training_data",
            "hmat_mlp_create", "hmat_mlp_destroy", "hmat_mlp_get_params", "hmat_mlp_set_params", "hmat_mlp_forward",
-           "hmat_mlp_grad", "hmat_mlp_train", "hmat_addmul", "hmat_invert", "hmat_cholesky"]
+           "hmat_mlp_grad", "hmat_mlp_train", "hmat_addmul", "hmat_invert", "hmat_cholesky", "hmat_pcg"]
 MLP_NPARAM = 4673
 
 
@@ -53,7 +55,8 @@ class HmatError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("max_rank", ctypes.c_int64), ("precision", ctypes.c_int),
                 ("spin_limit", ctypes.c_int64), ("reuse_schedule", ctypes.c_int), ("predictor", ctypes.c_void_p),
-                ("record_training", ctypes.c_int), ("seed", ctypes.c_uint64)]
+                ("record_training", ctypes.c_int), ("seed", ctypes.c_uint64), ("mode", ctypes.c_int),
+                ("rank_rule", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -69,7 +72,7 @@ class Stats(ctypes.Structure):
                 ("rand_fallbacks", ctypes.c_int64), ("sketch_attempts", ctypes.c_int64),
                 ("sketch_columns", ctypes.c_int64), ("training_pairs", ctypes.c_int64), ("cp_seconds", ctypes.c_double),
                 ("cp_type_seconds", ctypes.c_double * 16), ("cp_type_count", ctypes.c_int64 * 16),
-                ("flops32", ctypes.c_double)]
+                ("flops32", ctypes.c_double), ("bytes", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         d = {}
@@ -213,9 +216,10 @@ class HMatrix:
         _check(lib().hmat_copy_values(self.ctx.h, self.h, src.h))
 
     def lu(self, eps: float, max_rank: int = 0, precision: int = HMAT_FP64, spin_limit: int = 0,
-           reuse_schedule: bool = False, predictor=None, record_training: bool = False):
+           reuse_schedule: bool = False, predictor=None, record_training: bool = False, mode: int = HMAT_ACCUMULATED,
+           rank_rule: int = HMAT_REL_FRO):
         o = Opts(eps, max_rank, precision, spin_limit, int(reuse_schedule), predictor.h if predictor else None,
-                 int(record_training))
+                 int(record_training), 0, mode, rank_rule)
         _check(lib().hmat_lu(self.ctx.h, self.h, ctypes.byref(o)))
 
     def cholesky(self, eps: float, max_rank: int = 0, precision: int = HMAT_FP64, spin_limit: int = 0):
@@ -243,6 +247,21 @@ class HMatrix:
         _check(lib().hmat_solve(self.ctx.h, self.h, ctypes.c_int(int(trans)), ctypes.c_int64(nrhs), _dptr(B),
                                 ctypes.c_int64(self.n)))
 
+    def pcg(self, csr, B, X, rtol: float = 1e-10, maxit: int = 500):
+        """hmat_pcg: CG for A X = B (torch tensors (nrhs, n), original ordering)
+        preconditioned by these factors; returns (iterations, relative
+        residuals) per right-hand side."""
+        nrhs = B.shape[0] if B.dim() == 2 else 1
+        rp = np.ascontiguousarray(csr.rowptr, np.int64)
+        ci = np.ascontiguousarray(csr.colidx, np.int64)
+        va = np.ascontiguousarray(csr.val, np.float64)
+        its = np.zeros(nrhs, np.int64)
+        res = np.zeros(nrhs)
+        _check(lib().hmat_pcg(self.ctx.h, self.h, ctypes.c_int64(self.n), _hp(rp, I64P), _hp(ci, I64P), _hp(va, F64P),
+                              ctypes.c_int64(nrhs), _dptr(B), _dptr(X), ctypes.c_double(rtol), ctypes.c_int64(maxit),
+                              _hp(its, I64P), _hp(res, F64P)))
+        return its, res
+
     def stats(self) -> dict:
         s = Stats()
         _check(lib().hmat_stats_get(self.h, ctypes.byref(s)))
@@ -265,18 +284,21 @@ class HMatrix:
 
 
 def addmul(ctx: Context, alpha: float, X: "HMatrix", Y: "HMatrix", Z: "HMatrix", eps: float, max_rank: int = 0,
-           precision: int = HMAT_FP64, spin_limit: int = 0, predictor=None, record_training: bool = False):
-    """hmat_addmul: Z <- blocktrunc(Z + alpha X Y), accumulated form, one launch."""
-    o = Opts(eps, max_rank, precision, spin_limit, 0, predictor.h if predictor else None, int(record_training))
+           precision: int = HMAT_FP64, spin_limit: int = 0, predictor=None, record_training: bool = False,
+           mode: int = HMAT_ACCUMULATED, rank_rule: int = HMAT_REL_FRO):
+    """hmat_addmul: Z <- blocktrunc(Z + alpha X Y), accumulated (or standard) form, one launch."""
+    o = Opts(eps, max_rank, precision, spin_limit, 0, predictor.h if predictor else None, int(record_training), 0,
+             mode, rank_rule)
     _check(lib().hmat_addmul(ctx.h, ctypes.c_double(alpha), X.h, Y.h, Z.h, ctypes.byref(o)))
 
 
 def lu_batched(ctx: Context, Hs, eps: float, max_rank: int = 0, precision: int = HMAT_FP64, spin_limit: int = 0,
-               reuse_schedule: bool = False, predictor=None, record_training: bool = False):
+               reuse_schedule: bool = False, predictor=None, record_training: bool = False,
+               mode: int = HMAT_ACCUMULATED, rank_rule: int = HMAT_REL_FRO):
     """hmat_lu_batched: factor the HMatrix objects Hs together in one launch."""
     arr = (ctypes.c_void_p * len(Hs))(*[H.h.value for H in Hs])
     o = Opts(eps, max_rank, precision, spin_limit, int(reuse_schedule), predictor.h if predictor else None,
-             int(record_training))
+             int(record_training), 0, mode, rank_rule)
     _check(lib().hmat_lu_batched(ctx.h, arr, ctypes.c_int(len(Hs)), ctypes.byref(o)))
 
 

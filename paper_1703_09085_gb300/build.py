@@ -8,6 +8,7 @@ from __future__ import annotations
 import os
 import subprocess
 import sys
+import time
 from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -39,6 +40,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
+    started = time.time()
 
     def compile_one(src):
         obj = os.path.join(BUILD, src + ".o")
@@ -59,6 +61,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
+    # stamp the library with the time the compilation started, so that a
+    # source edited while it ran makes the next build() recompile
+    os.utime(tmp, (started, started))
     os.replace(tmp, LIB)
     return LIB
 

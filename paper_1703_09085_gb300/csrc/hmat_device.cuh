@@ -103,6 +103,12 @@ static __device__ __forceinline__ void set_status(int* status, int code) {
 // J_in Vr = J_out.
 // ---------------------------------------------------------------------------
 // s.ivals[2] receives the sweeps run, s.ivals[3] the rotations applied.
+// A column whose squared norm is at most 1e-30 ||J||_F^2 (singular values
+// below 1e-15 of the largest) is left alone: rotating it against the others
+// changes no singular value above that level, and orthogonalising such
+// rounding-level columns to relative accuracy is what made the sweeps many
+// (the same cut-off as the one-sided Jacobi of LAPACK's xGESVJ for small
+// columns).
 template <class T>
 static __device__ void cta_jacobi_t(T* J, int p, int c, T* Vr, Smem& s, T tol) {
   int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -111,6 +117,9 @@ static __device__ void cta_jacobi_t(T* J, int p, int c, T* Vr, Smem& s, T tol) {
     s.ivals[2] = 0;
     s.ivals[3] = 0;
   }
+  double fro = 0.0;
+  for (int idx = tid; idx < p * c; idx += HM_THREADS) fro += (double)J[idx] * (double)J[idx];
+  const T negl = (T)(1e-30 * block_sum(fro, s));
   __syncthreads();
   if (c < 2) return;
   int N = c + (c & 1);
@@ -148,7 +157,7 @@ static __device__ void cta_jacobi_t(T* J, int p, int c, T* Vr, Smem& s, T tol) {
         al = warp_sum(al);
         be = warp_sum(be);
         ga = warp_sum(ga);
-        if (al == T(0) || be == T(0)) continue;
+        if (al <= negl || be <= negl) continue;
         if (fabs(ga) <= tol * sqrt(al) * sqrt(be)) continue;
         T zeta = (be - al) / (T(2) * ga);
         T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
@@ -704,9 +713,16 @@ static __device__ void cta_order_sigma(int c, Smem& s) {
   __syncthreads();
 }
 
-// "Choose new rank k": smallest k with sum_{i>k} s_i^2 <= eps^2 sum_i s_i^2.
-static __device__ int cta_choose_rank(int c, double eps, Smem& s) {
-  if (threadIdx.x == 0) {
+// "Choose new rank k": smallest k with sum_{i>k} s_i^2 <= eps^2 sum_i s_i^2
+// (rule 0, relative Frobenius), or the number of s_i > eps s_1 (rule 1,
+// relative spectral).
+static __device__ int cta_choose_rank(int c, double eps, Smem& s, int rule = 0) {
+  if (threadIdx.x == 0 && rule == 1) {
+    double s1 = c > 0 ? s.sigma[s.order[0]] : 0.0;
+    int k = 0;
+    while (k < c && s.sigma[s.order[k]] > eps * s1) ++k;
+    s.ivals[1] = k;
+  } else if (threadIdx.x == 0) {
     double total = 0.0;
     for (int i = 0; i < c; ++i) {
       double x = s.sigma[s.order[i]];
@@ -759,7 +775,7 @@ static __device__ __forceinline__ double qr_flops(double rows, double cols) {
 }
 
 static __device__ int trunc_core(const TruncIn& in, double eps, int cap, double* U, int ldu, double* V, int ldv,
-                          int* status, Smem& s, double* flops = nullptr) {
+                          int* status, Smem& s, double* flops = nullptr, int rule = 0) {
   int tid = threadIdx.x;
   int m = in.m;
   int q[2] = {0, 0};
@@ -812,7 +828,7 @@ static __device__ int trunc_core(const TruncIn& in, double eps, int cap, double*
   __syncthreads();
   cta_jacobi(J, p, c, Vr, s);
   cta_sort_sigma(J, p, c, s);
-  int k = cta_choose_rank(c, eps, s);
+  int k = cta_choose_rank(c, eps, s, rule);
   if (flops && tid == 0) {
     double f = 0.0;
     for (int j = 0; j < in.nb; ++j) {

@@ -941,6 +941,35 @@ struct Sym {
     (void)inmax;
   }
 
+  // C (m x n at cloc, ldc) += alpha Ahat Bhat^T of a product in low-rank
+  // form, exactly (Fig. rkupdate, dense target).
+  void dense_update(double alpha, const SProd& P, int64_t m, int64_t n, int64_t cloc, int ldc, int cobj) {
+    if (P.aid && P.btr) throw HmError(HMAT_ERR_INTERNAL, "dense update: transposed identity product");
+    HTask t = blank(P.aid || P.bid ? T_ADD : T_GEMM);
+    t.m = (int)m;
+    t.n = (int)n;
+    t.alpha = alpha;
+    t.c = cloc;
+    t.ldc = ldc;
+    if (P.aid) {
+      t.flags = F_TRANS;  // C += alpha Bhat^T
+      t.a = P.b;
+      t.lda = P.ldb;
+    } else if (P.bid) {
+      t.a = P.a;
+      t.lda = P.lda;
+    } else {
+      t.a = P.a;
+      t.lda = P.lda;
+      t.b = P.b;
+      t.ldb = P.ldb;
+      t.wa = P.wcode;
+      t.flags = P.btr ? F_B_TRANS : 0;
+    }
+    std::vector<int> reads = P.objs;
+    S.emit(t, reads, {cobj});
+  }
+
   void add_product(double alpha, SProd& P, SAcc& a) {
     int64_t m = rc(a.t).size, n = cc(a.r).size;
     if (a.dense) {
@@ -1113,6 +1142,119 @@ struct Sym {
     return L;
   }
 
+  // Block (t, r) of Z is a low-rank leaf (or a temporary) while the update
+  // is finer: four temporaries, row-restricted views of Z's factors, receive
+  // the updates of the sons through fill(i, j, target); then Fig. rkmerge
+  // (rowmerge of the block columns, then of the row) writes the merged
+  // result back (Fig. flush, third case; the standard multiplication does
+  // the same).
+  template <class F>
+  void via_temporaries(int tcl, int rcl, STarget z, F fill) {
+    if (!z.tmp && z.M->kind(z.b) != 2) throw HmError(HMAT_ERR_INTERNAL, "temporaries: dense target");
+    SLow base = z.tmp ? *z.tmp : leaf_low(z.M, z.b);
+    const CNodeH& tt = rc(tcl);
+    const CNodeH& rr = cc(rcl);
+    int64_t m = tt.size, n = rr.size;
+    if (tt.nsons != 2 || rr.nsons != 2) throw HmError(HMAT_ERR_ARG, "rkmerge needs binary cluster trees");
+    SLow tmp[2][2];
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) {
+        SLow& T = tmp[i][j];
+        T = base;
+        T.own = false;
+        T.u = base.u + (rc(tt.son[i]).off - tt.off);
+        T.v = base.v + (cc(rr.son[j]).off - rr.off);
+        T.cap = capof(rc(tt.son[i]).size, cc(rr.son[j]).size);
+        T.hold = base.hold;
+      }
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) {
+        STarget c;
+        c.tmp = &tmp[i][j];
+        c.t = tt.son[i];
+        c.r = rr.son[j];
+        fill(i, j, c);
+      }
+    // Fig. rkmerge: merge the block columns (rowmerge of adjoints), then the row
+    SLow col[2];
+    for (int j = 0; j < 2; ++j) {
+      int64_t nrj = cc(rr.son[j]).size;
+      SLow& C = col[j];
+      C.cap = capof(nrj, m);
+      own_storage(C, nrj, m);  // "A" role: r_j x cap, "B" role: t x cap
+      HTask t = blank(T_ROWMERGE);
+      t.m = (int)nrj;
+      t.p = (int)rc(tt.son[0]).size;
+      t.q = (int)rc(tt.son[1]).size;
+      t.a = tmp[0][j].v;
+      t.lda = tmp[0][j].ldv;
+      t.b = tmp[0][j].u;
+      t.ldb = tmp[0][j].ldu;
+      t.wa = tmp[0][j].zero ? 0 : tmp[0][j].wcode;
+      t.c = tmp[1][j].v;
+      t.ldc = tmp[1][j].ldv;
+      t.d = tmp[1][j].u;
+      t.ldd = tmp[1][j].ldu;
+      t.wb = tmp[1][j].zero ? 0 : tmp[1][j].wcode;
+      t.e = C.u;
+      t.lde = C.ldu;
+      t.f = C.v;
+      t.ldf = C.ldv;
+      t.rout = C.slot;
+      t.cap = C.cap;
+      int64_t l = (tmp[0][j].zero ? 0 : tmp[0][j].wmax) + (tmp[1][j].zero ? 0 : tmp[1][j].wmax);
+      if (l > HM_LMAX_HOST) throw HmError(HMAT_ERR_RANK, "merged width exceeds the truncation limit");
+      int ws = S.alloc(rk_ws(nrj, m, l) + (int64_t)nrj * l + (mixed ? m * l + rand_ws(nrj, m, l) : 0));
+      t.ws = S.chunk_loc(ws);
+      std::vector<int> reads;
+      for (int i = 0; i < 2; ++i)
+        if (tmp[i][j].obj >= 0) reads.push_back(tmp[i][j].obj);
+      S.emit(t, reads, {C.obj, S.chunk_obj(ws)});
+      set_features(tcl, rr.son[j]);
+      S.release(ws);
+      C.wcode = width_from_slot(C.slot);
+      C.zero = false;
+    }
+    SLow out = base;
+    if (z.tmp) {
+      own_storage(*z.tmp, m, n);
+      out = *z.tmp;
+    }
+    HTask t = blank(T_ROWMERGE);
+    t.m = (int)m;
+    t.p = (int)cc(rr.son[0]).size;
+    t.q = (int)cc(rr.son[1]).size;
+    t.a = col[0].v;  // column j = Bc_j Ac_j^T: "A" role Bc_j (t x k), "B" role Ac_j (r_j x k)
+    t.lda = col[0].ldv;
+    t.b = col[0].u;
+    t.ldb = col[0].ldu;
+    t.wa = col[0].wcode;
+    t.c = col[1].v;
+    t.ldc = col[1].ldv;
+    t.d = col[1].u;
+    t.ldd = col[1].ldu;
+    t.wb = col[1].wcode;
+    t.e = out.u;
+    t.lde = out.ldu;
+    t.f = out.v;
+    t.ldf = out.ldv;
+    t.rout = out.slot;
+    t.cap = out.cap;
+    int64_t l = (int64_t)col[0].cap + col[1].cap;
+    if (l > HM_LMAX_HOST) throw HmError(HMAT_ERR_RANK, "merged width exceeds the truncation limit");
+    int ws = S.alloc(rk_ws(m, n, l) + (int64_t)m * l + (mixed ? n * l + rand_ws(m, n, l) : 0));
+    t.ws = S.chunk_loc(ws);
+    S.emit(t, {col[0].obj, col[1].obj}, {out.obj, S.chunk_obj(ws)});
+    set_features(tcl, rcl);
+    S.release(ws);
+    if (z.tmp) {
+      z.tmp->wcode = width_from_slot(z.tmp->slot);
+      z.tmp->zero = false;
+    } else {
+      z.M->zero[(size_t)z.b] = 0;
+    }
+  }
+
   // Fig. flush
   void flush(SAcc& a, STarget z) {
     int64_t m = rc(a.t).size, n = cc(a.r).size;
@@ -1176,112 +1318,148 @@ struct Sym {
         }
     } else {
       // (t, r) is a leaf of Z with pending products: temporaries + rkmerge
-      if (!z.tmp && z.M->kind(z.b) != 2) throw HmError(HMAT_ERR_INTERNAL, "flush: pending products on a dense leaf");
-      SLow base = z.tmp ? *z.tmp : leaf_low(z.M, z.b);
-      const CNodeH& tt = rc(a.t);
-      const CNodeH& rr = cc(a.r);
-      if (tt.nsons != 2 || rr.nsons != 2) throw HmError(HMAT_ERR_ARG, "rkmerge needs binary cluster trees");
-      SLow tmp[2][2];
-      for (int i = 0; i < 2; ++i)
-        for (int j = 0; j < 2; ++j) {
-          SLow& T = tmp[i][j];
-          T = base;
-          T.own = false;
-          T.u = base.u + (rc(tt.son[i]).off - tt.off);
-          T.v = base.v + (cc(rr.son[j]).off - rr.off);
-          T.cap = capof(rc(tt.son[i]).size, cc(rr.son[j]).size);
-          T.hold = base.hold;
-        }
       auto sons = split(a);
-      for (int i = 0; i < 2; ++i)
-        for (int j = 0; j < 2; ++j) {
-          STarget c;
-          c.tmp = &tmp[i][j];
-          c.t = tt.son[i];
-          c.r = rr.son[j];
-          flush(sons[(size_t)i][(size_t)j], c);
-        }
-      // Fig. rkmerge: merge the block columns (rowmerge of adjoints), then the row
-      SLow col[2];
-      for (int j = 0; j < 2; ++j) {
-        int64_t nrj = cc(rr.son[j]).size;
-        SLow& C = col[j];
-        C.cap = capof(nrj, m);
-        own_storage(C, nrj, m);  // "A" role: r_j x cap, "B" role: t x cap
-        HTask t = blank(T_ROWMERGE);
-        t.m = (int)nrj;
-        t.p = (int)rc(tt.son[0]).size;
-        t.q = (int)rc(tt.son[1]).size;
-        t.a = tmp[0][j].v;
-        t.lda = tmp[0][j].ldv;
-        t.b = tmp[0][j].u;
-        t.ldb = tmp[0][j].ldu;
-        t.wa = tmp[0][j].zero ? 0 : tmp[0][j].wcode;
-        t.c = tmp[1][j].v;
-        t.ldc = tmp[1][j].ldv;
-        t.d = tmp[1][j].u;
-        t.ldd = tmp[1][j].ldu;
-        t.wb = tmp[1][j].zero ? 0 : tmp[1][j].wcode;
-        t.e = C.u;
-        t.lde = C.ldu;
-        t.f = C.v;
-        t.ldf = C.ldv;
-        t.rout = C.slot;
-        t.cap = C.cap;
-        int64_t l = (tmp[0][j].zero ? 0 : tmp[0][j].wmax) + (tmp[1][j].zero ? 0 : tmp[1][j].wmax);
-        if (l > HM_LMAX_HOST) throw HmError(HMAT_ERR_RANK, "merged width exceeds the truncation limit");
-        int ws = S.alloc(rk_ws(nrj, m, l) + (int64_t)nrj * l + (mixed ? m * l + rand_ws(nrj, m, l) : 0));
-        t.ws = S.chunk_loc(ws);
-        std::vector<int> reads;
-        for (int i = 0; i < 2; ++i)
-          if (tmp[i][j].obj >= 0) reads.push_back(tmp[i][j].obj);
-        S.emit(t, reads, {C.obj, S.chunk_obj(ws)});
-        set_features(a.t, rr.son[j]);
-        S.release(ws);
-        C.wcode = width_from_slot(C.slot);
-        C.zero = false;
-      }
-      SLow out = base;
-      if (z.tmp) {
-        own_storage(*z.tmp, m, n);
-        out = *z.tmp;
-      }
-      HTask t = blank(T_ROWMERGE);
-      t.m = (int)m;
-      t.p = (int)cc(rr.son[0]).size;
-      t.q = (int)cc(rr.son[1]).size;
-      t.a = col[0].v;  // column j = Bc_j Ac_j^T: "A" role Bc_j (t x k), "B" role Ac_j (r_j x k)
-      t.lda = col[0].ldv;
-      t.b = col[0].u;
-      t.ldb = col[0].ldu;
-      t.wa = col[0].wcode;
-      t.c = col[1].v;
-      t.ldc = col[1].ldv;
-      t.d = col[1].u;
-      t.ldd = col[1].ldu;
-      t.wb = col[1].wcode;
-      t.e = out.u;
-      t.lde = out.ldu;
-      t.f = out.v;
-      t.ldf = out.ldv;
-      t.rout = out.slot;
-      t.cap = out.cap;
-      int64_t l = (int64_t)col[0].cap + col[1].cap;
-      if (l > HM_LMAX_HOST) throw HmError(HMAT_ERR_RANK, "merged width exceeds the truncation limit");
-      int ws = S.alloc(rk_ws(m, n, l) + (int64_t)m * l + (mixed ? n * l + rand_ws(m, n, l) : 0));
-      t.ws = S.chunk_loc(ws);
-      S.emit(t, {col[0].obj, col[1].obj}, {out.obj, S.chunk_obj(ws)});
-      set_features(a.t, a.r);
-      S.release(ws);
-      if (z.tmp) {
-        z.tmp->wcode = width_from_slot(z.tmp->slot);
-        z.tmp->zero = false;
-      } else {
-        z.M->zero[(size_t)z.b] = 0;
-      }
+      via_temporaries(a.t, a.r, z, [&](int i, int j, STarget c) { flush(sons[(size_t)i][(size_t)j], c); });
     }
     a.P.clear();
     a.R = SLow();
+  }
+
+  // ---- standard multiplication (Section 4 before "Accumulated updates") ------
+  // The product P of a leaf pair restricted to rows ro.. (rn of them) of its
+  // row cluster and columns co.. (cn) of its column cluster: row ranges of
+  // the factors; an identity factor becomes a block of the dense one
+  // (Section 3, "Splitting": no arithmetic).
+  SProd restrict_prod(const SProd& P, int64_t ro, int64_t rn, int64_t co, int64_t cn) const {
+    SProd Q = P;
+    if (P.aid) {  // A = I, Bhat^T given (m x n): block (t', r') of Bhat^T, A = I
+      Q.b = P.btr ? P.b + ro + co * P.ldb : P.b + co + ro * P.ldb;
+      Q.wcode = Q.wcap = (int)rn;
+    } else if (P.bid) {  // B = I, Ahat (m x n): block (t', r') of Ahat
+      Q.a = P.a + ro + co * P.lda;
+      Q.wcode = Q.wcap = (int)cn;
+    } else {
+      Q.a = P.a + ro;
+      Q.b = P.btr ? P.b + co * P.ldb : P.b + co;
+    }
+    return Q;
+  }
+
+  // Fig. rkupdate of alpha P into the block (t, r) of Z (or a temporary):
+  // dense leaf N += alpha Ahat Bhat^T, admissible leaf rkadd (one truncation
+  // per product), subdivided block the product restricted to the sons.
+  void rkupdate_prod(double alpha, const SProd& P, int t, int r, STarget z) {
+    int64_t m = rc(t).size, n = cc(r).size;
+    if (z.tmp) {
+      rkadd_into(alpha, P, *z.tmp, m, n, t, r);
+      return;
+    }
+    hmat* M = z.M;
+    int kind = M->kind(z.b);
+    if (kind == 1) {
+      dense_update(alpha, P, m, n, hl(M, z.b), (int)m, obj_of(M, z.b));
+      M->zero[(size_t)z.b] = 0;
+    } else if (kind == 2) {
+      SLow L = leaf_low(M, z.b);
+      rkadd_into(alpha, P, L, m, n, t, r);
+      M->zero[(size_t)z.b] = 0;
+    } else {
+      const CNodeH& tt = rc(t);
+      const CNodeH& rr = cc(r);
+      for (int i = 0; i < tt.nsons; ++i)
+        for (int j = 0; j < rr.nsons; ++j) {
+          const CNodeH& ti = rc(tt.son[i]);
+          const CNodeH& rj = cc(rr.son[j]);
+          SProd Q = restrict_prod(P, ti.off - tt.off, ti.size, rj.off - rr.off, rj.size);
+          rkupdate_prod(alpha, Q, tt.son[i], rr.son[j], target_of(M, M->bt->child(z.b, i, j), tt.son[i], rr.son[j]));
+        }
+    }
+  }
+
+  // Z|_{t x r} <- Z|_{t x r} + alpha X|_{t x s} Y|_{s x r} with every product
+  // of a leaf pair applied at once (the standard form the accumulated one is
+  // compared with; Section 4, the remark after the complexity theorem).
+  void mult_std(double alpha, const hmat* X, int xb, const hmat* Y, int yb, STarget z) {
+    if (X->kind(xb) != 0 || Y->kind(yb) != 0) {
+      SProd P = leaf_product(X, xb, Y, yb);
+      if (!P.zero) rkupdate_prod(alpha, P, z.t, z.r, z);
+      return;
+    }
+    int ns = X->sc(xb).nsons;
+    if (!z.tmp && z.M->kind(z.b) == 0) {
+      const CNodeH& tt = rc(z.t);
+      const CNodeH& rr = cc(z.r);
+      for (int i = 0; i < tt.nsons; ++i)
+        for (int j = 0; j < rr.nsons; ++j) {
+          STarget c = target_of(z.M, z.M->bt->child(z.b, i, j), tt.son[i], rr.son[j]);
+          for (int k = 0; k < ns; ++k) mult_std(alpha, X, X->bt->child(xb, i, k), Y, Y->bt->child(yb, k, j), c);
+        }
+      return;
+    }
+    // (t, r) is a leaf of Z (or a temporary) and the product is finer
+    via_temporaries(z.t, z.r, z, [&](int i, int j, STarget c) {
+      for (int k = 0; k < ns; ++k) mult_std(alpha, X, X->bt->child(xb, i, k), Y, Y->bt->child(yb, k, j), c);
+    });
+  }
+
+  // ---- H-LU in the standard form ---------------------------------------------
+  void trsm_L_std(hmat* G, int d, int b) {
+    if (G->kind(b) != 0) {
+      trsm_L(G, d, b);  // leaf: the same H-solve as the accumulated form
+      return;
+    }
+    const CNodeH& t = G->tc(b);
+    const CNodeH& r = G->sc(b);
+    for (int j = 0; j < r.nsons; ++j)
+      for (int i = 0; i < t.nsons; ++i) {
+        int bi = G->bt->child(b, i, j);
+        trsm_L_std(G, G->bt->child(d, i, i), bi);
+        for (int l = i + 1; l < t.nsons; ++l)
+          mult_std(-1.0, G, G->bt->child(d, l, i), G, bi, target_of(G, G->bt->child(b, l, j), t.son[l], r.son[j]));
+      }
+  }
+
+  void trsm_U_std(hmat* G, int d, int b) {
+    if (G->kind(b) != 0) {
+      trsm_U(G, d, b);
+      return;
+    }
+    const CNodeH& r = G->tc(b);
+    const CNodeH& t = G->sc(b);
+    for (int j = 0; j < r.nsons; ++j)
+      for (int i = 0; i < t.nsons; ++i) {
+        int bi = G->bt->child(b, j, i);
+        trsm_U_std(G, G->bt->child(d, i, i), bi);
+        for (int l = i + 1; l < t.nsons; ++l)
+          mult_std(-1.0, G, bi, G, G->bt->child(d, i, l), target_of(G, G->bt->child(b, j, l), r.son[j], t.son[l]));
+      }
+  }
+
+  // Block LU with Schur complement (Section 6) with every update applied at
+  // once.
+  void lu_std(hmat* G, int b) {
+    int kind = G->kind(b);
+    if (kind == 1) {
+      HTask t = blank(T_LU);
+      t.m = (int)G->rows(b);
+      t.a = hl(G, b);
+      t.lda = t.m;
+      S.emit(t, {}, {obj_of(G, b)});
+      return;
+    }
+    if (kind != 0) throw HmError(HMAT_ERR_ARG, "H-LU: admissible diagonal block");
+    const CNodeH& t = G->tc(b);
+    int p = t.nsons;
+    for (int i = 0; i < p; ++i) {
+      int di = G->bt->child(b, i, i);
+      lu_std(G, di);
+      for (int j = i + 1; j < p; ++j) trsm_L_std(G, di, G->bt->child(b, i, j));
+      for (int j = i + 1; j < p; ++j) trsm_U_std(G, di, G->bt->child(b, j, i));
+      for (int j = i + 1; j < p; ++j)
+        for (int l = i + 1; l < p; ++l)
+          mult_std(-1.0, G, G->bt->child(b, j, i), G, G->bt->child(b, i, l),
+                   target_of(G, G->bt->child(b, j, l), t.son[j], t.son[l]));
+    }
   }
 
   // ---- H-LU with accumulators --------------------------------------------------
@@ -1613,6 +1791,7 @@ struct RunResult {
   unsigned long long truncations = 0;
   double flops = 0.0;
   double flops32 = 0.0;
+  double bytes = 0.0;  // algorithmic bytes of the tasks
   unsigned long long type_ns[16] = {0}, type_cnt[16] = {0}, wait_ns = 0;
   unsigned long long rand_ok = 0, rand_fail = 0, sketch_attempts = 0, sketch_cols = 0;
   unsigned long long bad[6] = {0, 0, 0, 0, 0, 0};
@@ -1710,6 +1889,7 @@ struct LaunchOpts {
   bool record = false;
   std::vector<float>* rec_out = nullptr;
   uint64_t seed = 0;  // 0: the default seed of the randomised sketches
+  int rank_rule = 0;  // HMAT_REL_FRO or HMAT_REL_SPEC
 };
 
 void upload_sched(hmat_ctx* ctx, const Sched& S, DevSched& D) {
@@ -1751,6 +1931,7 @@ RunResult launch_sched(hmat_ctx* ctx, const Sched& S, DevSched& D, double* hbase
   e.fail_task = (long long*)dmp + 5;
   e.flops = (double*)((unsigned long long*)dmp + 3);
   e.flops32 = (double*)((unsigned long long*)dmp + 4);
+  e.bytes = (double*)((unsigned long long*)dmp + 6);
   e.type_ns = (unsigned long long*)dmp + 8;
   e.type_cnt = (unsigned long long*)dmp + 24;
   e.wait_ns = (unsigned long long*)dmp + 40;
@@ -1774,6 +1955,7 @@ RunResult launch_sched(hmat_ctx* ctx, const Sched& S, DevSched& D, double* hbase
     e.rec = D.rec.as<float>();
   }
   e.eps = eps;
+  e.rank_rule = lo.rank_rule;
   e.mixed = mixed ? 1 : 0;
   e.rand_min_l = 8;
   e.seed = lo.seed ? lo.seed : 0x5EEDull;
@@ -1827,6 +2009,7 @@ RunResult launch_sched(hmat_ctx* ctx, const Sched& S, DevSched& D, double* hbase
   rr.fail_task = (long long)misc[5] - 1;
   std::memcpy(&rr.flops, &misc[3], sizeof(double));
   std::memcpy(&rr.flops32, &misc[4], sizeof(double));
+  std::memcpy(&rr.bytes, &misc[6], sizeof(double));
   return rr;
 }
 
@@ -2030,15 +2213,35 @@ std::vector<DenseLeafDesc> layout_from_csr(hmat* H, const hmat_btree* bt, int64_
     return dl;
 }
 
+// Checks of the options every factorisation shares: the mode (standard only
+// where the call supports it) and the rank rule (the spectral one needs the
+// exact FP64 truncations: the mixed form's checks bound Frobenius residuals).
+void check_opts(const hmat_opts* opts, bool standard_ok) {
+  if (!opts) return;
+  require(opts->mode == HMAT_ACCUMULATED || (standard_ok && opts->mode == HMAT_STANDARD),
+          standard_ok ? "mode must be HMAT_ACCUMULATED or HMAT_STANDARD" : "this call has the accumulated form only");
+  require(opts->rank_rule == HMAT_REL_FRO || opts->rank_rule == HMAT_REL_SPEC, "rank_rule must be REL_FRO or REL_SPEC");
+  require(opts->rank_rule == HMAT_REL_FRO || opts->precision == HMAT_FP64,
+          "the relative spectral rank rule needs precision HMAT_FP64");
+}
+
 // Symbolic H-LU of H into S (ordered by level); returns host seconds.
-double schedule_lu(hmat* H, int64_t max_rank, bool mixed, Sched& S) {
+double schedule_lu(hmat* H, int64_t max_rank, bool mixed, bool standard, Sched& S) {
   auto t0 = std::chrono::steady_clock::now();
   S.next_slot = H->nslots;
   Sym sym(S, *H->bt->R, *H->bt->C, max_rank);
   sym.mixed = mixed;
   sym.add_matrix(H);
-  SAcc root = sym.acc_new(0, 0);
-  sym.lu(H, 0, root);
+  if (standard) {
+    sym.lu_std(H, 0);
+  } else {
+    if (standard) {
+      sym.lu_std(H, 0);
+    } else {
+      SAcc root = sym.acc_new(0, 0);
+      sym.lu(H, 0, root);
+    }
+  }
   S.order_by_level();
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
@@ -2055,9 +2258,12 @@ hmat_status hmat_analyze_lu(const hmat_btree* bt, int64_t n, const int64_t* rowp
     layout_from_csr(&H, bt, n, rowptr, colidx, val);
     int64_t mr = (opts && opts->max_rank > 0) ? std::min<int64_t>(opts->max_rank, H.max_rank) : H.max_rank;
     Sched S;
-    double secs = schedule_lu(&H, mr, opts && opts->precision == HMAT_MIXED, S);
+    check_opts(opts, true);
+    double secs = schedule_lu(&H, mr, opts && opts->precision == HMAT_MIXED, opts && opts->mode == HMAT_STANDARD, S);
     hmat_stats s = H.st;
     s.tasks = (int64_t)S.tasks.size();
+    s.truncations = 0;  // truncation tasks of the schedule (those whose product is zero skip at run time)
+    for (const HTask& t : S.tasks) s.truncations += (t.type == T_RKADD || t.type == T_ROWMERGE) ? 1 : 0;
     s.schedule_seconds = secs;
     s.levels = S.levels();
     s.critical_flops = S.critical_flops();
@@ -2249,6 +2455,7 @@ struct SchedCache {
   std::vector<std::vector<char>> zero_after;
   int64_t mr = 0;
   bool mixed = false;
+  int mode = HMAT_ACCUMULATED;
   double* base = nullptr;
   Sched S;
   DevSched D;
@@ -2266,6 +2473,7 @@ uint64_t hash_flags(const std::vector<char>& v) {
 // the batch; each instance's leaf rank slots get their own range.
 void lu_batch(hmat_ctx* ctx, hmat* const* Hs, int count, const hmat_opts* opts) {
   check_ctx(ctx);
+  check_opts(opts, true);
   require(Hs != nullptr && count >= 1, "no H-matrices");
   for (int i = 0; i < count; ++i) require(Hs[i] != nullptr && Hs[i]->ctx == ctx, "null H-matrix or other context");
   double eps = opts ? opts->eps : 0.0;
@@ -2286,7 +2494,9 @@ void lu_batch(hmat_ctx* ctx, hmat* const* Hs, int count, const hmat_opts* opts) 
   for (int i = 0; i < count; ++i) zh[(size_t)i] = hash_flags(Hs[i]->zero);
   bool reuse = opts && opts->reuse_schedule;
   SchedCache* C = Hs[0]->cache.get();
-  bool hit = reuse && C && C->mixed == mixed && C->mr == mr0 && C->base == base && (int)C->mats.size() == count &&
+  bool standard = opts && opts->mode == HMAT_STANDARD;
+  bool hit = reuse && C && C->mixed == mixed && C->mode == (standard ? HMAT_STANDARD : HMAT_ACCUMULATED) &&
+             C->mr == mr0 && C->base == base && (int)C->mats.size() == count &&
              C->zero_hash == zh;
   for (int i = 0; hit && i < count; ++i) hit = C->mats[(size_t)i] == Hs[i] && C->trees[(size_t)i] == Hs[i]->bt;
   std::shared_ptr<SchedCache> fresh;
@@ -2304,8 +2514,12 @@ void lu_batch(hmat_ctx* ctx, hmat* const* Hs, int count, const hmat_opts* opts) 
     Sym sym(S, *H->bt->R, *H->bt->C, mr);
     sym.mixed = mixed;
     sym.add_matrix(H, (int64_t)(H->store.as<double>() - base), slotbase[(size_t)i]);
-    SAcc root = sym.acc_new(0, 0);
-    sym.lu(H, 0, root);
+    if (standard) {
+      sym.lu_std(H, 0);
+    } else {
+      SAcc root = sym.acc_new(0, 0);
+      sym.lu(H, 0, root);
+    }
   }
   S.order_by_level();
   upload_sched(ctx, S, C->D);
@@ -2317,6 +2531,7 @@ void lu_batch(hmat_ctx* ctx, hmat* const* Hs, int count, const hmat_opts* opts) 
   C->zero_hash = zh;
   C->mr = mr0;
   C->mixed = mixed;
+  C->mode = standard ? HMAT_STANDARD : HMAT_ACCUMULATED;
   C->base = base;
   if (reuse) Hs[0]->cache = fresh;
   } else {
@@ -2332,6 +2547,7 @@ void lu_batch(hmat_ctx* ctx, hmat* const* Hs, int count, const hmat_opts* opts) 
   lo.record = opts && opts->record_training;
   lo.rec_out = &Hs[0]->train;
   lo.seed = opts ? opts->seed : 0;
+  lo.rank_rule = opts ? opts->rank_rule : 0;
   RunResult rr = launch_sched(ctx, S, C->D, base, allranks.as<int>(), eps, spin, nullptr, nullptr, mixed, lo);
   for (int i = 0; i < count; ++i)
     HM_CUDA(cudaMemcpyAsync(Hs[i]->ranks.p, allranks.as<int>() + slotbase[(size_t)i], (size_t)Hs[i]->nslots * sizeof(int),
@@ -2349,6 +2565,8 @@ void lu_batch(hmat_ctx* ctx, hmat* const* Hs, int count, const hmat_opts* opts) 
     st.truncations = (int64_t)rr.truncations;
     st.flops = rr.flops;
     st.flops32 = rr.flops32;
+  st.bytes = rr.bytes;
+    st.bytes = rr.bytes;
     st.rand_truncations = (int64_t)rr.rand_ok;
     st.rand_fallbacks = (int64_t)rr.rand_fail;
     st.sketch_attempts = (int64_t)rr.sketch_attempts;
@@ -2377,6 +2595,7 @@ void lu_batch(hmat_ctx* ctx, hmat* const* Hs, int count, const hmat_opts* opts) 
 // In-place H-Cholesky with accumulated updates: one schedule, one launch.
 void chol_run(hmat_ctx* ctx, hmat* G, const hmat_opts* opts) {
   check_ctx(ctx);
+  check_opts(opts, false);
   require(G && G->ctx == ctx, "null H-matrix or other context");
   double eps = opts ? opts->eps : 0.0;
   require(eps >= 0.0, "eps must be >= 0");
@@ -2405,6 +2624,7 @@ void chol_run(hmat_ctx* ctx, hmat* G, const hmat_opts* opts) {
   lo.record = opts && opts->record_training;
   lo.rec_out = &G->train;
   lo.seed = opts ? opts->seed : 0;
+  lo.rank_rule = opts ? opts->rank_rule : 0;
   RunResult rr = launch_sched(ctx, S, D, G->store.as<double>(), allranks.as<int>(), eps, spin, nullptr, nullptr,
                               mixed, lo);
   HM_CUDA(cudaMemcpyAsync(G->ranks.p, allranks.as<int>(), (size_t)G->nslots * sizeof(int), cudaMemcpyDeviceToDevice,
@@ -2416,6 +2636,7 @@ void chol_run(hmat_ctx* ctx, hmat* G, const hmat_opts* opts) {
   st.truncations = (int64_t)rr.truncations;
   st.flops = rr.flops;
   st.flops32 = rr.flops32;
+  st.bytes = rr.bytes;
   st.rand_truncations = (int64_t)rr.rand_ok;
   st.rand_fallbacks = (int64_t)rr.rand_fail;
   st.sketch_attempts = (int64_t)rr.sketch_attempts;
@@ -2445,6 +2666,7 @@ void chol_run(hmat_ctx* ctx, hmat* G, const hmat_opts* opts) {
 // H-matrix for H_12, H_21 lives for the call; one schedule, one launch.
 void invert_run(hmat_ctx* ctx, hmat* G, const hmat_opts* opts) {
   check_ctx(ctx);
+  check_opts(opts, false);
   require(G && G->ctx == ctx, "null H-matrix or other context");
   double eps = opts ? opts->eps : 0.0;
   require(eps >= 0.0, "eps must be >= 0");
@@ -2492,6 +2714,7 @@ void invert_run(hmat_ctx* ctx, hmat* G, const hmat_opts* opts) {
   lo.record = opts && opts->record_training;
   lo.rec_out = &G->train;
   lo.seed = opts ? opts->seed : 0;
+  lo.rank_rule = opts ? opts->rank_rule : 0;
   RunResult rr = launch_sched(ctx, S, D, base, allranks.as<int>(), eps, spin, nullptr, nullptr, mixed, lo);
   HM_CUDA(cudaMemcpyAsync(G->ranks.p, allranks.as<int>(), (size_t)G->nslots * sizeof(int), cudaMemcpyDeviceToDevice,
                           ctx->stream));
@@ -2502,6 +2725,7 @@ void invert_run(hmat_ctx* ctx, hmat* G, const hmat_opts* opts) {
   st.truncations = (int64_t)rr.truncations;
   st.flops = rr.flops;
   st.flops32 = rr.flops32;
+  st.bytes = rr.bytes;
   st.rand_truncations = (int64_t)rr.rand_ok;
   st.rand_fallbacks = (int64_t)rr.rand_fail;
   st.sketch_attempts = (int64_t)rr.sketch_attempts;
@@ -2528,6 +2752,7 @@ void invert_run(hmat_ctx* ctx, hmat* G, const hmat_opts* opts) {
 // the root pair, one flush into Z, one launch.
 void addmul_run(hmat_ctx* ctx, double alpha, const hmat* X, const hmat* Y, hmat* Z, const hmat_opts* opts) {
   check_ctx(ctx);
+  check_opts(opts, true);
   require(X && Y && Z, "null H-matrix");
   require(X->ctx == ctx && Y->ctx == ctx && Z->ctx == ctx, "H-matrix of another context");
   require(Z != X && Z != Y, "addmul: Z must not be X or Y");
@@ -2557,14 +2782,18 @@ void addmul_run(hmat_ctx* ctx, double alpha, const hmat* X, const hmat* Y, hmat*
   Sym sym(S, *T, *T, mr);
   sym.mixed = mixed;
   for (int i = 0; i < 3; ++i) sym.add_matrix(M[i], (int64_t)(M[i]->store.as<double>() - base), slotbase[i]);
-  SAcc root = sym.acc_new(0, 0);
-  sym.addproduct(alpha, X, 0, Y, 0, root);
   STarget z;
   z.M = Z;
   z.b = 0;
   z.t = 0;
   z.r = 0;
-  sym.flush(root, z);
+  if (opts && opts->mode == HMAT_STANDARD) {
+    sym.mult_std(alpha, X, 0, Y, 0, z);
+  } else {
+    SAcc root = sym.acc_new(0, 0);
+    sym.addproduct(alpha, X, 0, Y, 0, root);
+    sym.flush(root, z);
+  }
   S.order_by_level();
   upload_sched(ctx, S, D);
   double sched_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -2577,6 +2806,7 @@ void addmul_run(hmat_ctx* ctx, double alpha, const hmat* X, const hmat* Y, hmat*
   lo.record = opts && opts->record_training;
   lo.rec_out = &Z->train;
   lo.seed = opts ? opts->seed : 0;
+  lo.rank_rule = opts ? opts->rank_rule : 0;
   RunResult rr = launch_sched(ctx, S, D, base, allranks.as<int>(), eps, spin, nullptr, nullptr, mixed, lo);
   HM_CUDA(cudaMemcpyAsync(Z->ranks.p, allranks.as<int>() + slotbase[2], (size_t)Z->nslots * sizeof(int),
                           cudaMemcpyDeviceToDevice, ctx->stream));
@@ -2586,6 +2816,7 @@ void addmul_run(hmat_ctx* ctx, double alpha, const hmat* X, const hmat* Y, hmat*
   st.truncations = (int64_t)rr.truncations;
   st.flops = rr.flops;
   st.flops32 = rr.flops32;
+  st.bytes = rr.bytes;
   st.rand_truncations = (int64_t)rr.rand_ok;
   st.rand_fallbacks = (int64_t)rr.rand_fail;
   st.sketch_attempts = (int64_t)rr.sketch_attempts;
@@ -2701,6 +2932,126 @@ hmat_status trunc_lowrank_batched(hmat_ctx* ctx, int64_t count, const int64_t* m
     HM_CUDA(cudaStreamSynchronize(ctx->stream));
     if (randomised) *randomised = status[1];
     if (status[0]) throw HmError(status[0], "trunc_lowrank: device status");
+  });
+}
+
+hmat_status hmat_pcg(hmat_ctx* ctx, const hmat* LU, int64_t n, const int64_t* rowptr, const int64_t* colidx,
+                     const double* val, int64_t nrhs, const double* B, double* X, double rtol, int64_t maxit,
+                     int64_t* iters, double* relres) {
+  return guarded([&] {
+    check_ctx(ctx);
+    require(LU && rowptr && colidx && val && B && X && iters && relres && nrhs >= 0 && maxit >= 0,
+            "pcg: bad arguments");
+    require(n == LU->n, "pcg: size does not match the factors");
+    require(rtol >= 0.0, "pcg: rtol must be >= 0");
+    if (nrhs == 0 || n == 0) return;
+    cudaStream_t st = ctx->stream;
+    // the CSR in the permuted ordering of the factors
+    const std::vector<int64_t>& perm = LU->bt->R->perm;
+    std::vector<int64_t> iperm((size_t)n);
+    for (int64_t i = 0; i < n; ++i) iperm[(size_t)perm[(size_t)i]] = i;
+    std::vector<int64_t> prp((size_t)n + 1, 0), pci;
+    std::vector<double> pva;
+    pci.reserve((size_t)rowptr[n]);
+    pva.reserve((size_t)rowptr[n]);
+    for (int64_t i = 0; i < n; ++i) {
+      int64_t r = perm[(size_t)i];
+      for (int64_t e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+        require(colidx[e] >= 0 && colidx[e] < n, "pcg: column index out of range");
+        require(std::isfinite(val[e]), "pcg: non-finite matrix value");
+        pci.push_back(iperm[(size_t)colidx[e]]);
+        pva.push_back(val[e]);
+      }
+      prp[(size_t)i + 1] = (int64_t)pci.size();
+    }
+    DevBuf drp, dci, dva, dperm;
+    upload(drp, prp, st);
+    upload(dci, pci, st);
+    upload(dva, pva, st);
+    upload(dperm, perm, st);
+    size_t blk = (size_t)n * nrhs * sizeof(double);
+    DevBuf Bp(blk), Xp(blk), R(blk), Z(blk), P(blk), Q(blk), dd(3 * nrhs * sizeof(double));
+    double* dscal = dd.as<double>();
+    // the solve with the factors as a schedule built once (L then U, Fig. addeval leaves)
+    Sched S;
+    S.next_slot = LU->nslots;
+    Sym sym(S, *LU->bt->R, *LU->bt->C, LU->max_rank);
+    sym.add_matrix(LU);
+    int zobj = S.new_obj();
+    int64_t zx = tag_ext(0, 0);
+    sym.hsolve(LU, 0, TRSM_L, zx, (int)n, zobj, (int)nrhs);
+    sym.hsolve(LU, 0, TRSM_U, zx, (int)n, zobj, (int)nrhs);
+    DevSched D;
+    upload_sched(ctx, S, D);
+    auto precond = [&]() {  // Z <- (LU)^{-1} R
+      HM_CUDA(cudaMemcpyAsync(Z.p, R.p, blk, cudaMemcpyDeviceToDevice, st));
+      RunResult rr = launch_sched(ctx, S, D, LU->store.as<double>(), LU->ranks.as<int>(), 0.0, 0, Z.as<double>(),
+                                  nullptr, false);
+      if (rr.status) throw HmError(rr.status, "pcg: device status of the preconditioner solve");
+    };
+    std::vector<double> h(3 * (size_t)nrhs);
+    auto dots = [&](const DevBuf& a, const DevBuf& b, int slot) {  // into h[slot * nrhs ..]
+      HM_CUDA(launch_col_dots(n, nrhs, a.as<double>(), b.as<double>(), dscal + slot * nrhs, st));
+    };
+    auto fetch = [&]() {
+      HM_CUDA(cudaMemcpyAsync(h.data(), dscal, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+      HM_CUDA(cudaStreamSynchronize(st));
+    };
+    HM_CUDA(launch_permute(B, Bp.as<double>(), dperm.as<int64_t>(), n, nrhs, true, st));
+    HM_CUDA(cudaMemsetAsync(Xp.p, 0, blk, st));
+    HM_CUDA(cudaMemcpyAsync(R.p, Bp.p, blk, cudaMemcpyDeviceToDevice, st));
+    precond();
+    HM_CUDA(cudaMemcpyAsync(P.p, Z.p, blk, cudaMemcpyDeviceToDevice, st));
+    dots(R, Z, 0);
+    dots(Bp, Bp, 1);
+    dots(R, R, 2);
+    fetch();
+    std::vector<double> rz(h.begin(), h.begin() + nrhs), nb((size_t)nrhs), rr2(h.begin() + 2 * nrhs, h.end());
+    for (int64_t c = 0; c < nrhs; ++c) {
+      nb[(size_t)c] = std::sqrt(h[(size_t)(nrhs + c)]);
+      iters[c] = 0;
+    }
+    std::vector<double> coef((size_t)nrhs);
+    for (int64_t it = 0; it < maxit; ++it) {
+      std::vector<char> active((size_t)nrhs);
+      bool any = false;
+      for (int64_t c = 0; c < nrhs; ++c) {
+        active[(size_t)c] = std::sqrt(rr2[(size_t)c]) > rtol * nb[(size_t)c];
+        any = any || active[(size_t)c];
+      }
+      if (!any) break;
+      HM_CUDA(launch_csr_spmv(n, drp.as<int64_t>(), dci.as<int64_t>(), dva.as<double>(), P.as<double>(),
+                              Q.as<double>(), nrhs, st));
+      dots(P, Q, 0);
+      fetch();
+      for (int64_t c = 0; c < nrhs; ++c) coef[(size_t)c] = active[(size_t)c] ? rz[(size_t)c] / h[(size_t)c] : 0.0;
+      HM_CUDA(cudaMemcpyAsync(dscal, coef.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
+      HM_CUDA(launch_cg_xr(n, nrhs, dscal, P.as<double>(), Q.as<double>(), Xp.as<double>(), R.as<double>(), st));
+      precond();
+      dots(R, Z, 0);
+      dots(R, R, 2);
+      fetch();
+      for (int64_t c = 0; c < nrhs; ++c) {
+        coef[(size_t)c] = active[(size_t)c] ? h[(size_t)c] / rz[(size_t)c] : 0.0;
+        if (active[(size_t)c]) {
+          rz[(size_t)c] = h[(size_t)c];
+          rr2[(size_t)c] = h[(size_t)(2 * nrhs + c)];
+          iters[c] += 1;
+        }
+      }
+      HM_CUDA(cudaMemcpyAsync(dscal + nrhs, coef.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
+      HM_CUDA(launch_cg_p(n, nrhs, dscal + nrhs, Z.as<double>(), P.as<double>(), st));
+    }
+    // true relative residuals ||b - A x|| / ||b||
+    HM_CUDA(launch_csr_spmv(n, drp.as<int64_t>(), dci.as<int64_t>(), dva.as<double>(), Xp.as<double>(),
+                            Q.as<double>(), nrhs, st));
+    HM_CUDA(launch_sub(n * nrhs, Bp.as<double>(), Q.as<double>(), R.as<double>(), st));
+    dots(R, R, 0);
+    fetch();
+    for (int64_t c = 0; c < nrhs; ++c)
+      relres[c] = nb[(size_t)c] > 0.0 ? std::sqrt(h[(size_t)c]) / nb[(size_t)c] : 0.0;
+    HM_CUDA(launch_permute(Xp.as<double>(), X, dperm.as<int64_t>(), n, nrhs, false, st));
+    HM_CUDA(cudaStreamSynchronize(st));
   });
 }
 

@@ -596,7 +596,7 @@ __device__ void task_rkadd(const ExecEnv& e, const HTask& t, Smem& s, long long 
   in.SB[0] = SB;
   in.W = W;
   in.Jg = Jg;
-  int k = trunc_core(in, e.eps, t.cap, Uout, t.lde, Vout, t.ldf, e.status, s, &f);
+  int k = trunc_core(in, e.eps, t.cap, Uout, t.lde, Vout, t.ldf, e.status, s, &f, e.rank_rule);
   if (threadIdx.x == 0) {
     if (t.rout >= 0) e.ranks[t.rout] = k;
     atomicAdd(e.counters, 1ull);
@@ -768,7 +768,7 @@ __device__ void task_rowmerge(const ExecEnv& e, const HTask& t, Smem& s, long lo
   in.SB[1] = SB1;
   in.W = W;
   in.Jg = Jg;
-  int k = trunc_core(in, e.eps, t.cap, Uout, t.lde, Vout, t.ldf, e.status, s, &f);
+  int k = trunc_core(in, e.eps, t.cap, Uout, t.lde, Vout, t.ldf, e.status, s, &f, e.rank_rule);
   if (threadIdx.x == 0) {
     if (t.rout >= 0) e.ranks[t.rout] = k;
     atomicAdd(e.counters, 1ull);
@@ -813,6 +813,62 @@ __device__ double task_flops(const ExecEnv& e, const HTask& t) {
     default:
       return 0.0;
   }
+}
+
+// Algorithmic bytes of a task: what it must read and write once (FP64),
+// e.g. 8 [(m + n) l + (m + n) k] for a truncation of stacked width l to rank
+// k; l_in is the stacked width read before the task ran (-1: not a
+// truncation).  Counted by thread 0 after the task.
+__device__ double task_bytes(const ExecEnv& e, const HTask& t, int l_in) {
+  switch (t.type) {
+    case T_LU:
+    case T_INV:
+    case T_CHOL:
+      return 16.0 * t.m * t.m;
+    case T_TRSM:
+      return 8.0 * ((double)t.m * t.m + 2.0 * t.m * width_of(e, t.wa));
+    case T_GEMM: {
+      double w = width_of(e, t.wa);
+      return 8.0 * (2.0 * t.m * t.n + (t.m + t.n) * w);
+    }
+    case T_ADD:
+      return 24.0 * t.m * t.n;
+    case T_COPY:
+      return 16.0 * t.m * t.n;
+    case T_ZERO:
+      return 8.0 * t.m * t.n;
+    case T_HMV:
+    case T_DENSIFY: {
+      double w = t.type == T_HMV ? width_of(e, t.wa) : 0.0, b = 0.0;
+      for (int li = 0; li < t.list_len; ++li) {
+        const LeafRef& L = e.leaves[t.list_begin + li];
+        double f = L.kind == 1 ? (double)L.rows * L.cols : (double)e.ranks[L.rank_slot] * (L.rows + L.cols);
+        b += 8.0 * (f + (t.type == T_HMV ? 2.0 * (L.rows + L.cols) * w : (double)L.rows * L.cols));
+      }
+      return b;
+    }
+    case T_RKADD:
+    case T_ROWMERGE: {
+      if (l_in <= 0) return 0.0;
+      int n = t.type == T_RKADD ? t.n : t.p + t.q;
+      int k = t.rout >= 0 ? e.ranks[t.rout] : 0;
+      return 8.0 * ((double)(t.m + n) * l_in + (double)(t.m + n) * k);
+    }
+    default:
+      return 0.0;
+  }
+}
+
+// Stacked width of a truncation task before it runs (rank slots are
+// overwritten in place).
+__device__ int trunc_width(const ExecEnv& e, const HTask& t) {
+  if (t.type == T_RKADD) {
+    bool aid = t.flags & F_A_IDENT, bid = t.flags & F_B_IDENT;
+    int w = aid ? t.m : (bid ? t.n : width_of(e, t.wa));
+    return w + (t.rin >= 0 ? e.ranks[t.rin] : 0);
+  }
+  if (t.type == T_ROWMERGE) return width_of(e, t.wa) + width_of(e, t.wb);
+  return -1;
 }
 
 __device__ void run_task(const ExecEnv& e, const HTask& t, Smem& s, long long ti) {
@@ -929,9 +985,16 @@ __global__ void __launch_bounds__(HM_THREADS, 1) exec_tasks(ExecEnv e) {
         double f = task_flops(e, task);
         if (f > 0.0) atomicAdd(e.flops, f);
       }
+      int l_in = 0;
+      if (threadIdx.x == 0) l_in = trunc_width(e, task);
+      __syncthreads();  // every thread has read the rank slots the task may overwrite
       run_task(e, task, s, t);
       __syncthreads();
       if (threadIdx.x == 0 && hm_status_won) *e.fail_task = t + 1;
+      if (threadIdx.x == 0) {
+        double b = task_bytes(e, task, l_in);
+        if (b > 0.0) atomicAdd(e.bytes, b);
+      }
       if (threadIdx.x == 0 && s.bcast[7] > 0.0) atomicAdd(e.flops32, s.bcast[7]);
       if (threadIdx.x == 0 && task.type >= 0 && task.type < 16) {
         uint64_t dt = global_ns() - cur_t0;
@@ -1071,8 +1134,115 @@ __global__ void to_dense_kernel(const LeafRef* leaves, int nleaves, const double
 }
 
 // ---------------------------------------------------------------------------
+// Conjugate-gradient building blocks (grid-stride loops over n x nrhs).
+// ---------------------------------------------------------------------------
+__global__ void permute_kernel(const double* src, double* dst, const int64_t* perm, int64_t n, int64_t nrhs,
+                               int gather) {
+  int64_t total = n * nrhs;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = idx % n, c = idx / n;
+    if (gather) dst[idx] = src[c * n + perm[i]];
+    else dst[c * n + perm[i]] = src[idx];
+  }
+}
+
+// one warp per row, all right-hand sides of that row
+__global__ void csr_spmv_kernel(int64_t n, const int64_t* rowptr, const int64_t* colidx, const double* val,
+                                const double* X, double* Y, int64_t nrhs) {
+  int lane = threadIdx.x & 31;
+  int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+    int64_t e0 = rowptr[i], e1 = rowptr[i + 1];
+    for (int64_t c = 0; c < nrhs; ++c) {
+      double a = 0.0;
+      for (int64_t e = e0 + lane; e < e1; e += 32) a += val[e] * X[c * n + colidx[e]];
+      a = warp_sum(a);
+      if (lane == 0) Y[c * n + i] = a;
+    }
+  }
+}
+
+// one block per column
+__global__ void col_dots_kernel(int64_t n, const double* X, const double* Y, double* out) {
+  __shared__ double red[32];
+  int64_t c = blockIdx.x;
+  double a = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) a += X[c * n + i] * Y[c * n + i];
+  a = warp_sum(a);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double b = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    b = warp_sum(b);
+    if (threadIdx.x == 0) out[c] = b;
+  }
+}
+
+__global__ void cg_xr_kernel(int64_t n, int64_t nrhs, const double* alpha, const double* P, const double* Q,
+                             double* X, double* R) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * nrhs; idx += (int64_t)gridDim.x * blockDim.x) {
+    double a = alpha[idx / n];
+    X[idx] += a * P[idx];
+    R[idx] -= a * Q[idx];
+  }
+}
+
+__global__ void cg_p_kernel(int64_t n, int64_t nrhs, const double* beta, const double* Z, double* P) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * nrhs; idx += (int64_t)gridDim.x * blockDim.x)
+    P[idx] = Z[idx] + beta[idx / n] * P[idx];
+}
+
+__global__ void sub_kernel(int64_t count, const double* A, const double* B, double* D) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < count; idx += (int64_t)gridDim.x * blockDim.x)
+    D[idx] = A[idx] - B[idx];
+}
+
+// ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
+static int grid_for(int64_t work) {
+  int64_t g = (work + 255) / 256;
+  return (int)(g < 1 ? 1 : (g > 152 * 32 ? 152 * 32 : g));
+}
+
+cudaError_t launch_permute(const double* src, double* dst, const int64_t* perm, int64_t n, int64_t nrhs, bool gather,
+                           cudaStream_t st) {
+  (void)cudaGetLastError();
+  permute_kernel<<<grid_for(n * nrhs), 256, 0, st>>>(src, dst, perm, n, nrhs, gather ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_csr_spmv(int64_t n, const int64_t* rowptr, const int64_t* colidx, const double* val,
+                            const double* X, double* Y, int64_t nrhs, cudaStream_t st) {
+  (void)cudaGetLastError();
+  csr_spmv_kernel<<<grid_for(32 * n), 256, 0, st>>>(n, rowptr, colidx, val, X, Y, nrhs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_col_dots(int64_t n, int64_t nrhs, const double* X, const double* Y, double* out, cudaStream_t st) {
+  (void)cudaGetLastError();
+  col_dots_kernel<<<(unsigned)nrhs, 1024, 0, st>>>(n, X, Y, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_xr(int64_t n, int64_t nrhs, const double* alpha, const double* P, const double* Q, double* X,
+                         double* R, cudaStream_t st) {
+  (void)cudaGetLastError();
+  cg_xr_kernel<<<grid_for(n * nrhs), 256, 0, st>>>(n, nrhs, alpha, P, Q, X, R);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_p(int64_t n, int64_t nrhs, const double* beta, const double* Z, double* P, cudaStream_t st) {
+  (void)cudaGetLastError();
+  cg_p_kernel<<<grid_for(n * nrhs), 256, 0, st>>>(n, nrhs, beta, Z, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sub(int64_t count, const double* A, const double* B, double* D, cudaStream_t st) {
+  (void)cudaGetLastError();
+  sub_kernel<<<grid_for(count), 256, 0, st>>>(count, A, B, D);
+  return cudaGetLastError();
+}
 size_t smem_bytes() { return sizeof(Smem); }
 
 cudaError_t launch_exec(const ExecEnv& env, int grid, cudaStream_t st) {

@@ -92,3 +92,34 @@ def test_null_arguments_return_a_status(hm, name, nargs):
     buf = ctypes.create_string_buffer(256)
     L.hmat_last_error(buf, ctypes.c_size_t(256))
     assert buf.value
+
+
+def test_standard_schedule_builds_on_the_host(hm):
+    """hmat_analyze_lu (host only) in both modes: the standard form applies
+    every product at once (Section 4), so its schedule truncates more; a
+    rank rule the mixed form cannot honour and an unknown mode are refused
+    before any work."""
+    import ctypes
+    p = hs.small_laplace(16, 3, 64, 1e-4)
+    ct = hm.ClusterTree(_NullCtx(), p.coords(), p.leaf)
+    bt = hm.BlockTree(_NullCtx(), ct, ct, p.eta)
+    csr = p.matrix()
+
+    def analyze(mode, precision=hm.HMAT_FP64, rule=hm.HMAT_REL_FRO):
+        o = hm.Opts(p.eps, 0, precision, 0, 0, None, 0, 0, mode, rule)
+        st = hm.Stats()
+        rc = hm.lib().hmat_analyze_lu(bt.h, ctypes.c_int64(csr.n),
+                                      np.ascontiguousarray(csr.rowptr, np.int64).ctypes.data_as(hm.I64P),
+                                      np.ascontiguousarray(csr.colidx, np.int64).ctypes.data_as(hm.I64P),
+                                      np.ascontiguousarray(csr.val, np.float64).ctypes.data_as(hm.F64P),
+                                      ctypes.byref(o), ctypes.byref(st))
+        return rc, st.as_dict()
+
+    rc_a, acc = analyze(hm.HMAT_ACCUMULATED)
+    rc_s, std = analyze(hm.HMAT_STANDARD)
+    assert rc_a == 0 and rc_s == 0
+    # every product of a leaf pair is truncated into its target at once, so
+    # the standard schedule holds more truncations (Section 4)
+    assert std["truncations"] > acc["truncations"] > 0
+    assert analyze(7)[0] == hm.HMAT_ERR_ARG
+    assert analyze(hm.HMAT_ACCUMULATED, hm.HMAT_MIXED, hm.HMAT_REL_SPEC)[0] == hm.HMAT_ERR_ARG

@@ -106,3 +106,23 @@ def test_rkadd_is_truncated_sum(eps):
     assert err <= np.sqrt(np.sum(s[k:] ** 2)) * (1 + 1e-6) + 1e-12 * s[0]
     if eps == 0.0:
         assert err <= 1e-12 * s[0]
+
+
+@pytest.mark.parametrize("m,n,ell,eps", [(40, 30, 12, 1e-3), (25, 60, 20, 1e-6), (16, 16, 16, 0.0)])
+def test_spectral_rank_rule_is_eckart_young_in_the_2_norm(m, n, ell, eps):
+    """Rank rule 1 (relative spectral): the truncation keeps the smallest k
+    with sigma_{k+1} <= eps sigma_1, and the error in the spectral norm is
+    exactly sigma_{k+1} (Eckart-Young), against LAPACK's singular values."""
+    A, B = hs.lowrank_stack(m, n, ell, seed=31 + m, decay=0.4)
+    R = A @ B.T
+    s = np.linalg.svd(R, compute_uv=False)
+    oracle.set_rank_rule(1)
+    try:
+        C, D = oracle.trunc(A, B, eps)
+    finally:
+        oracle.set_rank_rule(0)
+    k = C.shape[1]
+    assert k == int(np.sum(s > eps * s[0])) if eps > 0 else k == int(np.sum(s > 1e-13 * s[0]))
+    err = np.linalg.norm(R - C @ D.T, 2)
+    nxt = s[k] if k < len(s) else 0.0
+    assert abs(err - nxt) <= 1e-10 * s[0]

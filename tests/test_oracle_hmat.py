@@ -319,3 +319,34 @@ def test_literal_accumulators_agree_with_dense_reading_hmul():
         assert np.linalg.norm(res[literal] - ref, 2) / nrm < 1e-3
     assert np.linalg.norm(res[True] - res[False], 2) / nrm < 1e-3
     assert tr[True] > tr[False]
+
+
+# ---------------------------------------------------------------------------
+# Preconditioned CG with the H-LU factors (the PCG check of the stress case)
+# ---------------------------------------------------------------------------
+def test_pcg_with_exact_factors_converges_in_one_step():
+    """With eps = 0 the preconditioner is A^{-1}: one CG step solves A x = b
+    to rounding (the residual of the exact solve)."""
+    p = hs.small_laplace(16, 2, 8, 0.0)
+    ct, bt, csr, H = oracle.setup(p)
+    H.lu(0.0, True)
+    B = np.stack([hs.normal(4 + c, p.n) for c in range(3)], axis=1)
+    X, its, res = H.pcg(csr, B, rtol=1e-10)
+    assert np.all(its <= 2) and np.all(res <= 1e-10)
+    A = csr.to_dense()
+    assert np.abs(A @ X - B).max() <= 1e-9 * np.abs(B).max()
+
+
+def test_pcg_iterations_fall_with_eps():
+    """A diffusion problem: the H-LU preconditioner at a tighter eps needs
+    fewer CG iterations to the same residual, and every run reaches it."""
+    p = hs.Problem("diffusion2d_32", 32, 2, 16, 2.0, 1e-2, kind="diffusion", lc=0.1, seed=11)
+    B = np.stack([hs.normal(40 + c, p.n) for c in range(2)], axis=1)
+    its = {}
+    for eps in (1e-1, 1e-3):
+        ct, bt, csr, H = oracle.setup(p)
+        H.lu(eps, True)
+        X, it, res = H.pcg(csr, B, rtol=1e-10)
+        assert np.all(res <= 1e-9)
+        its[eps] = int(it.max())
+    assert its[1e-3] < its[1e-1]
