@@ -42,14 +42,24 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     started = time.time()
 
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if not f.endswith((".cu", ".cpp"))]
+    headers.append(os.path.join(INCLUDE, "hmat.h"))
+    newest_header = max(os.path.getmtime(h) for h in headers)
+
     def compile_one(src):
         obj = os.path.join(BUILD, src + ".o")
-        cmd = [nvcc] + ARCH + COMMON + ["-c", os.path.join(CSRC, src), "-o", obj]
+        srcp = os.path.join(CSRC, src)
+        if (not force and os.path.exists(obj) and
+                os.path.getmtime(obj) > max(os.path.getmtime(srcp), newest_header)):
+            return obj  # this translation unit is up to date
+        cmd = [nvcc] + ARCH + COMMON + ["-c", srcp, "-o", obj]
         if src.endswith(".cu"):
             cmd += ["-Xptxas", "-v"] if verbose else []
+        t0 = time.time()
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, r.stdout, r.stderr))
+        os.utime(obj, (t0, t0))  # an edit during the compilation makes it stale
         if verbose:
             sys.stderr.write(r.stderr)
         return obj

@@ -518,6 +518,13 @@ int64_t rand_ws(int64_t m, int64_t n, int64_t l) {
 // Symbolic arithmetic: the paper's procedures emitting tasks
 // ===========================================================================
 
+// Sizes of the small non-leaf blocks that accumulate densely when asked to:
+// the smaller side at most DENSE_ACC_MIN (its identity-factor truncation then
+// stays within the stacked-width limit with a full-capacity input rank), the
+// larger at most DENSE_ACC_MAX.
+const int64_t DENSE_ACC_MIN = 128;
+const int64_t DENSE_ACC_MAX = 256;
+
 // A low-rank matrix under construction: own storage, or a row-restricted view
 // of another one (Section 3, "Splitting": no arithmetic).
 struct SLow {
@@ -543,12 +550,17 @@ struct SPend {
 
 // Accumulator (Rhat_{t,r}, P_{t,r}) (Section 4).  Blocks with a leaf cluster
 // on either side keep Rhat in standard representation (exact additions, one
-// truncation when flushed into an admissible leaf); all others factorised.
+// truncation when flushed into an admissible leaf); all others factorised,
+// except, where the symbolic pass is told so, small blocks (dense_small):
+// they too add their products exactly and truncate once per flush.  A dense
+// accumulator split into its sons hands them views of its block (same
+// storage, same dependency object).
 struct SAcc {
   int t = 0, r = 0;
   bool dense = false;
   bool dzero = true;
   int64_t dloc = -1;
+  int dld = 0;     // leading dimension of the dense block (a view keeps its parent's)
   int dobj = -1;
   HoldP dhold;
   SLow R;
@@ -580,6 +592,7 @@ struct Sym {
   const hmat_ctree& CT;
   int64_t maxrank;
   bool mixed = false;
+  bool dense_small = false;  // small non-leaf blocks also accumulate densely
   std::vector<const hmat*> mats;
   std::vector<int> objbase;
   std::vector<int64_t> hoffs;
@@ -861,8 +874,10 @@ struct Sym {
     SAcc a;
     a.t = t;
     a.r = r;
-    a.dense = rc(t).nsons == 0 || cc(r).nsons == 0;
-    a.R.cap = capof(rc(t).size, cc(r).size);
+    int64_t m = rc(t).size, n = cc(r).size;
+    a.dense = rc(t).nsons == 0 || cc(r).nsons == 0 ||
+              (dense_small && std::min(m, n) <= DENSE_ACC_MIN && std::max(m, n) <= DENSE_ACC_MAX);
+    a.R.cap = capof(m, n);
     return a;
   }
 
@@ -872,6 +887,7 @@ struct Sym {
     int c = S.alloc(m * n);
     a.dhold = std::make_shared<Hold>(&S, c);
     a.dloc = S.chunk_loc(c);
+    a.dld = (int)m;
     a.dobj = S.chunk_obj(c);
     HTask z = blank(T_ZERO);
     z.m = (int)m;
@@ -979,7 +995,7 @@ struct Sym {
       t.n = (int)n;
       t.alpha = alpha;
       t.c = a.dloc;
-      t.ldc = (int)m;
+      t.ldc = a.dld;
       if (P.aid) {
         t.flags = F_TRANS;  // D += alpha Bhat^T
         t.a = P.b;
@@ -1016,7 +1032,6 @@ struct Sym {
 
   // Fig. split
   std::vector<std::vector<SAcc>> split(SAcc& a) {
-    if (a.dense) throw HmError(HMAT_ERR_INTERNAL, "split: accumulator in standard representation");
     const CNodeH& t = rc(a.t);
     const CNodeH& r = cc(a.r);
     std::vector<std::vector<SAcc>> sons((size_t)t.nsons);
@@ -1025,7 +1040,18 @@ struct Sym {
         SAcc s = acc_new(t.son[i], r.son[j]);
         int64_t ro = rc(s.t).off - t.off, co = cc(s.r).off - r.off;
         int64_t sm = rc(s.t).size, sn = cc(s.r).size;
-        if (!a.R.zero) {
+        if (a.dense) {
+          // the son's block of the parent's dense block: a view (or, while
+          // the parent has no storage yet, a zero block of its own)
+          s.dense = true;
+          if (a.dloc >= 0) {
+            s.dloc = a.dloc + ro + co * a.dld;
+            s.dld = a.dld;
+            s.dobj = a.dobj;
+            s.dhold = a.dhold;
+            s.dzero = a.dzero;
+          }
+        } else if (!a.R.zero) {
           if (s.dense) {
             dense_ensure(s);
             HTask g = blank(T_GEMM);
@@ -1039,7 +1065,7 @@ struct Sym {
             g.ldb = a.R.ldv;
             g.wa = a.R.wcode;
             g.c = s.dloc;
-            g.ldc = (int)sm;
+            g.ldc = s.dld;
             S.emit(g, {a.R.obj}, {s.dobj});
             s.dzero = false;
           } else {
@@ -1255,11 +1281,40 @@ struct Sym {
     }
   }
 
+  // The pending products of a dense accumulator expanded down to the leaf
+  // cases, each added exactly into the accumulator's own block (its sons are
+  // views of it; Fig. split with the son accumulators in the parent's block).
+  void resolve_pending(SAcc& a) {
+    auto sons = split(a);
+    for (auto& row : sons)
+      for (SAcc& c : row)
+        if (!c.P.empty()) resolve_pending(c);
+    a.P.clear();
+  }
+
   // Fig. flush
   void flush(SAcc& a, STarget z) {
     int64_t m = rc(a.t).size, n = cc(a.r).size;
     if (a.dense) {
-      if (!a.P.empty()) throw HmError(HMAT_ERR_INTERNAL, "flush: pending products on a leaf-cluster block");
+      if (!z.tmp && z.M->kind(z.b) == 0) {
+        // subdivided target: the sub-blocks (and the pending products split
+        // over them) into the sons of the target
+        auto sons = split(a);
+        for (size_t i = 0; i < sons.size(); ++i)
+          for (size_t j = 0; j < sons[i].size(); ++j)
+            flush(sons[i][j], target_of(z.M, z.M->bt->child(z.b, (int)i, (int)j), sons[i][j].t, sons[i][j].r));
+        a.P.clear();
+        a.dhold.reset();
+        a.dloc = -1;
+        a.dzero = true;
+        return;
+      }
+      if (!a.P.empty()) {
+        // a leaf target: every pending product added into the block itself
+        dense_ensure(a);
+        resolve_pending(a);
+        a.dzero = false;
+      }
       if (a.dloc < 0 || a.dzero) return;
       bool zdense = !z.tmp && z.M->kind(z.b) == 1;
       if (zdense) {
@@ -1268,7 +1323,7 @@ struct Sym {
         t.n = (int)n;
         t.alpha = 1.0;
         t.a = a.dloc;
-        t.lda = (int)m;
+        t.lda = a.dld;
         t.c = hl(z.M, z.b);
         t.ldc = (int)m;
         int o = obj_of(z.M, z.b);
@@ -1281,13 +1336,13 @@ struct Sym {
         if (m <= n) {
           P.aid = true;
           P.b = a.dloc;
-          P.ldb = (int)m;
+          P.ldb = a.dld;
           P.btr = true;
           P.wcode = P.wcap = (int)m;
         } else {
           P.bid = true;
           P.a = a.dloc;
-          P.lda = (int)m;
+          P.lda = a.dld;
           P.wcode = P.wcap = (int)n;
         }
         if (z.tmp) {
@@ -1298,6 +1353,7 @@ struct Sym {
           z.M->zero[(size_t)z.b] = 0;
         }
       }
+      a.P.clear();
       a.dhold.reset();
       a.dloc = -1;
       a.dzero = true;
@@ -2231,6 +2287,7 @@ double schedule_lu(hmat* H, int64_t max_rank, bool mixed, bool standard, Sched& 
   S.next_slot = H->nslots;
   Sym sym(S, *H->bt->R, *H->bt->C, max_rank);
   sym.mixed = mixed;
+  sym.dense_small = mixed;
   sym.add_matrix(H);
   if (standard) {
     sym.lu_std(H, 0);
@@ -2513,6 +2570,7 @@ void lu_batch(hmat_ctx* ctx, hmat* const* Hs, int count, const hmat_opts* opts) 
     S.set_pool(i);
     Sym sym(S, *H->bt->R, *H->bt->C, mr);
     sym.mixed = mixed;
+    sym.dense_small = mixed;
     sym.add_matrix(H, (int64_t)(H->store.as<double>() - base), slotbase[(size_t)i]);
     if (standard) {
       sym.lu_std(H, 0);
@@ -2610,6 +2668,7 @@ void chol_run(hmat_ctx* ctx, hmat* G, const hmat_opts* opts) {
   S.set_pool(0);
   Sym sym(S, *G->bt->R, *G->bt->C, mr);
   sym.mixed = mixed;
+  sym.dense_small = mixed;
   sym.add_matrix(G);
   SAcc root = sym.acc_new(0, 0);
   sym.chol(G, 0, root);
@@ -2699,6 +2758,7 @@ void invert_run(hmat_ctx* ctx, hmat* G, const hmat_opts* opts) {
   S.set_pool(0);
   Sym sym(S, *G->bt->R, *G->bt->C, mr);
   sym.mixed = mixed;
+  sym.dense_small = mixed;
   for (int i = 0; i < 2; ++i) sym.add_matrix(M[i], (int64_t)(M[i]->store.as<double>() - base), slotbase[i]);
   SAcc root = sym.acc_new(0, 0);
   sym.invert(G, H.get(), 0, root);
@@ -2781,6 +2841,7 @@ void addmul_run(hmat_ctx* ctx, double alpha, const hmat* X, const hmat* Y, hmat*
   S.set_pool(0);
   Sym sym(S, *T, *T, mr);
   sym.mixed = mixed;
+  sym.dense_small = mixed;
   for (int i = 0; i < 3; ++i) sym.add_matrix(M[i], (int64_t)(M[i]->store.as<double>() - base), slotbase[i]);
   STarget z;
   z.M = Z;

@@ -18,7 +18,9 @@ def ctx():
 def test_laplace3d_32_mixed_matches_plain_fp64(ctx):
     """32^3, leaf 64, eps 1e-4: the chosen (mixed) form and the plain FP64 form,
     which the smaller parity tests pin to the oracle, reach the same
-    preconditioner quality on the same block structure."""
+    preconditioner quality on the same block structure.  The mixed form also
+    accumulates the small non-leaf blocks densely (one truncation per flush
+    instead of one per product), so it runs fewer truncations."""
     g = hm()
     p = hs.laplace3d_32()
     a = GpuProblem(ctx, p)
@@ -27,7 +29,7 @@ def test_laplace3d_32_mixed_matches_plain_fp64(ctx):
     b.H.lu(p.eps, precision=g.HMAT_MIXED, reuse_schedule=True)
     sa, sb = a.H.stats(), b.H.stats()
     assert sa["status"] == 0 and sb["status"] == 0
-    assert sa["truncations"] == sb["truncations"]  # the same schedule of truncations
+    assert 0 < sb["truncations"] < sa["truncations"]
     v0 = hs.start_vector(p.n, 0)
     ea = a.precond_error(v0[a.perm])
     eb = b.precond_error(v0[b.perm])
