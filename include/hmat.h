@@ -138,6 +138,8 @@ typedef struct {
                                factors read and truncated factors written
                                (8 [(m + n) l + (m + n) k] per truncation),
                                dense leaves and thin blocks read and written */
+  int64_t gang_truncations; /* truncations of large blocks run by a gang of CTAs
+                               (TSQR over row blocks; mixed form)             */
 } hmat_stats;
 
 /* Message of the last failure on this thread, copied into buf (NUL-terminated,

@@ -72,7 +72,7 @@ class Stats(ctypes.Structure):
                 ("rand_fallbacks", ctypes.c_int64), ("sketch_attempts", ctypes.c_int64),
                 ("sketch_columns", ctypes.c_int64), ("training_pairs", ctypes.c_int64), ("cp_seconds", ctypes.c_double),
                 ("cp_type_seconds", ctypes.c_double * 16), ("cp_type_count", ctypes.c_int64 * 16),
-                ("flops32", ctypes.c_double), ("bytes", ctypes.c_double)]
+                ("flops32", ctypes.c_double), ("bytes", ctypes.c_double), ("gang_truncations", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         d = {}

@@ -431,6 +431,23 @@ struct Sched {
     return id;
   }
 
+  // Members 1..G-1 of a gang whose member 0 was just emitted as task id0:
+  // the same task with its rank, the same predecessors, and no object
+  // bookkeeping (later tasks depend on member 0 alone, which finishes last).
+  void emit_gang_members(int32_t id0, int G) {
+    for (int r = 1; r < G; ++r) {
+      HTask t = tasks[(size_t)id0];
+      t.pad0 = r;
+      int64_t d0 = dep_ptr[(size_t)id0], d1 = dep_ptr[(size_t)id0 + 1];
+      for (int64_t k = d0; k < d1; ++k) dep_idx.push_back(dep_idx[(size_t)k]);
+      dep_ptr.push_back((int64_t)dep_idx.size());
+      level.push_back(level[(size_t)id0]);
+      cpath.push_back(cpath[(size_t)id0]);
+      for (int k = 0; k < 4; ++k) feat.push_back(feat[4 * (size_t)id0 + k]);
+      tasks.push_back(t);
+    }
+  }
+
   // Reorder the list by ASAP level (stable): still a topological order, and
   // tasks that can run together sit next to each other, so the in-order
   // dequeue of the executor sees the available parallelism.
@@ -944,12 +961,24 @@ struct Sym {
     int64_t l = (int64_t)P.wcap + (rin >= 0 ? Z.wmax : 0);
     if (l > HM_LMAX_HOST) throw HmError(HMAT_ERR_RANK, "stacked width exceeds the truncation limit");
     int inmax = Z.wmax;
-    int ws = S.alloc(rk_ws(m, n, l) + (mixed ? rand_ws(m, n, l) : 0));
+    // a large factored block of the mixed form: a gang of CTAs (TSQR)
+    int G = 1;
+    if (mixed && !P.aid && !P.bid && std::min(m, n) >= 4 * HM_GANG_MIN_ROWS && l <= 128)
+      G = (int)std::min<int64_t>(8, std::min(m, n) / HM_GANG_MIN_ROWS);
+    int64_t base_ws = rk_ws(m, n, l) + (mixed ? rand_ws(m, n, l) : 0);
+    int ws = S.alloc(base_ws + (G > 1 ? gang_ws_doubles(m, n, l, G) : 0));
     t.ws = S.chunk_loc(ws);
+    if (G > 1) {
+      t.pad0 = 0;
+      t.pad1 = G;
+      t.q = (int)l;
+      t.list_begin = (int32_t)base_ws;
+    }
     std::vector<int> reads = P.objs;
     if (rin >= 0 && inobj >= 0 && inobj != Z.obj) reads.push_back(inobj);
-    S.emit(t, reads, {Z.obj, S.chunk_obj(ws)});
+    int32_t id0 = S.emit(t, reads, {Z.obj, S.chunk_obj(ws)});
     set_features(ft, fr);
+    if (G > 1) S.emit_gang_members(id0, G);
     S.release(ws);
     Z.wcode = width_from_slot(Z.slot);
     Z.zero = false;
@@ -1852,6 +1881,7 @@ struct RunResult {
   unsigned long long rand_ok = 0, rand_fail = 0, sketch_attempts = 0, sketch_cols = 0;
   unsigned long long bad[6] = {0, 0, 0, 0, 0, 0};
   long long fail_task = -1;  // task that recorded the device status first (-1: none)
+  unsigned long long gang = 0;  // truncations run by a gang of CTAs
   std::vector<uint32_t> task_ns;  // filled when profiling
   std::vector<uint32_t> task_aux;
 };
@@ -1934,7 +1964,7 @@ std::string describe_failure(const Sched& S, long long ft, hmat* const* Hs, int 
 
 // A schedule uploaded to the device, with its scratch arena.
 struct DevSched {
-  DevBuf tasks, ptr, idx, leaves, done, ws, misc, tns, feat, rec;
+  DevBuf tasks, ptr, idx, leaves, done, gang, ws, misc, tns, feat, rec;
   size_t ntasks = 0;
 };
 
@@ -1956,6 +1986,7 @@ void upload_sched(hmat_ctx* ctx, const Sched& S, DevSched& D) {
   upload(D.leaves, S.leaves, st);
   upload(D.feat, S.feat, st);
   D.done.alloc(S.tasks.size() * sizeof(int));
+  D.gang.alloc(S.tasks.size() * sizeof(int));
   D.ws.alloc((size_t)std::max<int64_t>(S.ws_top, 1) * sizeof(double));
   D.misc.alloc(64 * 8);
   D.ntasks = S.tasks.size();
@@ -1967,6 +1998,7 @@ RunResult launch_sched(hmat_ctx* ctx, const Sched& S, DevSched& D, double* hbase
   if (D.ntasks == 0) return rr;
   cudaStream_t st = ctx->stream;
   HM_CUDA(cudaMemsetAsync(D.done.p, 0, D.ntasks * sizeof(int), st));
+  HM_CUDA(cudaMemsetAsync(D.gang.p, 0, D.ntasks * sizeof(int), st));
   HM_CUDA(cudaMemsetAsync(D.misc.p, 0, 64 * 8, st));
   ExecEnv e;
   e.hbase = hbase;
@@ -1980,6 +2012,7 @@ RunResult launch_sched(hmat_ctx* ctx, const Sched& S, DevSched& D, double* hbase
   e.dep_idx = D.idx.as<int32_t>();
   e.leaves = D.leaves.as<LeafRef>();
   e.done = D.done.as<int>();
+  e.gang = D.gang.as<int>();
   void* dmp = D.misc.p;
   e.head = (unsigned long long*)dmp;
   e.counters = (unsigned long long*)dmp + 44;
@@ -2048,6 +2081,7 @@ RunResult launch_sched(hmat_ctx* ctx, const Sched& S, DevSched& D, double* hbase
   rr.rand_fail = misc[46];
   for (int i = 0; i < 6; ++i) rr.bad[i] = misc[47 + i];
   rr.sketch_attempts = misc[53];
+  rr.gang = misc[55];
   rr.sketch_cols = misc[54];
   if (lo.record && lo.rec_out) {
     size_t cnt = (size_t)std::min<unsigned long long>(misc[60], (unsigned long long)e.rec_cap);
@@ -2624,7 +2658,10 @@ void lu_batch(hmat_ctx* ctx, hmat* const* Hs, int count, const hmat_opts* opts) 
     st.flops = rr.flops;
     st.flops32 = rr.flops32;
   st.bytes = rr.bytes;
+  st.gang_truncations = (int64_t)rr.gang;
     st.bytes = rr.bytes;
+  st.gang_truncations = (int64_t)rr.gang;
+    st.gang_truncations = (int64_t)rr.gang;
     st.rand_truncations = (int64_t)rr.rand_ok;
     st.rand_fallbacks = (int64_t)rr.rand_fail;
     st.sketch_attempts = (int64_t)rr.sketch_attempts;
@@ -2696,6 +2733,7 @@ void chol_run(hmat_ctx* ctx, hmat* G, const hmat_opts* opts) {
   st.flops = rr.flops;
   st.flops32 = rr.flops32;
   st.bytes = rr.bytes;
+  st.gang_truncations = (int64_t)rr.gang;
   st.rand_truncations = (int64_t)rr.rand_ok;
   st.rand_fallbacks = (int64_t)rr.rand_fail;
   st.sketch_attempts = (int64_t)rr.sketch_attempts;
@@ -2786,6 +2824,7 @@ void invert_run(hmat_ctx* ctx, hmat* G, const hmat_opts* opts) {
   st.flops = rr.flops;
   st.flops32 = rr.flops32;
   st.bytes = rr.bytes;
+  st.gang_truncations = (int64_t)rr.gang;
   st.rand_truncations = (int64_t)rr.rand_ok;
   st.rand_fallbacks = (int64_t)rr.rand_fail;
   st.sketch_attempts = (int64_t)rr.sketch_attempts;
@@ -2878,6 +2917,7 @@ void addmul_run(hmat_ctx* ctx, double alpha, const hmat* X, const hmat* Y, hmat*
   st.flops = rr.flops;
   st.flops32 = rr.flops32;
   st.bytes = rr.bytes;
+  st.gang_truncations = (int64_t)rr.gang;
   st.rand_truncations = (int64_t)rr.rand_ok;
   st.rand_fallbacks = (int64_t)rr.rand_fail;
   st.sketch_attempts = (int64_t)rr.sketch_attempts;

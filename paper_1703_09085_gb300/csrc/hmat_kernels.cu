@@ -416,6 +416,351 @@ __device__ int task_fact32(const ExecEnv& e, const HTask& t, Smem& s, int m, int
   return k;
 }
 
+// ---------------------------------------------------------------------------
+// Gang truncation: one large rkadd of the mixed form run by G CTAs together.
+// A single CTA is latency-bound on a 1024 x 1024 or 4096 x 4096 block (every
+// Householder step sweeps its whole panel); here every CTA takes its own row
+// blocks of the stacked factors and the thin QRs are TSQRs (Demmel, Grigori,
+// Hoemmen and Langou, SIAM J. Sci. Comput. 2012): a Householder QR of each
+// row block, then one of the stacked l x l R factors, repeated by every
+// member.  The steps are those of Fig. rkadd with the FP32 core of the mixed
+// form: SB = Q_B R_B, Mhat = SA R_B^T, Mhat = Q_T R_T, the core on R_T, C =
+// Q_T (core vectors), D = Q_B (core weights) S.  The members meet at five
+// gang barriers (a counter per task, bounded waits); any case the gang does
+// not cover (a zero product, a stacked width the stacks cannot hold, a failed
+// cancellation guard, a non-finite result) is left to member 0, which runs the
+// single-CTA task on the untouched inputs.
+// ---------------------------------------------------------------------------
+// Arrive at gang barrier k (1-based) of the gang whose member 0 is task c0
+// and wait for all G members.
+__device__ void gang_sync(const ExecEnv& e, long long c0, int k, int G) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int* ctr = e.gang + c0;
+    __threadfence();
+    atomicAdd(ctr, 1);
+    uint64_t t0 = global_ns();
+    long long it = 0;
+    while (ld_acquire(ctr) < k * G) {
+      if (++it > e.spin_iters || global_ns() - t0 > e.spin_ns) {
+        set_status(e.status, DS_TIMEOUT);
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// A member that leaves before barrier `last` arrives at the ones it skips.
+__device__ void gang_leave(const ExecEnv& e, long long c0, int passed, int last) {
+  __syncthreads();
+  if (threadIdx.x == 0 && last > passed) {
+    __threadfence();
+    atomicAdd(e.gang + c0, last - passed);
+  }
+  __syncthreads();
+}
+
+// The gang region of a task (doubles from the task's scratch base + offset).
+struct GangWs {
+  double* xch;     // G x HM_GANG_XCH
+  float* RB;       // G x L x L: R of every member's block of SB
+  float* RM;       // G x L x L: R of every member's block of Mhat
+  float* SAf;      // m x L (ld m): FP32 SA, later C's rows
+  float* SBf;      // n x L (ld n): FP32 SB, then its blocks' reflectors
+  float* Mh;       // m x L (ld m): Mhat, then its blocks' reflectors
+  float* Vs;       // n x L (ld n): D's rows
+  double* tloc;    // G x 4L: tau and R diagonal of the member's two block QRs
+  float* stk;      // G x (3 G L L + L L): every member's two stacks and small panels
+  double* tstk;    // G x 4L: tau and R diagonal of the member's two stack QRs
+};
+
+__device__ GangWs gang_ws(double* base, int m, int n, int L, int G) {
+  GangWs g;
+  g.xch = base;
+  float* f = (float*)(base + (int64_t)G * HM_GANG_XCH);
+  g.RB = f;
+  g.RM = g.RB + (int64_t)G * L * L;
+  g.SAf = g.RM + (int64_t)G * L * L;
+  g.SBf = g.SAf + (int64_t)m * L;
+  g.Mh = g.SBf + (int64_t)n * L;
+  g.Vs = g.Mh + (int64_t)m * L;
+  g.stk = g.Vs + (int64_t)n * L;
+  int64_t fl = (int64_t)(g.stk - f) + (int64_t)G * (3 * (int64_t)G * L * L + (int64_t)L * L);
+  double* d = (double*)f + (fl + 1) / 2;
+  g.tloc = d;
+  g.tstk = d + (int64_t)G * 4 * L;
+  return g;
+}
+
+// Stack the G members' l x l R factors (blocks of R, ld L) into stk (G l x l,
+// ld G l) and factor it; returns nothing, the R factor stays in stk's upper
+// triangle with its diagonal in rd.
+__device__ void gang_stack_qr(const float* R, int G, int l, int L, float* stk, double* tau, double* rd, Smem& s) {
+  int gl = G * l;
+  for (int idx = threadIdx.x; idx < gl * l; idx += HM_THREADS) {
+    int row = idx % gl, c = idx / gl;
+    int q = row / l, i = row % l;
+    stk[idx] = R[(int64_t)q * L * L + i + (int64_t)c * L];
+  }
+  cta_qr_rows<float>(stk, gl, gl, l, tau, rd, s);
+}
+
+// R (l x l, ld L) of a QR held as reflectors in X (ld ldx) and diagonal rd.
+__device__ void gang_put_r(const float* X, int ldx, const double* rd, int l, float* R, int L) {
+  for (int idx = threadIdx.x; idx < l * l; idx += HM_THREADS) {
+    int i = idx % l, c = idx / l;
+    R[i + (int64_t)c * L] = c < i ? 0.f : (c == i ? (float)rd[i] : X[i + (int64_t)c * ldx]);
+  }
+}
+
+__device__ void task_rkadd(const ExecEnv& e, const HTask& t, Smem& s, long long ti);
+
+__device__ void task_rkadd_gang(const ExecEnv& e, const HTask& t, Smem& s, long long ti) {
+  const int r = t.pad0, G = t.pad1, L = t.q;
+  const long long c0 = ti - r;  // member 0: the gang's counter
+  const int m = t.m, n = t.n, tid = threadIdx.x;
+  bool btr = t.flags & F_B_TRANS;
+  int w = width_of(e, t.wa);
+  int kin = t.rin >= 0 ? e.ranks[t.rin] : 0;
+  int l = w + kin;
+  const double* A = loc(e, t.a);
+  const double* B = loc(e, t.b);
+  const double* Uin = loc(e, t.c);
+  const double* Vin = loc(e, t.d);
+  GangWs g = gang_ws(loc(e, t.ws) + t.list_begin, m, n, L, G);
+  int mb = (m + G - 1) / G, nb = (n + G - 1) / G;
+  int ra = r * mb, rm = min(m, ra + mb) - ra;  // this member's rows of SA / Mhat / C
+  int ca = r * nb, rn = min(n, ca + nb) - ca;  // and of SB / D
+  auto sa = [&](int i, int j) -> double {    // stacked [alpha A | Uin]
+    return j < w ? t.alpha * A[(int64_t)j * t.lda + i] : Uin[(int64_t)(j - w) * t.ldc + i];
+  };
+  auto sb = [&](int i, int j) -> double {    // stacked [B | Vin]
+    return j < w ? (btr ? B[(int64_t)i * t.ldb + j] : B[(int64_t)j * t.ldb + i]) : Vin[(int64_t)(j - w) * t.ldd + i];
+  };
+  // 1. the largest entries and the non-zero pattern of this member's rows
+  double ma = 0.0, mbx = 0.0;
+  int nza = 0, nzb = 0;
+  if (l <= L) {
+    for (int idx = tid; idx < rm * l; idx += HM_THREADS) {
+      double v = sa(ra + idx % rm, idx / rm);
+      ma = fmax(ma, fabs(v));
+      if (idx / rm < w && v != 0.0) nza = 1;
+    }
+    for (int idx = tid; idx < rn * l; idx += HM_THREADS) {
+      double v = sb(ca + idx % rn, idx / rn);
+      mbx = fmax(mbx, fabs(v));
+      if (idx / rn < w && v != 0.0) nzb = 1;
+    }
+  }
+  ma = block_max(ma, s);
+  mbx = block_max(mbx, s);
+  nza = __syncthreads_or(nza);
+  nzb = __syncthreads_or(nzb);
+  if (tid == 0) {
+    double* x = g.xch + (int64_t)r * HM_GANG_XCH;
+    x[0] = ma;
+    x[1] = mbx;
+    x[2] = nza;
+    x[3] = nzb;
+  }
+  gang_sync(e, c0, 1, G);
+  // 2. the same decision on every member
+  double MA = 0.0, MB = 0.0;
+  bool any_a = false, any_b = false;
+  for (int q = 0; q < G; ++q) {
+    const double* x = g.xch + (int64_t)q * HM_GANG_XCH;
+    MA = fmax(MA, x[0]);
+    MB = fmax(MB, x[1]);
+    any_a = any_a || x[2] != 0.0;
+    any_b = any_b || x[3] != 0.0;
+  }
+  double S = MA * MB;
+  bool zero = w == 0 || ((t.flags & F_CHECK_ZERO) && !(any_a && any_b));
+  bool ok = !zero && l <= L && l <= HM_FACT32_DIRECT && l >= e.rand_min_l && l <= rm && l <= rn && l <= m &&
+            l <= n && 3 * (int64_t)l * l + 2 * l <= 2 * (int64_t)HM_JAC_SMEM && S > 0.0 &&
+            isfinite(S);
+  if (!ok) {
+    gang_leave(e, c0, 1, 5);
+    if (r == 0) task_rkadd(e, t, s, ti);
+    return;
+  }
+  // 3. FP32 copies of this member's rows, scaled by the largest entries
+  {
+    double ia = 1.0 / MA, ib = 1.0 / MB;
+    for (int idx = tid; idx < rm * l; idx += HM_THREADS) {
+      int i = idx % rm, j = idx / rm;
+      g.SAf[(int64_t)j * m + ra + i] = (float)(sa(ra + i, j) * ia);
+    }
+    for (int idx = tid; idx < rn * l; idx += HM_THREADS) {
+      int i = idx % rn, j = idx / rn;
+      g.SBf[(int64_t)j * n + ca + i] = (float)(sb(ca + i, j) * ib);
+    }
+  }
+  double* tauB = g.tloc + (int64_t)r * 4 * L;
+  double* rdB = tauB + L;
+  double* tauM = rdB + L;
+  double* rdM = tauM + L;
+  float* stkB = g.stk + (int64_t)r * (3 * (int64_t)G * L * L + (int64_t)L * L);  // G l x l, ld G l
+  float* stkM = stkB + (int64_t)G * L * L;                                        // G l x l, ld G l
+  float* Ys = stkM + (int64_t)G * L * L;                                          // G l x k, ld G l
+  float* Xs = Ys + (int64_t)G * L * L;                                            // l x k, ld l
+  double* tsB = g.tstk + (int64_t)r * 4 * L;
+  double* rsB = tsB + L;
+  double* tsM = rsB + L;
+  double* rsM = tsM + L;
+  // 4. QR of this member's block of SB; its R to the exchange
+  cta_qr_rows<float>(g.SBf + ca, n, rn, l, tauB, rdB, s);
+  gang_put_r(g.SBf + ca, n, rdB, l, g.RB + (int64_t)r * L * L, L);
+  gang_sync(e, c0, 2, G);
+  // 5. R_B from the stacked R factors; Mhat = SA R_B^T on this member's rows,
+  //    with the sums of the cancellation guard; QR of its block
+  gang_stack_qr(g.RB, G, l, L, stkB, tsB, rsB, s);
+  const int gl = G * l;
+  float smm = 0.f, sab = 0.f;
+  for (int idx = tid; idx < rm * l; idx += HM_THREADS) {
+    int i = idx % rm, c = idx / rm;
+    float v = 0.f, a = 0.f;
+    for (int j = c; j < l; ++j) {
+      float rcj = j == c ? (float)rsB[c] : stkB[c + (int64_t)j * gl];
+      float x = g.SAf[(int64_t)j * m + ra + i] * rcj;
+      v += x;
+      a += fabsf(x);
+    }
+    g.Mh[(int64_t)c * m + ra + i] = v;
+    smm += v * v;
+    sab += a * a;
+  }
+  double tm = block_sum((double)smm, s), ta = block_sum((double)sab, s);
+  cta_qr_rows<float>(g.Mh + ra, m, rm, l, tauM, rdM, s);
+  gang_put_r(g.Mh + ra, m, rdM, l, g.RM + (int64_t)r * L * L, L);
+  if (tid == 0) {
+    double* x = g.xch + (int64_t)r * HM_GANG_XCH;
+    x[4] = tm;
+    x[5] = ta;
+  }
+  gang_sync(e, c0, 3, G);
+  double TM = 0.0, TA = 0.0;
+  for (int q = 0; q < G; ++q) {
+    TM += g.xch[(int64_t)q * HM_GANG_XCH + 4];
+    TA += g.xch[(int64_t)q * HM_GANG_XCH + 5];
+  }
+  if (!isfinite(TM) || !isfinite(TA) || TA * 9e-14 > 1e-2 * e.eps * e.eps * TM) {
+    gang_leave(e, c0, 3, 5);
+    if (r == 0) task_rkadd(e, t, s, ti);
+    return;
+  }
+  // 6. R_T from the stacked R factors of Mhat; the FP32 core on R_T (in
+  //    shared memory: R_T, then the core's W, Vrot, norms and permutation)
+  gang_stack_qr(g.RM, G, l, L, stkM, tsM, rsM, s);
+  float* J = (float*)s.jac;
+  float* cw = J + l * l;
+  for (int idx = tid; idx < l * l; idx += HM_THREADS) {
+    int i = idx % l, c = idx / l;
+    J[idx] = c < i ? 0.f : (c == i ? (float)rsM[i] : stkM[i + (int64_t)c * gl]);
+  }
+  __syncthreads();
+  core_f32(J, l, l, cw, s, HM_CORE_SWEEPS);
+  if (tid == 0) {
+    double total = 0.0;
+    for (int i = 0; i < l; ++i) total += s.sigma[i] * s.sigma[i];
+    double bound = e.eps * e.eps * total, tail = 0.0;
+    int k = l;
+    while (k > 0) {
+      double x = s.sigma[s.order[k - 1]];
+      if (tail + x * x <= bound) {
+        tail += x * x;
+        --k;
+      } else {
+        break;
+      }
+    }
+    s.ivals[13] = k > t.cap ? 1 : 0;
+    s.ivals[4] = k > t.cap ? t.cap : k;
+  }
+  __syncthreads();
+  const int k = s.ivals[4];
+  const float* W = cw;
+  const float* Vrot = cw + l * l;
+  const int* perm = (const int*)(cw + 2 * l * l + l);
+  // 7. C = Q_T Q_c Vrot(:, order): the core's reflectors (in J) on the kept
+  //    rotation columns, then the stack's reflectors, then this member's
+  //    block reflectors; D = Q_B P W(:, order) S likewise
+  for (int idx = tid; idx < l * k; idx += HM_THREADS) {
+    int i = idx % l, jj = idx / l;
+    Xs[idx] = Vrot[(int64_t)s.order[jj] * l + i];
+  }
+  cta_apply_q_rows<float>(J, l, l, l, s.tauB, Xs, l, k, s);
+  for (int idx = tid; idx < gl * k; idx += HM_THREADS) {
+    int i = idx % gl, jj = idx / gl;
+    Ys[idx] = i < l ? Xs[i + (int64_t)jj * l] : 0.f;
+  }
+  cta_apply_q_rows<float>(stkM, gl, gl, l, tsM, Ys, gl, k, s);
+  float* Cr = g.SAf;  // this member's rows of C (ld m), SA is no longer needed
+  for (int idx = tid; idx < rm * k; idx += HM_THREADS) {
+    int i = idx % rm, jj = idx / rm;
+    Cr[(int64_t)jj * m + ra + i] = i < l ? Ys[(int64_t)r * l + i + (int64_t)jj * gl] : 0.f;
+  }
+  cta_apply_q_rows<float>(g.Mh + ra, m, rm, l, tauM, Cr + ra, m, k, s);
+  // D: P W(:, order) S through the stack of SB and this member's block of SB
+  for (int idx = tid; idx < l * k; idx += HM_THREADS) Xs[idx] = 0.f;
+  __syncthreads();
+  for (int idx = tid; idx < l * k; idx += HM_THREADS) {
+    int j = idx % l, jj = idx / l;
+    Xs[(int64_t)jj * l + perm[j]] = W[(int64_t)s.order[jj] * l + j];
+  }
+  __syncthreads();
+  for (int idx = tid; idx < gl * k; idx += HM_THREADS) {
+    int i = idx % gl, jj = idx / gl;
+    Ys[idx] = i < l ? Xs[i + (int64_t)jj * l] : 0.f;
+  }
+  cta_apply_q_rows<float>(stkB, gl, gl, l, tsB, Ys, gl, k, s);
+  for (int idx = tid; idx < rn * k; idx += HM_THREADS) {
+    int i = idx % rn, jj = idx / rn;
+    g.Vs[(int64_t)jj * n + ca + i] = i < l ? Ys[(int64_t)r * l + i + (int64_t)jj * gl] : 0.f;
+  }
+  cta_apply_q_rows<float>(g.SBf + ca, n, rn, l, tauB, g.Vs + ca, n, k, s);
+  // 8. every member's rows finite?  Then the result, in FP64
+  int bad = 0;
+  for (int idx = tid; idx < rm * k; idx += HM_THREADS)
+    if (!isfinite(Cr[(int64_t)(idx / rm) * m + ra + idx % rm])) bad = 1;
+  for (int idx = tid; idx < rn * k; idx += HM_THREADS)
+    if (!isfinite(g.Vs[(int64_t)(idx / rn) * n + ca + idx % rn])) bad = 1;
+  bad = __syncthreads_or(bad);
+  if (tid == 0) g.xch[(int64_t)r * HM_GANG_XCH + 6] = bad;
+  gang_sync(e, c0, 4, G);
+  bool anybad = false;
+  for (int q = 0; q < G; ++q) anybad = anybad || g.xch[(int64_t)q * HM_GANG_XCH + 6] != 0.0;
+  if (anybad) {
+    gang_leave(e, c0, 4, 5);
+    if (r == 0) task_rkadd(e, t, s, ti);  // the inputs are untouched so far
+    return;
+  }
+  double* Uout = loc(e, t.e);
+  double* Vout = loc(e, t.f);
+  for (int idx = tid; idx < rm * k; idx += HM_THREADS) {
+    int i = idx % rm, jj = idx / rm;
+    Uout[(int64_t)jj * t.lde + ra + i] = (double)Cr[(int64_t)jj * m + ra + i];
+  }
+  for (int idx = tid; idx < rn * k; idx += HM_THREADS) {
+    int i = idx % rn, jj = idx / rn;
+    Vout[(int64_t)jj * t.ldf + ca + i] = (double)g.Vs[(int64_t)jj * n + ca + i] * S;
+  }
+  gang_sync(e, c0, 5, G);
+  if (r == 0 && tid == 0) {
+    if (s.ivals[13]) set_status(e.status, DS_RANK);
+    if (t.rout >= 0) e.ranks[t.rout] = k;
+    atomicAdd(e.counters, 1ull);
+    atomicAdd(e.counters + 1, 1ull);
+    atomicAdd(e.counters + 11, 1ull);  // truncations run by a gang
+  }
+  if (r == 0)
+    count_f32(s, 2.0 * (n + m) * (double)l * l + (double)m * l * l + 4.0 * (double)G * l * l * l +
+                     4.0 * (m + n) * (double)l * k);
+}
+
 __device__ void task_rkadd(const ExecEnv& e, const HTask& t, Smem& s, long long ti) {
   int m = t.m, n = t.n;
   bool aid = t.flags & F_A_IDENT, bid = t.flags & F_B_IDENT, btr = t.flags & F_B_TRANS;
@@ -931,7 +1276,8 @@ __device__ void run_task(const ExecEnv& e, const HTask& t, Smem& s, long long ti
       task_chol(e, t, s);
       break;
     case T_RKADD:
-      task_rkadd(e, t, s, ti);
+      if (t.pad1 > 1) task_rkadd_gang(e, t, s, ti);
+      else task_rkadd(e, t, s, ti);
       break;
     case T_ROWMERGE:
       task_rowmerge(e, t, s, ti);
@@ -1002,6 +1348,11 @@ __global__ void __launch_bounds__(HM_THREADS, 1) exec_tasks(ExecEnv e) {
         atomicAdd(e.type_cnt + task.type, 1ull);
         if (e.task_ns) e.task_ns[t] = (uint32_t)(dt < 0xffffffffull ? dt : 0xffffffffull);
       }
+    }
+    if (skip && threadIdx.x == 0) {
+      // a skipped gang member still arrives at all its gang's barriers
+      const HTask& sk = e.tasks[t];
+      if (sk.type == T_RKADD && sk.pad1 > 1) atomicAdd(e.gang + (t - sk.pad0), 5);
     }
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -20,6 +20,7 @@ struct ExecEnv {
   const int32_t* dep_idx;
   const LeafRef* leaves;
   int* done;                  // per task, 0 -> 1 when finished
+  int* gang;                  // per task, the gang barrier counter of a gang's member 0
   unsigned long long* head;   // next task to take
   int* status;                // device status word (hmat_status numbering)
   long long* fail_task;       // 1 + index of the task that set the status first

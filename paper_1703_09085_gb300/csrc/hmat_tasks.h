@@ -75,6 +75,18 @@ struct LeafRef {
   int64_t a, b;        // dense: N at a; low rank: U at a, V at b
 };
 
+// Gang tasks: a T_RKADD with pad1 = G > 1 is run by G CTAs together, the
+// task list holding G consecutive copies (pad0 = the member's rank); only
+// member 0 is a dependency of later tasks, and it finishes last.  q holds
+// the stacked-width capacity L, list_begin the offset (doubles) of the gang
+// region in the task's scratch.
+#define HM_GANG_XCH 8  // doubles of exchange per member
+#define HM_GANG_MIN_ROWS 128  // rows of a member's block
+static inline int64_t gang_ws_doubles(int64_t m, int64_t n, int64_t L, int64_t G) {
+  int64_t fl = 2 * G * L * L + 3 * (m + n) * L + G * (3 * G * L * L + L * L);
+  return G * HM_GANG_XCH + (fl + 1) / 2 + G * 4 * L + G * 4 * L + 64;
+}
+
 // Device status word values (hmat_status numbering).
 enum DevStatus : int32_t {
   DS_OK = 0, DS_SINGULAR = 3, DS_NONFINITE = 4, DS_RANK = 5, DS_TIMEOUT = 6, DS_INTERNAL = 9

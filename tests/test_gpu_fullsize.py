@@ -30,6 +30,7 @@ def test_laplace3d_32_mixed_matches_plain_fp64(ctx):
     sa, sb = a.H.stats(), b.H.stats()
     assert sa["status"] == 0 and sb["status"] == 0
     assert 0 < sb["truncations"] < sa["truncations"]
+    assert sb["gang_truncations"] > 0  # the 1024 x 1024 blocks ran as gangs of CTAs
     v0 = hs.start_vector(p.n, 0)
     ea = a.precond_error(v0[a.perm])
     eb = b.precond_error(v0[b.perm])

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 import hmat_synth as hs
+import oracle
 from gpu_util import GpuProblem, hm
 from oracle import mlp as omlp
 
@@ -113,12 +114,17 @@ def test_training_lowers_loss_and_sizes_sketches(ctx):
     h, q = res["heuristic"], res["predictor"]
     print({k: (h[k], q[k]) for k in ("sketch_columns", "sketch_attempts", "rand_truncations", "rand_fallbacks",
                                      "factor_seconds")}, errs)
-    # the same preconditioner quality (the heuristic run is pinned to the
-    # oracle by the H-LU tests)
+    # the same preconditioner quality, and both within 2x of the oracle's at
+    # the same eps (Section 7's measure)
     assert errs["predictor"] <= 2.0 * errs["heuristic"] and errs["heuristic"] <= 2.0 * errs["predictor"]
+    ct, bt, csr, OH = oracle.setup(p)
+    OH.lu(p.eps, True)
+    err_o, _ = OH.precond_error(csr, v0)
+    for name in errs:
+        assert errs[name] <= 2.0 * err_o and err_o <= 2.0 * errs[name], (name, errs[name], err_o)
     # the gain: first sketches sized closer to the rank need fewer retries and
     # no more columns over all attempts
-    assert q["rand_truncations"] > 5000 and h["rand_truncations"] > 5000
+    assert q["rand_truncations"] > 2000 and h["rand_truncations"] > 2000
     assert q["sketch_attempts"] <= 0.95 * h["sketch_attempts"]
     assert q["sketch_columns"] <= h["sketch_columns"]
     assert q["rand_fallbacks"] <= 1.5 * h["rand_fallbacks"] + 5
