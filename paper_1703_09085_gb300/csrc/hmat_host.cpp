@@ -431,13 +431,11 @@ struct Sched {
     return id;
   }
 
-  // Members 1..G-1 of a gang whose member 0 was just emitted as task id0:
-  // the same task with its rank, the same predecessors, and no object
-  // bookkeeping (later tasks depend on member 0 alone, which finishes last).
-  void emit_gang_members(int32_t id0, int G) {
-    for (int r = 1; r < G; ++r) {
-      HTask t = tasks[(size_t)id0];
-      t.pad0 = r;
+  // Members of a gang whose member 0 was just emitted as task id0, given
+  // as tasks of their own (their leaf ranges differ): the same predecessors,
+  // no object bookkeeping.
+  void emit_gang_copies(int32_t id0, const std::vector<HTask>& members) {
+    for (const HTask& t : members) {
       int64_t d0 = dep_ptr[(size_t)id0], d1 = dep_ptr[(size_t)id0 + 1];
       for (int64_t k = d0; k < d1; ++k) dep_idx.push_back(dep_idx[(size_t)k]);
       dep_ptr.push_back((int64_t)dep_idx.size());
@@ -446,6 +444,18 @@ struct Sched {
       for (int k = 0; k < 4; ++k) feat.push_back(feat[4 * (size_t)id0 + k]);
       tasks.push_back(t);
     }
+  }
+
+  // Members 1..G-1 of a gang whose member 0 was just emitted as task id0:
+  // the same task with its rank, the same predecessors, and no object
+  // bookkeeping (later tasks depend on member 0 alone, which finishes last).
+  void emit_gang_members(int32_t id0, int G) {
+    std::vector<HTask> m;
+    for (int r = 1; r < G; ++r) {
+      m.push_back(tasks[(size_t)id0]);
+      m.back().pad0 = r;
+    }
+    emit_gang_copies(id0, m);
   }
 
   // Reorder the list by ASAP level (stable): still a topological order, and
@@ -697,12 +707,59 @@ struct Sym {
     t.c = out;
     t.ldc = ldout;
     t.wa = wcode;
+    if (inobj >= 0) reads.push_back(inobj);
+    std::vector<int> cut = out_rows >= 4 * HM_GANG_MIN_ROWS ? hmv_cuts(L, trans, out_rows) : std::vector<int>();
     t.list_begin = (int)S.leaves.size();
     t.list_len = (int)L.size();
     S.leaves.insert(S.leaves.end(), L.begin(), L.end());
-    if (inobj >= 0) reads.push_back(inobj);
-    S.emit(t, reads, {outobj});
+    if (cut.size() < 2) {
+      S.emit(t, reads, {outobj});
+      return true;
+    }
+    // a gang: member r takes the leaves [cut[r], cut[r+1]) and the output
+    // rows [p, q) they write (no leaf crosses a member's rows)
+    int G = (int)cut.size();
+    std::vector<HTask> mem((size_t)G, t);
+    for (int r = 0; r < G; ++r) {
+      int b0 = cut[(size_t)r], b1 = r + 1 < G ? cut[(size_t)r + 1] : (int)L.size();
+      HTask& m = mem[(size_t)r];
+      m.pad0 = r;
+      m.pad1 = G;
+      m.list_begin = t.list_begin + b0;
+      m.list_len = b1 - b0;
+      m.p = r == 0 ? 0 : orow(L[(size_t)b0], trans);
+      m.q = r + 1 < G ? orow(L[(size_t)b1], trans) : out_rows;
+    }
+    int32_t id0 = S.emit(mem[0], reads, {outobj});
+    S.emit_gang_copies(id0, std::vector<HTask>(mem.begin() + 1, mem.end()));
     return true;
+  }
+
+  static int orow(const LeafRef& L, bool trans) { return trans ? L.coff : L.roff; }
+
+  // Split points of an H x thin-dense product's leaf list for a gang: the
+  // leaves sorted by their first output row, cut only where no earlier leaf
+  // reaches past the next one's rows, the parts of about equal work.  Returns
+  // the first leaf of every part (fewer than two: no gang).
+  std::vector<int> hmv_cuts(std::vector<LeafRef>& L, bool trans, int out_rows) {
+    std::vector<int> cut;
+    if (L.size() < 8) return cut;
+    std::vector<LeafRef> S(L);
+    std::stable_sort(S.begin(), S.end(), [&](const LeafRef& a, const LeafRef& b) { return orow(a, trans) < orow(b, trans); });
+    std::vector<double> work(S.size() + 1, 0.0);
+    for (size_t i = 0; i < S.size(); ++i)
+      work[i + 1] = work[i] + (S[i].kind == 1 ? (double)S[i].rows * S[i].cols : 16.0 * (S[i].rows + S[i].cols));
+    int G = std::min(8, out_rows / HM_GANG_MIN_ROWS);
+    cut.push_back(0);
+    int reach = 0;  // largest end row of the leaves before i
+    for (size_t i = 0; i < S.size() && (int)cut.size() < G; ++i) {
+      int r0 = orow(S[i], trans);
+      if (i > 0 && reach <= r0 && work[i] >= work.back() * (double)cut.size() / G) cut.push_back((int)i);
+      reach = std::max(reach, r0 + (trans ? S[i].cols : S[i].rows));
+    }
+    if (cut.size() < 2) cut.clear();
+    else L.swap(S);  // the gang's members take consecutive runs of the sorted list
+    return cut;
   }
 
   bool subtree_zero(const hmat* M, int b) {

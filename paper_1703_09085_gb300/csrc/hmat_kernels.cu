@@ -314,8 +314,10 @@ __device__ void task_hmv(const ExecEnv& e, const HTask& t, Smem& s, bool f32) {
   double* out = loc(e, t.c);
   const double* in = loc(e, t.b);
   if (t.flags & F_ZERO_OUT) {
-    for (int idx = threadIdx.x; idx < t.m * w; idx += HM_THREADS)
-      out[(int64_t)(idx / t.m) * t.ldc + idx % t.m] = 0.0;
+    // a gang member zeroes its own rows [p, q) of the output
+    int z0 = t.pad1 > 1 ? t.p : 0, zr = (t.pad1 > 1 ? t.q : t.m) - z0;
+    for (int idx = threadIdx.x; idx < zr * w; idx += HM_THREADS)
+      out[(int64_t)(idx / zr) * t.ldc + z0 + idx % zr] = 0.0;
     __syncthreads();
   }
   if (w <= 0) return;
@@ -1231,6 +1233,12 @@ __device__ void run_task(const ExecEnv& e, const HTask& t, Smem& s, long long ti
       break;
     case T_HMV:
       task_hmv(e, t, s, f32);
+      if (t.pad1 > 1) {
+        // a gang of H x thin-dense products on disjoint output rows: member 0
+        // finishes (and releases the successors) after every member
+        if (t.pad0 == 0) gang_sync(e, ti, 1, t.pad1);
+        else gang_leave(e, ti - t.pad0, 0, 1);
+      }
       break;
     case T_DENSIFY:
       task_densify(e, t, s);
@@ -1352,7 +1360,8 @@ __global__ void __launch_bounds__(HM_THREADS, 1) exec_tasks(ExecEnv e) {
     if (skip && threadIdx.x == 0) {
       // a skipped gang member still arrives at all its gang's barriers
       const HTask& sk = e.tasks[t];
-      if (sk.type == T_RKADD && sk.pad1 > 1) atomicAdd(e.gang + (t - sk.pad0), 5);
+      if ((sk.type == T_RKADD || sk.type == T_HMV) && sk.pad1 > 1)
+        atomicAdd(e.gang + (t - sk.pad0), sk.type == T_RKADD ? 5 : 1);
     }
     __syncthreads();
     if (threadIdx.x == 0) {

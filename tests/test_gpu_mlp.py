@@ -110,18 +110,26 @@ def test_training_lowers_loss_and_sizes_sketches(ctx):
         st = gp.H.stats()
         assert st["status"] == 0
         errs[name] = gp.precond_error(v0[gp.perm])
+        rk = gp.H.ranks()
+        st["adm_mean_rank"] = float(rk[rk >= 0].mean())
         res[name] = st
     h, q = res["heuristic"], res["predictor"]
     print({k: (h[k], q[k]) for k in ("sketch_columns", "sketch_attempts", "rand_truncations", "rand_fallbacks",
                                      "factor_seconds")}, errs)
-    # the same preconditioner quality, and both within 2x of the oracle's at
-    # the same eps (Section 7's measure)
+    # the same preconditioner quality with and without the predictor, and
+    # never worse than 2x the oracle's at the same eps (Section 7's measure).
+    # The randomised truncation stops on an a-posteriori estimate that
+    # overstates the error, so it may keep a slightly larger rank and land
+    # below the oracle's error; the mean rank bounds that excess.
     assert errs["predictor"] <= 2.0 * errs["heuristic"] and errs["heuristic"] <= 2.0 * errs["predictor"]
     ct, bt, csr, OH = oracle.setup(p)
     OH.lu(p.eps, True)
     err_o, _ = OH.precond_error(csr, v0)
+    r_o = OH.ranks()
+    r_o = r_o[r_o >= 0].mean()
     for name in errs:
-        assert errs[name] <= 2.0 * err_o and err_o <= 2.0 * errs[name], (name, errs[name], err_o)
+        assert errs[name] <= 2.0 * err_o, (name, errs[name], err_o)
+        assert res[name]["adm_mean_rank"] <= r_o + 1.0, (name, res[name]["adm_mean_rank"], r_o)
     # the gain: first sketches sized closer to the rank need fewer retries and
     # no more columns over all attempts
     assert q["rand_truncations"] > 2000 and h["rand_truncations"] > 2000
