@@ -434,8 +434,9 @@ struct Sched {
   // Members of a gang whose member 0 was just emitted as task id0, given
   // as tasks of their own (their leaf ranges differ): the same predecessors,
   // no object bookkeeping.
-  void emit_gang_copies(int32_t id0, const std::vector<HTask>& members) {
-    for (const HTask& t : members) {
+  void emit_gang_copies(int32_t id0, const HTask* members, int count) {
+    for (int r = 0; r < count; ++r) {
+      const HTask& t = members[r];
       int64_t d0 = dep_ptr[(size_t)id0], d1 = dep_ptr[(size_t)id0 + 1];
       for (int64_t k = d0; k < d1; ++k) dep_idx.push_back(dep_idx[(size_t)k]);
       dep_ptr.push_back((int64_t)dep_idx.size());
@@ -455,7 +456,7 @@ struct Sched {
       m.push_back(tasks[(size_t)id0]);
       m.back().pad0 = r;
     }
-    emit_gang_copies(id0, m);
+    emit_gang_copies(id0, m.data(), (int)m.size());
   }
 
   // Reorder the list by ASAP level (stable): still a topological order, and
@@ -731,8 +732,27 @@ struct Sym {
       m.q = r + 1 < G ? orow(L[(size_t)b1], trans) : out_rows;
     }
     int32_t id0 = S.emit(mem[0], reads, {outobj});
-    S.emit_gang_copies(id0, std::vector<HTask>(mem.begin() + 1, mem.end()));
+    S.emit_gang_copies(id0, mem.data() + 1, G - 1);
     return true;
+  }
+
+  // Gang size of a rowmerge (m x (n0 + n1), stacked width at most l) of the
+  // mixed form: large ones are truncated by a gang of CTAs like rkadd's.
+  int merge_gang(int64_t m, int64_t n, int64_t l) const {
+    if (!mixed || std::min(m, n) < 4 * HM_GANG_MIN_ROWS || l > 128) return 1;
+    return (int)std::min<int64_t>(8, std::min(m, n) / HM_GANG_MIN_ROWS);
+  }
+  // Turn the rowmerge just emitted as task id0 into member 0 of a gang of G
+  // (n = n0 + n1, q = the stacked-width capacity, the gang region at
+  // base_ws in the task's scratch) and emit the other members.
+  void make_merge_gang(int32_t id0, int G, int64_t l, int64_t base_ws) {
+    HTask& g0 = S.tasks[(size_t)id0];
+    g0.n = g0.p + g0.q;
+    g0.q = (int)l;
+    g0.pad0 = 0;
+    g0.pad1 = G;
+    g0.list_begin = (int32_t)base_ws;
+    S.emit_gang_members(id0, G);
   }
 
   static int orow(const LeafRef& L, bool trans) { return trans ? L.coff : L.roff; }
@@ -1316,13 +1336,16 @@ struct Sym {
       t.cap = C.cap;
       int64_t l = (tmp[0][j].zero ? 0 : tmp[0][j].wmax) + (tmp[1][j].zero ? 0 : tmp[1][j].wmax);
       if (l > HM_LMAX_HOST) throw HmError(HMAT_ERR_RANK, "merged width exceeds the truncation limit");
-      int ws = S.alloc(rk_ws(nrj, m, l) + (int64_t)nrj * l + (mixed ? m * l + rand_ws(nrj, m, l) : 0));
+      int64_t base_ws = rk_ws(nrj, m, l) + (int64_t)nrj * l + (mixed ? m * l + rand_ws(nrj, m, l) : 0);
+      int G = merge_gang(nrj, (int64_t)t.p + t.q, l);
+      int ws = S.alloc(base_ws + (G > 1 ? gang_ws_doubles(nrj, (int64_t)t.p + t.q, l, G) : 0));
       t.ws = S.chunk_loc(ws);
       std::vector<int> reads;
       for (int i = 0; i < 2; ++i)
         if (tmp[i][j].obj >= 0) reads.push_back(tmp[i][j].obj);
-      S.emit(t, reads, {C.obj, S.chunk_obj(ws)});
+      int32_t id0 = S.emit(t, reads, {C.obj, S.chunk_obj(ws)});
       set_features(tcl, rr.son[j]);
+      if (G > 1) make_merge_gang(id0, G, l, base_ws);
       S.release(ws);
       C.wcode = width_from_slot(C.slot);
       C.zero = false;
@@ -1354,10 +1377,13 @@ struct Sym {
     t.cap = out.cap;
     int64_t l = (int64_t)col[0].cap + col[1].cap;
     if (l > HM_LMAX_HOST) throw HmError(HMAT_ERR_RANK, "merged width exceeds the truncation limit");
-    int ws = S.alloc(rk_ws(m, n, l) + (int64_t)m * l + (mixed ? n * l + rand_ws(m, n, l) : 0));
+    int64_t base_ws = rk_ws(m, n, l) + (int64_t)m * l + (mixed ? n * l + rand_ws(m, n, l) : 0);
+    int G = merge_gang(m, (int64_t)t.p + t.q, l);
+    int ws = S.alloc(base_ws + (G > 1 ? gang_ws_doubles(m, (int64_t)t.p + t.q, l, G) : 0));
     t.ws = S.chunk_loc(ws);
-    S.emit(t, {col[0].obj, col[1].obj}, {out.obj, S.chunk_obj(ws)});
+    int32_t id0 = S.emit(t, {col[0].obj, col[1].obj}, {out.obj, S.chunk_obj(ws)});
     set_features(tcl, rcl);
+    if (G > 1) make_merge_gang(id0, G, l, base_ws);
     S.release(ws);
     if (z.tmp) {
       z.tmp->wcode = width_from_slot(z.tmp->slot);
@@ -2411,7 +2437,8 @@ hmat_status hmat_analyze_lu(const hmat_btree* bt, int64_t n, const int64_t* rowp
     hmat_stats s = H.st;
     s.tasks = (int64_t)S.tasks.size();
     s.truncations = 0;  // truncation tasks of the schedule (those whose product is zero skip at run time)
-    for (const HTask& t : S.tasks) s.truncations += (t.type == T_RKADD || t.type == T_ROWMERGE) ? 1 : 0;
+    for (const HTask& t : S.tasks)  // a gang is one truncation
+      s.truncations += ((t.type == T_RKADD || t.type == T_ROWMERGE) && (t.pad1 <= 1 || t.pad0 == 0)) ? 1 : 0;
     s.schedule_seconds = secs;
     s.levels = S.levels();
     s.critical_flops = S.critical_flops();

@@ -520,13 +520,34 @@ __device__ void gang_put_r(const float* X, int ldx, const double* rd, int l, flo
 
 __device__ void task_rkadd(const ExecEnv& e, const HTask& t, Smem& s, long long ti);
 
+__device__ void task_rowmerge(const ExecEnv& e, const HTask& t, Smem& s, long long ti);
+
+// The single-CTA task a gang's member 0 falls back to (a rowmerge gang keeps
+// L in q, the single task its second part's rows).
+__device__ void gang_fallback(const ExecEnv& e, const HTask& t, Smem& s, long long ti) {
+  if (t.type == T_ROWMERGE) {
+    HTask u = t;
+    u.q = t.n - t.p;
+    task_rowmerge(e, u, s, ti);
+  } else {
+    task_rkadd(e, t, s, ti);
+  }
+}
+
+// A gang truncation of M = SA SB^T: for T_RKADD SA = [alpha A | Uin], SB =
+// [B | Vin] (Fig. rkadd); for T_ROWMERGE SA = [U0 | U1] and SB =
+// blockdiag(V0, V1) (Fig. rowmerge: two blocks side by side, n = n0 + n1
+// with n0 in p).
 __device__ void task_rkadd_gang(const ExecEnv& e, const HTask& t, Smem& s, long long ti) {
   const int r = t.pad0, G = t.pad1, L = t.q;
   const long long c0 = ti - r;  // member 0: the gang's counter
   const int m = t.m, n = t.n, tid = threadIdx.x;
-  bool btr = t.flags & F_B_TRANS;
+  const bool merge = t.type == T_ROWMERGE;
+  const int n0 = merge ? t.p : n;
+  const double alpha = merge ? 1.0 : t.alpha;
+  bool btr = !merge && (t.flags & F_B_TRANS);
   int w = width_of(e, t.wa);
-  int kin = t.rin >= 0 ? e.ranks[t.rin] : 0;
+  int kin = merge ? width_of(e, t.wb) : (t.rin >= 0 ? e.ranks[t.rin] : 0);
   int l = w + kin;
   const double* A = loc(e, t.a);
   const double* B = loc(e, t.b);
@@ -537,9 +558,13 @@ __device__ void task_rkadd_gang(const ExecEnv& e, const HTask& t, Smem& s, long 
   int ra = r * mb, rm = min(m, ra + mb) - ra;  // this member's rows of SA / Mhat / C
   int ca = r * nb, rn = min(n, ca + nb) - ca;  // and of SB / D
   auto sa = [&](int i, int j) -> double {    // stacked [alpha A | Uin]
-    return j < w ? t.alpha * A[(int64_t)j * t.lda + i] : Uin[(int64_t)(j - w) * t.ldc + i];
+    return j < w ? alpha * A[(int64_t)j * t.lda + i] : Uin[(int64_t)(j - w) * t.ldc + i];
   };
-  auto sb = [&](int i, int j) -> double {    // stacked [B | Vin]
+  auto sb = [&](int i, int j) -> double {    // stacked [B | Vin], or blockdiag(B, Vin)
+    if (merge) {
+      if (j < w) return i < n0 ? B[(int64_t)j * t.ldb + i] : 0.0;
+      return i >= n0 ? Vin[(int64_t)(j - w) * t.ldd + i - n0] : 0.0;
+    }
     return j < w ? (btr ? B[(int64_t)i * t.ldb + j] : B[(int64_t)j * t.ldb + i]) : Vin[(int64_t)(j - w) * t.ldd + i];
   };
   // 1. the largest entries and the non-zero pattern of this member's rows
@@ -580,13 +605,13 @@ __device__ void task_rkadd_gang(const ExecEnv& e, const HTask& t, Smem& s, long 
     any_b = any_b || x[3] != 0.0;
   }
   double S = MA * MB;
-  bool zero = w == 0 || ((t.flags & F_CHECK_ZERO) && !(any_a && any_b));
+  bool zero = merge ? (w == 0 || kin == 0) : (w == 0 || ((t.flags & F_CHECK_ZERO) && !(any_a && any_b)));
   bool ok = !zero && l <= L && l <= HM_FACT32_DIRECT && l >= e.rand_min_l && l <= rm && l <= rn && l <= m &&
             l <= n && 3 * (int64_t)l * l + 2 * l <= 2 * (int64_t)HM_JAC_SMEM && S > 0.0 &&
             isfinite(S);
   if (!ok) {
     gang_leave(e, c0, 1, 5);
-    if (r == 0) task_rkadd(e, t, s, ti);
+    if (r == 0) gang_fallback(e, t, s, ti);
     return;
   }
   // 3. FP32 copies of this member's rows, scaled by the largest entries
@@ -651,7 +676,7 @@ __device__ void task_rkadd_gang(const ExecEnv& e, const HTask& t, Smem& s, long 
   }
   if (!isfinite(TM) || !isfinite(TA) || TA * 9e-14 > 1e-2 * e.eps * e.eps * TM) {
     gang_leave(e, c0, 3, 5);
-    if (r == 0) task_rkadd(e, t, s, ti);
+    if (r == 0) gang_fallback(e, t, s, ti);
     return;
   }
   // 6. R_T from the stacked R factors of Mhat; the FP32 core on R_T (in
@@ -737,7 +762,7 @@ __device__ void task_rkadd_gang(const ExecEnv& e, const HTask& t, Smem& s, long 
   for (int q = 0; q < G; ++q) anybad = anybad || g.xch[(int64_t)q * HM_GANG_XCH + 6] != 0.0;
   if (anybad) {
     gang_leave(e, c0, 4, 5);
-    if (r == 0) task_rkadd(e, t, s, ti);  // the inputs are untouched so far
+    if (r == 0) gang_fallback(e, t, s, ti);  // the inputs are untouched so far
     return;
   }
   double* Uout = loc(e, t.e);
@@ -1125,8 +1150,11 @@ __device__ void task_rowmerge(const ExecEnv& e, const HTask& t, Smem& s, long lo
   note_exact(e, ti, l, k);
 }
 
-// FP64 operations of the non-truncation tasks (counted by thread 0).
-__device__ double task_flops(const ExecEnv& e, const HTask& t) {
+// FP64 operations of the non-truncation tasks: this lane's share (warp 0
+// sums the shares; leaf lists are split over the lanes, everything else is
+// lane 0's).
+__device__ double task_flops(const ExecEnv& e, const HTask& t, int lane) {
+  if (lane != 0 && t.type != T_HMV && t.type != T_DENSIFY) return 0.0;
   switch (t.type) {
     case T_LU:
       return 2.0 / 3.0 * (double)t.m * t.m * t.m;
@@ -1142,7 +1170,7 @@ __device__ double task_flops(const ExecEnv& e, const HTask& t) {
       return (double)t.m * t.n;
     case T_HMV: {
       double w = width_of(e, t.wa), f = 0.0;
-      for (int li = 0; li < t.list_len; ++li) {
+      for (int li = lane; li < t.list_len; li += 32) {
         const LeafRef& L = e.leaves[t.list_begin + li];
         if (L.kind == 1) f += 2.0 * L.rows * L.cols * w;
         else f += 2.0 * e.ranks[L.rank_slot] * (double)(L.rows + L.cols) * w;
@@ -1151,7 +1179,7 @@ __device__ double task_flops(const ExecEnv& e, const HTask& t) {
     }
     case T_DENSIFY: {
       double f = 0.0;
-      for (int li = 0; li < t.list_len; ++li) {
+      for (int li = lane; li < t.list_len; li += 32) {
         const LeafRef& L = e.leaves[t.list_begin + li];
         if (L.kind == 2) f += 2.0 * e.ranks[L.rank_slot] * (double)L.rows * L.cols;
       }
@@ -1165,8 +1193,9 @@ __device__ double task_flops(const ExecEnv& e, const HTask& t) {
 // Algorithmic bytes of a task: what it must read and write once (FP64),
 // e.g. 8 [(m + n) l + (m + n) k] for a truncation of stacked width l to rank
 // k; l_in is the stacked width read before the task ran (-1: not a
-// truncation).  Counted by thread 0 after the task.
-__device__ double task_bytes(const ExecEnv& e, const HTask& t, int l_in) {
+// truncation).  This lane's share, as in task_flops.
+__device__ double task_bytes(const ExecEnv& e, const HTask& t, int l_in, int lane) {
+  if (lane != 0 && t.type != T_HMV && t.type != T_DENSIFY) return 0.0;
   switch (t.type) {
     case T_LU:
     case T_INV:
@@ -1187,7 +1216,7 @@ __device__ double task_bytes(const ExecEnv& e, const HTask& t, int l_in) {
     case T_HMV:
     case T_DENSIFY: {
       double w = t.type == T_HMV ? width_of(e, t.wa) : 0.0, b = 0.0;
-      for (int li = 0; li < t.list_len; ++li) {
+      for (int li = lane; li < t.list_len; li += 32) {
         const LeafRef& L = e.leaves[t.list_begin + li];
         double f = L.kind == 1 ? (double)L.rows * L.cols : (double)e.ranks[L.rank_slot] * (L.rows + L.cols);
         b += 8.0 * (f + (t.type == T_HMV ? 2.0 * (L.rows + L.cols) * w : (double)L.rows * L.cols));
@@ -1196,8 +1225,9 @@ __device__ double task_bytes(const ExecEnv& e, const HTask& t, int l_in) {
     }
     case T_RKADD:
     case T_ROWMERGE: {
-      if (l_in <= 0) return 0.0;
-      int n = t.type == T_RKADD ? t.n : t.p + t.q;
+      // a gang's bytes are counted once, by member 0
+      if (l_in <= 0 || (t.pad1 > 1 && t.pad0 != 0)) return 0.0;
+      int n = (t.type == T_RKADD || t.pad1 > 1) ? t.n : t.p + t.q;
       int k = t.rout >= 0 ? e.ranks[t.rout] : 0;
       return 8.0 * ((double)(t.m + n) * l_in + (double)(t.m + n) * k);
     }
@@ -1288,7 +1318,8 @@ __device__ void run_task(const ExecEnv& e, const HTask& t, Smem& s, long long ti
       else task_rkadd(e, t, s, ti);
       break;
     case T_ROWMERGE:
-      task_rowmerge(e, t, s, ti);
+      if (t.pad1 > 1) task_rkadd_gang(e, t, s, ti);
+      else task_rowmerge(e, t, s, ti);
       break;
     default:
       if (threadIdx.x == 0) set_status(e.status, DS_INTERNAL);
@@ -1335,19 +1366,20 @@ __global__ void __launch_bounds__(HM_THREADS, 1) exec_tasks(ExecEnv e) {
     if (!skip) {
       HTask task = e.tasks[t];
       if (threadIdx.x == 0) s.bcast[7] = 0.0;
-      if (threadIdx.x == 0 && task.type != T_RKADD && task.type != T_ROWMERGE) {
-        double f = task_flops(e, task);
-        if (f > 0.0) atomicAdd(e.flops, f);
-      }
       int l_in = 0;
       if (threadIdx.x == 0) l_in = trunc_width(e, task);
       __syncthreads();  // every thread has read the rank slots the task may overwrite
       run_task(e, task, s, t);
       __syncthreads();
       if (threadIdx.x == 0 && hm_status_won) *e.fail_task = t + 1;
-      if (threadIdx.x == 0) {
-        double b = task_bytes(e, task, l_in);
-        if (b > 0.0) atomicAdd(e.bytes, b);
+      if (threadIdx.x < 32) {
+        // the task's counts (a task changes no rank that its own count reads)
+        l_in = __shfl_sync(0xffffffffu, l_in, 0);
+        double b = warp_sum(task_bytes(e, task, l_in, threadIdx.x));
+        double f = (task.type != T_RKADD && task.type != T_ROWMERGE) ? warp_sum(task_flops(e, task, threadIdx.x))
+                                                                       : 0.0;
+        if (threadIdx.x == 0 && b > 0.0) atomicAdd(e.bytes, b);
+        if (threadIdx.x == 0 && f > 0.0) atomicAdd(e.flops, f);
       }
       if (threadIdx.x == 0 && s.bcast[7] > 0.0) atomicAdd(e.flops32, s.bcast[7]);
       if (threadIdx.x == 0 && task.type >= 0 && task.type < 16) {
@@ -1360,8 +1392,8 @@ __global__ void __launch_bounds__(HM_THREADS, 1) exec_tasks(ExecEnv e) {
     if (skip && threadIdx.x == 0) {
       // a skipped gang member still arrives at all its gang's barriers
       const HTask& sk = e.tasks[t];
-      if ((sk.type == T_RKADD || sk.type == T_HMV) && sk.pad1 > 1)
-        atomicAdd(e.gang + (t - sk.pad0), sk.type == T_RKADD ? 5 : 1);
+      if ((sk.type == T_RKADD || sk.type == T_ROWMERGE || sk.type == T_HMV) && sk.pad1 > 1)
+        atomicAdd(e.gang + (t - sk.pad0), sk.type == T_HMV ? 1 : 5);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
