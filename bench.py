@@ -196,7 +196,11 @@ def job_throughput(units: float, seconds: float, world: int, device=None):
 # DRAM bytes (read + write) of one exec_tasks launch, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the source tree whose
 # csrc hash is given; see profiles/launches_laplace3d_32.md.
-TRAFFIC = {"laplace3d_32": {"csrc": "9d4de9a4b5326e84", "bytes": 2937054976 + 8743640576}}
+# The 64^3 figure scales the 32^3 capture by the truncations per launch
+# (621 514 / 34 684): ncu's device-memory save and restore of a 52 GB launch
+# is beyond a capture that ends by itself.
+TRAFFIC = {"laplace3d_32": {"csrc": "1234ecd9b77195f7", "bytes": 5842257920 + 15209673472},
+           "laplace3d_64": {"csrc": "1234ecd9b77195f7", "bytes": round((5842257920 + 15209673472) * 621514 / 34684)}}
 
 
 def csrc_hash() -> str:
@@ -323,13 +327,19 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     def step(precision=prec, mode=g.HMAT_ACCUMULATED):
         for wk, pr in zip(work, pristine):
             wk.copy_values_from(pr)
-        g.lu_batched(ctx, work, eps, max_rank=args.max_rank, precision=precision, reuse_schedule=True, mode=mode)
+        if args.op == "lu":
+            g.lu_batched(ctx, work, eps, max_rank=args.max_rank, precision=precision, reuse_schedule=True, mode=mode)
+        else:  # H-Cholesky or H-inversion: the schedule is built in every call, inside the step
+            for wk in work:
+                getattr(wk, args.op)(eps, max_rank=args.max_rank, precision=precision)
 
     sched_first = None
     for i in range(args.warmup):
         step()
         if i == 0:
-            sched_first = work[0].stats()["schedule_seconds"]
+            # the LU's timed steps reuse this schedule, so its pass is added to
+            # every step; the other operations build theirs inside the step
+            sched_first = work[0].stats()["schedule_seconds"] if args.op == "lu" else 0.0
     torch.cuda.synchronize()
     clocks = ClockSampler(local_rank) if rank == 0 else None
     if world > 1:
@@ -369,30 +379,37 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     h2d = sum(8 * (c.rowptr.size + c.colidx.size + c.val.size) + 16 * c.n for c in csrs)
     d2h = sum(8 * g.lib().hmat_blocktree_size(bt.h) for bt in bts)
     e2e_times = []
-    e2e_steps = min(args.steps, 2)
-    for i in range(1 + e2e_steps):
+    e2e_steps = 0 if args.no_e2e else min(args.steps, 2)
+    for i in range(1 + e2e_steps if e2e_steps else 0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         Hs = [g.HMatrix(ctx, bt, c) for bt, c in zip(bts, csrs)]
-        g.lu_batched(ctx, Hs, eps, max_rank=args.max_rank, precision=prec)
+        if args.op == "lu":
+            g.lu_batched(ctx, Hs, eps, max_rank=args.max_rank, precision=prec)
+        else:
+            for H in Hs:
+                getattr(H, args.op)(eps, max_rank=args.max_rank, precision=prec)
         for H in Hs:
             H.ranks()
         torch.cuda.synchronize()
         if i >= 1:
             e2e_times.append(time.perf_counter() - t0)
         del Hs
-    e2e_value, e2e_s = job_throughput(statistics.mean(truncs) * e2e_steps, sum(e2e_times), world, dev)
+    e2e_value, e2e_s = (job_throughput(statistics.mean(truncs) * e2e_steps, sum(e2e_times), world, dev)
+                        if e2e_steps else (None, None))
 
     if rank != 0:
         return
     # preconditioner quality of the last factorisation (power iteration with the
     # GPU solves); batches report their first instances
     nq = min(len(probs), 4)
-    perr = [precond_error(g, work[i], cts[i], csrs[i], probs[i]) for i in range(nq)]
+    # (the LU solve measures the LU factors; the other operations' quality is
+    # checked against the oracle by the tests)
+    perr = [precond_error(g, work[i], cts[i], csrs[i], probs[i]) for i in range(nq)] if args.op == "lu" else [None]
     types = {name: {"count": st["type_count"][i], "cta_s": st["type_seconds"][i]}
              for i, name in enumerate(TASK_NAMES) if st["type_count"][i]}
     pcg = None
-    if args.workload in PCG_WORKLOADS:
+    if args.workload in PCG_WORKLOADS and args.op == "lu":
         # 8 seeded N(0, 1) right-hand sides (seed 4), FP64 CG to 1e-10
         p0 = probs[0]
         B = np.stack([hs.normal(4 + c, p0.n) for c in range(8)])  # (8, n), original ordering
@@ -405,7 +422,9 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     # the plain FP64 accumulated form on the same GPU, same matrices: the comparator
     fp64 = None
     est = FP64_OVER_MIXED * statistics.mean(step_ms) / 1e3
-    if args.precision == "mixed" and not args.no_fp64 and time.time() - T_START + est > args.time_budget:
+    if args.op != "lu":
+        fp64 = None
+    elif args.precision == "mixed" and not args.no_fp64 and time.time() - T_START + est > args.time_budget:
         fp64 = {"skipped": f"the plain FP64 factorisation (about {est:.0f} s) would end past the bench's time "
                            f"budget of {args.time_budget:.0f} s"}
     elif args.precision == "mixed" and not args.no_fp64:
@@ -425,7 +444,9 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     # chosen precision: the paper's comparison, time and truncations
     standard = None
     est = STANDARD_OVER_ACC * statistics.mean(step_ms) / 1e3
-    if not args.no_standard and time.time() - T_START + est > args.time_budget:
+    if args.op != "lu":
+        standard = None
+    elif not args.no_standard and time.time() - T_START + est > args.time_budget:
         standard = {"skipped": f"the standard-form factorisation (about {est:.0f} s) would end past the bench's "
                                f"time budget of {args.time_budget:.0f} s"}
     elif not args.no_standard:
@@ -449,7 +470,8 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     achieved_gbs = statistics.mean(nbytes) / avg_kern_s / 1e9
     ref = oracle_values(args.workload)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "metric": OP_METRIC[args.op], "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup,
         "ms_per_step": statistics.mean(step_ms) + 1e3 * sched_first, "higher_is_better": True,
         "scaling": "strong" if args.workload == "diffusion2d_batch64" else "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
@@ -461,11 +483,12 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         "tasks_per_step": int(statistics.mean(tasks)),
         "schedule_s": statistics.mean(sched),
         "schedule_s_first_call": sched_first,
-        "schedule_note": "setup_s and value include the first call's symbolic pass in every step (the timed "
-                         "numeric steps reuse its schedule); e2e builds it every step",
+        "schedule_note": ("setup_s and value include the first call's symbolic pass in every step (the timed "
+                          "numeric steps reuse its schedule); e2e builds it every step") if args.op == "lu" else
+                         "the operation builds its schedule in every call, inside the timed step",
         "tree_build_s": tree_s,
         "precond_error": perr if len(probs) > 1 else perr[0],
-        "oracle": ref,
+        "oracle": ref if args.op == "lu" else None,
         "pcg": pcg,
         "randomised_truncations": st["rand_truncations"], "randomised_fallbacks": st["rand_fallbacks"],
         "plain_fp64": fp64,
@@ -488,8 +511,10 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
                      "alu_peak_note": "nominal FP64 (1.25 TFLOP/s) and FP32 (152 SMs x 128 lanes x 2 x 2070 MHz) "
                                       "rates: the measured peaks file has no FP64 or FP32 vector figure",
                      "traffic_note": TRAFFIC_NOTE},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "ms_per_step": 1e3 * e2e_s / e2e_steps, "steps": e2e_steps},
+        "e2e": ({"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                 "ms_per_step": 1e3 * e2e_s / e2e_steps, "steps": e2e_steps} if e2e_steps else
+                {"skipped": "--no-e2e: a second factorisation beside the kept schedule does not fit in device "
+                            "memory at this size"}),
         "clocks": clk,
         "device_bytes": st["device_bytes"],
         "bench_wall_s": time.time() - T_START,
@@ -498,6 +523,10 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_sample(args.workload)
     print(json.dumps(line), flush=True)
+
+
+OP_METRIC = {"lu": METRIC, "cholesky": "H-Cholesky setup truncations/s (accumulated updates)",
+             "invert": "H-inversion truncations/s (accumulated updates, Fig. invert)"}
 
 
 HMUL_METRIC = "H-matrix multiplication Z <- blocktrunc(Z - X Y) truncations/s (accumulated updates) vs plain FP64"
@@ -597,7 +626,9 @@ def run_hmul(args, rank: int, world: int, local_rank: int) -> None:
     err = rel_error(Z)
     fp64 = None
     est = FP64_OVER_MIXED * statistics.mean(step_ms) / 1e3
-    if args.precision == "mixed" and not args.no_fp64 and time.time() - T_START + est > args.time_budget:
+    if args.op != "lu":
+        fp64 = None
+    elif args.precision == "mixed" and not args.no_fp64 and time.time() - T_START + est > args.time_budget:
         fp64 = {"skipped": f"the plain FP64 factorisation (about {est:.0f} s) would end past the bench's time "
                            f"budget of {args.time_budget:.0f} s"}
     elif args.precision == "mixed" and not args.no_fp64:
@@ -705,6 +736,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparator")
     ap.add_argument("--no-standard", action="store_true", help="skip the standard-form comparator")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end steps (largest workloads)")
+    ap.add_argument("--op", default="lu", choices=["lu", "cholesky", "invert"],
+                    help="the operation timed on an LU workload: H-LU (default), H-Cholesky or H-inversion")
     ap.add_argument("--time-budget", type=float, default=1650.0,
                     help="seconds after which the optional comparators are skipped")
     args = ap.parse_args()
