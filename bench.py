@@ -218,6 +218,29 @@ def traffic_per_launch(workload: str):
     return rec["bytes"] if rec and rec["csrc"] == csrc_hash() else None
 
 
+def train_predictor(g, ctx):
+    """The rank predictor trained as the 64^3 configuration asks: (features,
+    rank) pairs of the exact truncations of plain FP64 H-LUs of the smaller
+    configurations (the 64^2 Laplacian, the 32^3 Laplacian, the first four
+    instances of the diffusion batch), then Adam on the GPU."""
+    t0 = time.perf_counter()
+    Xs, ys = [], []
+    for p in [hs.laplace2d_64(), hs.laplace3d_32()] + list(hs.diffusion2d_batch()[:4]):
+        ct = g.ClusterTree(ctx, p.coords(), p.leaf)
+        bt = g.BlockTree(ctx, ct, ct, p.eta)
+        H = g.HMatrix(ctx, bt, p.matrix())
+        H.lu(p.eps, record_training=True)
+        X, y = H.training_data()
+        Xs.append(X)
+        ys.append(y)
+    X, y = np.concatenate(Xs), np.concatenate(ys)
+    P = g.RankPredictor(ctx, seed=7)
+    loss0, _ = P.grad(X, y)
+    loss = P.train(X, y, epochs=60, batch=256, lr=3e-3, seed=3)
+    return P, {"pairs": int(len(y)), "sources": "FP64 H-LUs of laplace2d_64, laplace3d_32, diffusion batch 0-3",
+               "loss_before": float(loss0), "loss_after": float(loss), "seconds": time.perf_counter() - t0}
+
+
 def workload_config(args, probs, world: int) -> dict:
     """The config object of both arms' JSON lines."""
     par = (f"instances sharded: 64 instances over {world} rank(s) by LPT on n log2(n)^2"
@@ -225,7 +248,7 @@ def workload_config(args, probs, world: int) -> dict:
     return {"workload": args.workload, "instances": len(probs), "n": sum(p.n for p in probs), "leaf": probs[0].leaf,
             "eta": probs[0].eta, "eps": probs[0].eps, "precision": args.precision,
             "max_rank": args.max_rank or 64, "l2": "flushed between steps (256 MiB write)",
-            "parallelism": par}
+            "parallelism": par, "rank_predictor": "on" if getattr(args, "predictor", False) else "off"}
 
 
 def run_reference_hmul(args) -> None:
@@ -323,12 +346,14 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     work = [g.HMatrix(ctx, bt, c) for bt, c in zip(bts, csrs)]
     flush = torch.empty(int(256 * 2**20) // 4, dtype=torch.float32, device=dev)
     prec = g.HMAT_MIXED if args.precision == "mixed" else g.HMAT_FP64
+    predictor, pred_info = train_predictor(g, ctx) if args.predictor else (None, None)
 
     def step(precision=prec, mode=g.HMAT_ACCUMULATED):
         for wk, pr in zip(work, pristine):
             wk.copy_values_from(pr)
         if args.op == "lu":
-            g.lu_batched(ctx, work, eps, max_rank=args.max_rank, precision=precision, reuse_schedule=True, mode=mode)
+            g.lu_batched(ctx, work, eps, max_rank=args.max_rank, precision=precision, reuse_schedule=True, mode=mode,
+                         predictor=predictor if precision == prec else None)
         else:  # H-Cholesky or H-inversion: the schedule is built in every call, inside the step
             for wk in work:
                 getattr(wk, args.op)(eps, max_rank=args.max_rank, precision=precision)
@@ -385,7 +410,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         t0 = time.perf_counter()
         Hs = [g.HMatrix(ctx, bt, c) for bt, c in zip(bts, csrs)]
         if args.op == "lu":
-            g.lu_batched(ctx, Hs, eps, max_rank=args.max_rank, precision=prec)
+            g.lu_batched(ctx, Hs, eps, max_rank=args.max_rank, precision=prec, predictor=predictor)
         else:
             for H in Hs:
                 getattr(H, args.op)(eps, max_rank=args.max_rank, precision=prec)
@@ -491,6 +516,8 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         "oracle": ref if args.op == "lu" else None,
         "pcg": pcg,
         "randomised_truncations": st["rand_truncations"], "randomised_fallbacks": st["rand_fallbacks"],
+        "sketch_attempts": st["sketch_attempts"], "sketch_columns": st["sketch_columns"],
+        "rank_predictor": pred_info,
         "plain_fp64": fp64,
         "standard_form": standard,
         "task_types": types,
@@ -737,6 +764,8 @@ def main():
     ap.add_argument("--no-standard", action="store_true", help="skip the standard-form comparator")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end steps (largest workloads)")
+    ap.add_argument("--predictor", action="store_true",
+                    help="train the rank predictor on the smaller configurations' pairs and use it in the timed steps")
     ap.add_argument("--op", default="lu", choices=["lu", "cholesky", "invert"],
                     help="the operation timed on an LU workload: H-LU (default), H-Cholesky or H-inversion")
     ap.add_argument("--time-budget", type=float, default=1650.0,
