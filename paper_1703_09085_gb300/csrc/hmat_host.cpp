@@ -2741,10 +2741,7 @@ void lu_batch(hmat_ctx* ctx, hmat* const* Hs, int count, const hmat_opts* opts) 
     st.truncations = (int64_t)rr.truncations;
     st.flops = rr.flops;
     st.flops32 = rr.flops32;
-  st.bytes = rr.bytes;
-  st.gang_truncations = (int64_t)rr.gang;
     st.bytes = rr.bytes;
-  st.gang_truncations = (int64_t)rr.gang;
     st.gang_truncations = (int64_t)rr.gang;
     st.rand_truncations = (int64_t)rr.rand_ok;
     st.rand_fallbacks = (int64_t)rr.rand_fail;
