@@ -464,9 +464,14 @@ struct Sched {
   // dequeue of the executor sees the available parallelism.
   void order_by_level() {
     size_t n = tasks.size();
+    // a counting sort by level, stable (tasks of one level keep their order)
+    int32_t maxl = 0;
+    for (size_t i = 0; i < n; ++i) maxl = std::max(maxl, level[i]);
+    std::vector<int64_t> start((size_t)maxl + 2, 0);
+    for (size_t i = 0; i < n; ++i) ++start[(size_t)level[i] + 1];
+    for (size_t l = 1; l < start.size(); ++l) start[l] += start[l - 1];
     std::vector<int32_t> ord(n);
-    for (size_t i = 0; i < n; ++i) ord[i] = (int32_t)i;
-    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return level[(size_t)a] < level[(size_t)b]; });
+    for (size_t i = 0; i < n; ++i) ord[(size_t)start[(size_t)level[i]]++] = (int32_t)i;
     std::vector<int32_t> pos(n);
     for (size_t i = 0; i < n; ++i) pos[(size_t)ord[i]] = (int32_t)i;
     std::vector<HTask> t2(n);
