@@ -318,6 +318,19 @@ struct Sched {
   std::vector<float> feat;      // 4 static features per task (truncations only)
   std::vector<int32_t> level;   // longest chain of predecessors (ASAP level)
   std::vector<double> cpath;    // estimated flops of the longest chain ending here
+
+  // Room for the tasks an H-LU of nblocks blocks emits (about 43 per block at
+  // 64^3, three dependencies per task), so that the lists grow without being
+  // copied; a larger schedule still grows as usual.
+  void reserve_for_blocks(size_t nblocks) {
+    size_t nt = 48 * nblocks;
+    tasks.reserve(nt);
+    dep_ptr.reserve(nt + 1);
+    dep_idx.reserve(3 * nt);
+    level.reserve(nt);
+    cpath.reserve(nt);
+    feat.reserve(4 * nt);
+  }
   double est_total = 0.0;
 
   // Rough static cost of a task (ranks unknown on the host: a typical rank 8).
@@ -474,19 +487,36 @@ struct Sched {
     for (size_t i = 0; i < n; ++i) ord[(size_t)start[(size_t)level[i]]++] = (int32_t)i;
     std::vector<int32_t> pos(n);
     for (size_t i = 0; i < n; ++i) pos[(size_t)ord[i]] = (int32_t)i;
-    std::vector<HTask> t2(n);
     std::vector<int64_t> p2(n + 1, 0);
     std::vector<int32_t> d2;
     d2.reserve(dep_idx.size());
     for (size_t i = 0; i < n; ++i) {
       int32_t o = ord[i];
-      t2[i] = tasks[(size_t)o];
       for (int64_t k = dep_ptr[(size_t)o]; k < dep_ptr[(size_t)o + 1]; ++k) d2.push_back(pos[(size_t)dep_idx[(size_t)k]]);
       p2[i + 1] = (int64_t)d2.size();
     }
-    tasks.swap(t2);
     dep_ptr.swap(p2);
     dep_idx.swap(d2);
+    // the tasks themselves permuted in place, cycle by cycle (position j
+    // takes the task that was at ord[j]): no second copy of the list
+    {
+      std::vector<char> done(n, 0);
+      for (size_t i = 0; i < n; ++i) {
+        if (done[i]) continue;
+        HTask first = tasks[i];
+        size_t j = i;
+        for (;;) {
+          size_t k = (size_t)ord[j];
+          done[j] = 1;
+          if (k == i) {
+            tasks[j] = first;
+            break;
+          }
+          tasks[j] = tasks[k];
+          j = k;
+        }
+      }
+    }
     std::vector<int32_t> l2(n);
     std::vector<double> c2(n);
     std::vector<float> f2(4 * n);
@@ -2406,6 +2436,7 @@ void check_opts(const hmat_opts* opts, bool standard_ok) {
 // Symbolic H-LU of H into S (ordered by level); returns host seconds.
 double schedule_lu(hmat* H, int64_t max_rank, bool mixed, bool standard, Sched& S) {
   auto t0 = std::chrono::steady_clock::now();
+  S.reserve_for_blocks(H->bt->nodes.size());
   S.next_slot = H->nslots;
   Sym sym(S, *H->bt->R, *H->bt->C, max_rank);
   sym.mixed = mixed;
@@ -2414,12 +2445,8 @@ double schedule_lu(hmat* H, int64_t max_rank, bool mixed, bool standard, Sched& 
   if (standard) {
     sym.lu_std(H, 0);
   } else {
-    if (standard) {
-      sym.lu_std(H, 0);
-    } else {
-      SAcc root = sym.acc_new(0, 0);
-      sym.lu(H, 0, root);
-    }
+    SAcc root = sym.acc_new(0, 0);
+    sym.lu(H, 0, root);
   }
   S.order_by_level();
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -2686,6 +2713,9 @@ void lu_batch(hmat_ctx* ctx, hmat* const* Hs, int count, const hmat_opts* opts) 
   }
   Sched& S = C->S;
   if (!hit) {
+  size_t nblocks = 0;
+  for (int i = 0; i < count; ++i) nblocks += Hs[i]->bt->nodes.size();
+  S.reserve_for_blocks(nblocks);
   S.next_slot = nslots;
   for (int i = 0; i < count; ++i) {
     hmat* H = Hs[i];
