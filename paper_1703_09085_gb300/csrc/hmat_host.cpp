@@ -22,6 +22,7 @@
 #include <memory>
 #include <stdexcept>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "hmat.h"
@@ -287,6 +288,25 @@ namespace {
 // ===========================================================================
 // Task scheduler
 // ===========================================================================
+// f(begin, end) over [0, n) split into contiguous chunks run by up to 8 host
+// threads (one chunk, on the calling thread, for small n).  f must not throw.
+template <class F>
+void host_chunks(size_t n, F f) {
+  unsigned nt = std::min(8u, std::max(1u, std::thread::hardware_concurrency()));
+  if (n < ((size_t)1 << 16) || nt <= 1) {
+    f((size_t)0, n);
+    return;
+  }
+  size_t chunk = (n + nt - 1) / nt;
+  std::vector<std::thread> th;
+  for (unsigned t = 1; t < nt; ++t) {
+    size_t b = t * chunk, e = std::min(n, b + chunk);
+    if (b < e) th.emplace_back([&f, b, e] { f(b, e); });
+  }
+  f((size_t)0, std::min(n, chunk));
+  for (std::thread& x : th) x.join();
+}
+
 struct Sched {
   std::vector<HTask> tasks;
   std::vector<int64_t> dep_ptr{0};
@@ -485,50 +505,46 @@ struct Sched {
     for (size_t l = 1; l < start.size(); ++l) start[l] += start[l - 1];
     std::vector<int32_t> ord(n);
     for (size_t i = 0; i < n; ++i) ord[(size_t)start[(size_t)level[i]]++] = (int32_t)i;
+    // the gathers below touch memory in random order: split over host threads
     std::vector<int32_t> pos(n);
-    for (size_t i = 0; i < n; ++i) pos[(size_t)ord[i]] = (int32_t)i;
+    host_chunks(n, [&](size_t b, size_t e) {
+      for (size_t i = b; i < e; ++i) pos[(size_t)ord[i]] = (int32_t)i;
+    });
     std::vector<int64_t> p2(n + 1, 0);
-    std::vector<int32_t> d2;
-    d2.reserve(dep_idx.size());
-    for (size_t i = 0; i < n; ++i) {
-      int32_t o = ord[i];
-      for (int64_t k = dep_ptr[(size_t)o]; k < dep_ptr[(size_t)o + 1]; ++k) d2.push_back(pos[(size_t)dep_idx[(size_t)k]]);
-      p2[i + 1] = (int64_t)d2.size();
-    }
+    for (size_t i = 0; i < n; ++i) p2[i + 1] = p2[i] + (dep_ptr[(size_t)ord[i] + 1] - dep_ptr[(size_t)ord[i]]);
+    std::vector<int32_t> d2((size_t)p2[n]);
+    host_chunks(n, [&](size_t b, size_t e) {
+      for (size_t i = b; i < e; ++i) {
+        int64_t o = ord[i], at = p2[i];
+        for (int64_t k = dep_ptr[(size_t)o]; k < dep_ptr[(size_t)o + 1]; ++k) d2[(size_t)at++] = pos[(size_t)dep_idx[(size_t)k]];
+      }
+    });
     dep_ptr.swap(p2);
     dep_idx.swap(d2);
-    // the tasks themselves permuted in place, cycle by cycle (position j
-    // takes the task that was at ord[j]): no second copy of the list
     {
-      std::vector<char> done(n, 0);
-      for (size_t i = 0; i < n; ++i) {
-        if (done[i]) continue;
-        HTask first = tasks[i];
-        size_t j = i;
-        for (;;) {
-          size_t k = (size_t)ord[j];
-          done[j] = 1;
-          if (k == i) {
-            tasks[j] = first;
-            break;
-          }
-          tasks[j] = tasks[k];
-          j = k;
-        }
-      }
+      // the tasks gathered into fresh storage (first touched by the threads that
+      // fill it), then copied back in order
+      std::unique_ptr<HTask[]> t2(new HTask[n]);
+      host_chunks(n, [&](size_t b, size_t e) {
+        for (size_t i = b; i < e; ++i) t2[i] = tasks[(size_t)ord[i]];
+      });
+      host_chunks(n, [&](size_t b, size_t e) { std::copy(t2.get() + b, t2.get() + e, tasks.begin() + (ptrdiff_t)b); });
     }
     std::vector<int32_t> l2(n);
     std::vector<double> c2(n);
     std::vector<float> f2(4 * n);
-    for (size_t i = 0; i < n; ++i) {
-      l2[i] = level[(size_t)ord[i]];
-      c2[i] = cpath[(size_t)ord[i]];
-      for (int k = 0; k < 4; ++k) f2[4 * i + k] = feat[4 * (size_t)ord[i] + k];
-    }
+    host_chunks(n, [&](size_t b, size_t e) {
+      for (size_t i = b; i < e; ++i) {
+        l2[i] = level[(size_t)ord[i]];
+        c2[i] = cpath[(size_t)ord[i]];
+        for (int k = 0; k < 4; ++k) f2[4 * i + k] = feat[4 * (size_t)ord[i] + k];
+      }
+    });
     level.swap(l2);
     cpath.swap(c2);
     feat.swap(f2);
   }
+
   int32_t levels() const {
     int32_t m = 0;
     for (int32_t l : level) m = std::max(m, l + 1);
