@@ -199,8 +199,8 @@ def job_throughput(units: float, seconds: float, world: int, device=None):
 # The 64^3 figure scales the 32^3 capture by the truncations per launch
 # (621 514 / 34 684): ncu's device-memory save and restore of a 52 GB launch
 # is beyond a capture that ends by itself.
-TRAFFIC = {"laplace3d_32": {"csrc": "10cecb301102f392", "bytes": 5842257920 + 15209673472},
-           "laplace3d_64": {"csrc": "10cecb301102f392", "bytes": round((5842257920 + 15209673472) * 621514 / 34684)}}
+TRAFFIC = {"laplace3d_32": {"csrc": "a7e1365b93d004b9", "bytes": 5842257920 + 15209673472},
+           "laplace3d_64": {"csrc": "a7e1365b93d004b9", "bytes": round((5842257920 + 15209673472) * 621514 / 34684)}}
 
 
 def csrc_hash() -> str:

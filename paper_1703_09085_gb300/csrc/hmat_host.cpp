@@ -301,7 +301,12 @@ void host_chunks(size_t n, F f) {
   std::vector<std::thread> th;
   for (unsigned t = 1; t < nt; ++t) {
     size_t b = t * chunk, e = std::min(n, b + chunk);
-    if (b < e) th.emplace_back([&f, b, e] { f(b, e); });
+    if (b >= e) continue;
+    try {
+      th.emplace_back([&f, b, e] { f(b, e); });
+    } catch (...) {  // no thread to be had: this chunk on the calling thread
+      f(b, e);
+    }
   }
   f((size_t)0, std::min(n, chunk));
   for (std::thread& x : th) x.join();
