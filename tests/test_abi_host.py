@@ -123,3 +123,28 @@ def test_standard_schedule_builds_on_the_host(hm):
     assert std["truncations"] > acc["truncations"] > 0
     assert analyze(7)[0] == hm.HMAT_ERR_ARG
     assert analyze(hm.HMAT_ACCUMULATED, hm.HMAT_MIXED, hm.HMAT_REL_SPEC)[0] == hm.HMAT_ERR_ARG
+
+
+def test_symbolic_pass_is_deterministic(hm):
+    """The schedule of the 32^3 mixed H-LU (about a million tasks, so its level
+    ordering runs on several host threads) comes out the same on every call."""
+    import ctypes
+    p = hs.laplace3d_32()
+    ct = hm.ClusterTree(_NullCtx(), p.coords(), p.leaf)
+    bt = hm.BlockTree(_NullCtx(), ct, ct, p.eta)
+    csr = p.matrix()
+    rp = np.ascontiguousarray(csr.rowptr, np.int64)
+    ci = np.ascontiguousarray(csr.colidx, np.int64)
+    va = np.ascontiguousarray(csr.val, np.float64)
+    runs = []
+    for _ in range(2):
+        o = hm.Opts(p.eps, 0, hm.HMAT_MIXED, 0, 0, None, 0, 0, hm.HMAT_ACCUMULATED, hm.HMAT_REL_FRO)
+        st = hm.Stats()
+        assert hm.lib().hmat_analyze_lu(bt.h, ctypes.c_int64(csr.n), rp.ctypes.data_as(hm.I64P),
+                                        ci.ctypes.data_as(hm.I64P), va.ctypes.data_as(hm.F64P), ctypes.byref(o),
+                                        ctypes.byref(st)) == 0
+        d = st.as_dict()
+        runs.append(tuple(d[k] for k in ("tasks", "truncations", "levels", "critical_flops", "est_flops",
+                                         "device_bytes")))
+    assert runs[0] == runs[1]
+    assert runs[0][0] > 500000
